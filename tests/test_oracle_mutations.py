@@ -1,0 +1,66 @@
+"""Plant plausible mistakes in a copy of the oracle (on the CPU) and check that
+the pins catch every one: a dropped term, a wrong sign, a swapped index or a
+transposed operand anywhere in the scheme must fail some pin."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "ppmlr_oracle.c")
+
+MUTANTS = {
+    "slope_weight_swapped": ("(2.0 * xi[i - 1] + xi[i]) / (xi[i + 1] + xi[i])",
+                             "(2.0 * xi[i + 1] + xi[i]) / (xi[i + 1] + xi[i])"),
+    "edge_slope_sign": ("- x1 * z1 * dmi1 + x2 * z2 * dmi", "+ x1 * z1 * dmi1 + x2 * z2 * dmi"),
+    "edge_z_swapped": ("double z1 = (x0 + x1) / (2.0 * x1 + x2);", "double z1 = (x0 + x1) / (2.0 * x2 + x1);"),
+    "limiter_bound": ("double lim_m = 2.0 * fabs(dm)", "double lim_m = 4.0 * fabs(dm)"),
+    "monotone_wrong_edge": ("l = 3.0 * ai - 2.0 * r;", "l = 3.0 * ai - 2.0 * l;"),
+    "dod_curvature": ("(1.0 - 2.0 / 3.0 * y) * a6);\n}\ndouble orc_avg_left",
+                      "(1.0 - 1.0 / 3.0 * y) * a6);\n}\ndouble orc_avg_left"),
+    "riemann_pressure_sign": ("L[1] + WR * R[1] + PL - PR)", "L[1] + WR * R[1] + PR - PL)"),
+    "riemann_sigma_sign": ("ZL * ZR * (vR - vL)) / (ZL + ZR);", "ZL * ZR * (vL - vR)) / (ZL + ZR);"),
+    "riemann_impedance_swap": ("double Ps = (WR * PL + WL * PR", "double Ps = (WL * PL + WR * PR"),
+    "lagrange_u_sign": ("double uL = b->q[1][p] - dt *", "double uL = b->q[1][p] + dt *"),
+    "lagrange_energy_index": ("b->dC[6][p] = -dt * (b->rs[7][p] - b->rs[7][p - 1]);",
+                              "b->dC[6][p] = -dt * (b->rs[2][p] - b->rs[2][p - 1]);"),
+    "lagrange_width": ("double dxL = b->dx[p] + dt * (b->rs[0][p] - b->rs[0][p - 1]);",
+                       "double dxL = b->dx[p] + dt * (b->rs[0][p + 1] - b->rs[0][p - 1]);"),
+    "remap_flux_order": ("(b->dC[v][p] + b->F[v][p - 1] - b->F[v][p])", "(b->dC[v][p] + b->F[v][p] - b->F[v][p - 1])"),
+    "remap_donor": ("b->F[v][p] = del * orc_avg_left(b->aL[v][p + 1], b->aR[v][p + 1], b->a6[v][p + 1], y);",
+                    "b->F[v][p] = del * orc_avg_left(b->aL[v][p], b->aR[v][p], b->a6[v][p], y);"),
+    "pressure_half_dropped": ("(E - 0.5 * (mn * mn + m1 * m1 + m2 * m2) / rho", "(E - (mn * mn + m1 * m1 + m2 * m2) / rho"),
+    "alfven_trace_fast": ("double y = (v == 2 || v == 3) ? ya : yf;", "double y = yf;"),
+    "source_curl_sign": ("double J[3] = {0.0, -DB[2], DB[1]};", "double J[3] = {0.0, DB[2], -DB[1]};"),
+    "source_energy_term": ("+ BB[1][0] * cA[0] + BB[1][1] * cA[1] + BB[1][2] * cA[2];",
+                           "+ BB[1][0] * cA[0] - BB[1][1] * cA[1] + BB[1][2] * cA[2];"),
+    "dipole_sign": ("B[2] = M * (3.0 * mr * z + r2) / r5;", "B[2] = M * (3.0 * mr * z - r2) / r5;"),
+    "outflow_ghost": ("else if (kind == BC_OUTFLOW) src = side == 0 ? 0 : N - 1;",
+                      "else if (kind == BC_OUTFLOW) src = side == 0 ? 1 : N - 2;"),
+    "periodic_width": ("if (c->bc[d][0] == BC_PERIODIC) lo = ((-k) % n + n) % n;",
+                       "if (c->bc[d][0] == BC_PERIODIC) lo = k - 1;"),
+    "source_centre_field": ("double Bd0 = b->Bd[0][p], Bd1 = b->Bd[1][p], Bd2 = b->Bd[2][p];",
+                            "double Bd0 = b->Bd[0][p], Bd1 = b->Bd[2][p], Bd2 = b->Bd[1][p];"),
+    "inflow_field_sign": ("double Bp[3] = {c->inflow[4] - Bdg[0]", "double Bp[3] = {c->inflow[4] + Bdg[0]"),
+}
+
+PINS = ["tests/test_oracle_ppm.py", "tests/test_oracle_riemann.py", "tests/test_oracle_sources.py",
+        "tests/test_oracle_scheme.py", "tests/test_golden.py"]
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site not unique/found: {name}"
+    mutated = tmp_path / "mut.c"
+    mutated.write_text(src.replace(old, new))
+    lib = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
+                           "-o", str(lib), str(mutated), "-lm"])
+    env = dict(os.environ, PPMLR_ORACLE_LIB=str(lib), OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "--deselect", "tests/test_oracle_scheme.py::test_brio_wu_self_convergence", *PINS],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"planted mistake {name} passed every pin:\n{r.stdout[-2000:]}"
