@@ -1,0 +1,166 @@
+/*
+ * ppmlr.h -- C ABI of the GB300 (sm_103a) split-sweep PPMLR-MHD library.
+ *
+ * The library advances the ideal-MHD system in B' form of Guo et al.,
+ * "Large Scale GPU Accelerated PPMLR-MHD Simulations for Space Weather
+ * Forecast" (arXiv:1607.02214): conservation laws for rho, rho v, B' = B - B_d
+ * and E with the dipole-coupling terms on the right-hand side, closure
+ * E = p/(gamma-1) + rho v^2/2 + B'^2/2 (Sec. II, mu0 = 1 in code units).  One
+ * step is three directionally split 1D sweeps (Sec. III-A), each a PPM
+ * reconstruction, a characteristic Lagrangian step and a remap to the Eulerian
+ * grid (Sec. II), with the solar-wind inflow, outflow, inner-boundary and
+ * dipole treatment of Secs. II and IV-A.
+ *
+ * Conventions for every call:
+ *   - Status codes: every call returns a ppmlr_status; ppmlr_last_error() gives
+ *     the text of the last failure on that context.  Device-side conditions
+ *     (non-finite state, CFL violation) are raised by kernels into a device
+ *     flag word and reported by the next synchronising call (ppmlr_cfl_dt,
+ *     ppmlr_get_state, ppmlr_check).  Kernels never trap and never spin.
+ *   - State layout: 8 arrays of nx*ny*nz doubles, x fastest then y then z, in
+ *     the order rho, m_x, m_y, m_z, B'_x, B'_y, B'_z, E (interior cells only;
+ *     no ghost cells are stored).  Callers' arrays are only copied.
+ *   - Ownership: the context owns all the device memory it allocates
+ *     (ppmlr_create) and frees it in ppmlr_destroy.  Pointers passed in remain
+ *     the caller's.
+ *   - Streams: all work of a context is issued on its CUDA stream (the one
+ *     given at create time or by ppmlr_set_stream; NULL = legacy default).
+ */
+#ifndef PPMLR_H
+#define PPMLR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PPMLR_OK = 0,
+    PPMLR_E_INVALID = 1,    /* bad argument (NULL, size, enum, non-positive width ...) */
+    PPMLR_E_CUDA = 2,       /* a CUDA runtime call failed */
+    PPMLR_E_OOM = 3,        /* device allocation failed */
+    PPMLR_E_NONFINITE = 4,  /* a sweep produced a non-finite conserved value */
+    PPMLR_E_CFL = 5,        /* dt too large: a Lagrangian width <= 0 or a remap sliver >= one zone */
+    PPMLR_E_TIMEOUT = 6     /* a bounded device wait gave up */
+} ppmlr_status;
+
+typedef enum {
+    PPMLR_FP64 = 0,         /* every stage in IEEE double, no fused multiply-add */
+    PPMLR_MIXED = 1         /* FP32 reconstruction, Riemann, remap and sources; FP64 pressure
+                               recovery and FP64 state accumulation */
+} ppmlr_precision;
+
+typedef enum { PPMLR_BC_PERIODIC = 0, PPMLR_BC_OUTFLOW = 1, PPMLR_BC_INFLOW = 2 } ppmlr_bc_kind;
+
+/* Grid: n[d] cells along axis d (x, y, z); edges[d] points to n[d]+1 strictly
+ * ascending cell edges in host memory (copied at create time).  A stretched
+ * Cartesian grid as in Sec. III-B is given by its edges. */
+typedef struct {
+    int n[3];
+    const double *edges[3];
+} ppmlr_grid;
+
+/* Primitive state: density, velocity, TOTAL magnetic field B, thermal pressure. */
+typedef struct {
+    double rho, v[3], B[3], p;
+} ppmlr_prim;
+
+/* Boundary specification (Secs. II and IV-A):
+ *   face[axis][0|1]: kind of the low/high face of each axis.  PERIODIC wraps
+ *     (both faces of an axis must then be periodic); OUTFLOW copies the edge
+ *     cell; INFLOW imposes `inflow` with B' = inflow.B - B_d(ghost centre).
+ *     Ghost widths wrap on periodic faces and mirror the edge cells otherwise.
+ *   dipole_moment: M = B_E R_E^3 in code units, moment along -z (GSM, zero
+ *     tilt): B_d = M [3 (m.r) r - m r^2] / r^5, m = -z.  0 disables B_d and
+ *     its source terms.
+ *   r_inner, inner: cells with centre radius < r_inner are reset after every
+ *     sweep to rho = inner.rho, v = inner.v, p = inner.p and B' = 0 (inner.B is
+ *     ignored).  r_inner <= 0 disables the inner sphere.
+ *   p_min: pressure floor applied when recovering p from E; every use is
+ *     counted (ppmlr_get_diagnostics).
+ *   powell: 1 adds the -v div B' term of the induction equation. */
+typedef struct {
+    int face[3][2];
+    ppmlr_prim inflow;
+    double dipole_moment;
+    double r_inner;
+    ppmlr_prim inner;
+    double p_min;
+    int powell;
+} ppmlr_bc;
+
+typedef struct ppmlr_ctx ppmlr_ctx;
+
+/* Create a context on the current CUDA device: copies the grid, builds the
+ * ghost-extended geometry, allocates the state (2 x 8 arrays) and scratch.
+ * gamma > 1.  cuda_stream: a cudaStream_t (NULL = default stream).
+ * Errors: PPMLR_E_INVALID (NULL pointers, n < 1, non-ascending edges, bad
+ * face kinds, periodic on one face only), PPMLR_E_OOM, PPMLR_E_CUDA.  On
+ * failure *out is set to NULL. */
+ppmlr_status ppmlr_create(const ppmlr_grid *grid, double gamma, const ppmlr_bc *bc,
+                          ppmlr_precision prec, void *cuda_stream, ppmlr_ctx **out);
+
+/* Replace the stream used for all later work of the context. */
+ppmlr_status ppmlr_set_stream(ppmlr_ctx *ctx, void *cuda_stream);
+
+/* Copy a state in (U[v] = 8 arrays of nx*ny*nz doubles, layout above).
+ * on_device = 1: device pointers (copied on the context stream, asynchronous);
+ * 0: host pointers (the call returns once the copy is done).  Resets the
+ * device flag word. */
+ppmlr_status ppmlr_set_state(ppmlr_ctx *ctx, const double *const U[8], int on_device);
+
+/* Copy the state out (same layout).  Synchronises the context stream and
+ * reports pending device flags (PPMLR_E_NONFINITE / PPMLR_E_CFL) after the
+ * copy has completed. */
+ppmlr_status ppmlr_get_state(ppmlr_ctx *ctx, double *const U[8], int on_device);
+
+/* CFL time step (reading of the paper, which states none):
+ *   dt = cfl * min over non-inner interior cells and axes d of
+ *        dx_d / (|v_d| + max(c_f,d(B'), c_f,d(B' + B_d))).
+ * Computed on the device by a block-min reduction (no float atomics) and
+ * copied to *dt_out (synchronises).  The value also stays on the device for
+ * ppmlr_step_cfl.  Reports pending device flags. */
+ppmlr_status ppmlr_cfl_dt(ppmlr_ctx *ctx, double cfl, double *dt_out);
+
+/* One full step with the given dt: three sweeps, x,y,z on even steps and
+ * z,y,x on odd steps (Strang-type alternation; the paper does not state the
+ * order).  Asynchronous: device flags are reported by the next synchronising
+ * call.  dt must be finite and > 0 (else PPMLR_E_INVALID). */
+ppmlr_status ppmlr_step(ppmlr_ctx *ctx, double dt);
+
+/* nsteps steps, each with its dt computed on the device from the state at
+ * the start of that step (as ppmlr_cfl_dt with `cfl`), with no host
+ * synchronisation.  Asynchronous. */
+ppmlr_status ppmlr_step_cfl(ppmlr_ctx *ctx, double cfl, int nsteps);
+
+/* A single sweep along `axis` (0, 1, 2) with the given dt; does not advance
+ * the step counter.  For testing a sweep in isolation. */
+ppmlr_status ppmlr_sweep(ppmlr_ctx *ctx, int axis, double dt);
+
+/* Synchronise the context stream and report pending device flags. */
+ppmlr_status ppmlr_check(ppmlr_ctx *ctx);
+
+/* Diagnostics (synchronises): steps taken, pressure-floor uses so far
+ * (summed over sweeps), parity of the next step's sweep order (0: x,y,z). */
+ppmlr_status ppmlr_get_diagnostics(ppmlr_ctx *ctx, long long *step, long long *floor_hits, int *order_parity);
+
+/* Restore the step counter (checkpoint/resume: the state plus this counter
+ * reproduce a run bit for bit). */
+ppmlr_status ppmlr_set_step_count(ppmlr_ctx *ctx, long long step);
+
+/* dt of the most recent ppmlr_cfl_dt / ppmlr_step_cfl step (synchronises). */
+ppmlr_status ppmlr_get_dt(ppmlr_ctx *ctx, double *dt_out);
+
+/* Text of the last error on this context ("" if none; static string for a
+ * NULL context). */
+const char *ppmlr_last_error(const ppmlr_ctx *ctx);
+
+/* Free everything the context owns.  NULL is ignored. */
+void ppmlr_destroy(ppmlr_ctx *ctx);
+
+/* Kernel launches issued by this context so far (all kinds). */
+long long ppmlr_launch_count(const ppmlr_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PPMLR_H */

@@ -1,0 +1,398 @@
+// Host side of the C ABI declared in include/ppmlr.h: context lifetime,
+// ghost-extended geometry, state copies, sweep/step/CFL launches and the
+// device status word.  Built with -ffp-contract=off so that the geometry is
+// computed with the same IEEE double operations as the CPU reference.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "ppmlr_internal.h"
+
+using namespace ppmlr;
+
+struct ppmlr_ctx {
+    int n[3];
+    long long ncell;
+    double gamma;
+    ppmlr_bc bc;
+    ppmlr_precision prec;
+    cudaStream_t stream;
+    int device;
+    double *state;               // 16 arrays: U (8) then Unew (8), each padded
+    size_t stride;               // elements between arrays
+    double *U[8], *Un[8];
+    double *geo;                 // w[3], c[3]
+    double *w[3], *c[3];
+    int *flags;
+    unsigned long long *floors;
+    double *dt_dev;
+    double *partial;
+    unsigned int *counter;
+    int cfl_blocks;
+    Tile tile[3];
+    long long steps;
+    long long launches;
+    std::string err;
+};
+
+static const char *k_null_ctx = "null context";
+
+static ppmlr_status fail(ppmlr_ctx *c, ppmlr_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+static ppmlr_status cuda_fail(ppmlr_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, e == cudaErrorMemoryAllocation ? PPMLR_E_OOM : PPMLR_E_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(c, call, what)                                \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+// Ghost-extended widths and centres of one axis (same rules and arithmetic as
+// the CPU reference): periodic faces wrap, other faces mirror the edge widths
+// (clamped to the axis); centres extend the grid by the ghost widths.
+static void build_axis(int n, const double *edges, int bc_lo, int bc_hi, std::vector<double> &w,
+                       std::vector<double> &ce)
+{
+    w.assign(n + 2 * GH, 0.0);
+    ce.assign(n + 2 * GH, 0.0);
+    for (int i = 0; i < n; i++) w[GH + i] = edges[i + 1] - edges[i];
+    for (int k = 1; k <= GH; k++) {
+        int lo, hi;
+        if (bc_lo == PPMLR_BC_PERIODIC) lo = ((-k) % n + n) % n;
+        else { lo = k - 1; if (lo > n - 1) lo = n - 1; }
+        if (bc_hi == PPMLR_BC_PERIODIC) hi = (k - 1) % n;
+        else { hi = n - k; if (hi < 0) hi = 0; }
+        w[GH - k] = w[GH + lo];
+        w[GH + n - 1 + k] = w[GH + hi];
+    }
+    for (int i = 0; i < n; i++) ce[GH + i] = 0.5 * (edges[i] + edges[i + 1]);
+    double e = edges[0];
+    for (int k = 1; k <= GH; k++) { ce[GH - k] = e - 0.5 * w[GH - k]; e -= w[GH - k]; }
+    e = edges[n];
+    for (int k = 1; k <= GH; k++) { ce[GH + n - 1 + k] = e + 0.5 * w[GH + n - 1 + k]; e += w[GH + n - 1 + k]; }
+}
+
+// Tile shape for a sweep along an axis of N cells: whole pencils when they fit
+// in MAXT positions, else equal chunks; as many lanes as fit (powers of two
+// for the y/z sweeps, whose lanes are consecutive x cells).
+static Tile choose_tile(int dir, const int n[3], size_t real_size)
+{
+    Tile t;
+    const int N = n[dir];
+    t.nchunk = 1;
+    t.C = N;
+    while (t.C + 2 * GH > MAXT) {
+        t.nchunk++;
+        t.C = (N + t.nchunk - 1) / t.nchunk;
+    }
+    t.NP = t.C + 2 * GH;
+    int L = MAXT / t.NP;
+    if (L < 1) L = 1;
+    if (dir == 0) {
+        long long pencils = (long long)n[1] * n[2];
+        if (L > pencils) L = (int)pencils;
+        t.L = L;
+        t.ngx = (int)((pencils + L - 1) / L);
+        t.ntiles = t.ngx * t.nchunk;
+    } else {
+        int p2 = 1;
+        while (p2 * 2 <= L && p2 * 2 <= 16) p2 *= 2;
+        while (p2 > 1 && p2 / 2 >= n[0]) p2 /= 2;
+        t.L = p2;
+        t.ngx = (n[0] + t.L - 1) / t.L;
+        int other = dir == 1 ? n[2] : n[1];
+        t.ntiles = t.ngx * other * t.nchunk;
+    }
+    t.threads = ((t.NP * t.L + 31) / 32) * 32;
+    t.smem = (size_t)NSM * t.NP * t.L * real_size;
+    return t;
+}
+
+static bool is_sweep_noop(const ppmlr_ctx *c, int d)
+{
+    return c->n[d] == 1 && c->bc.face[d][0] == PPMLR_BC_PERIODIC && c->bc.face[d][1] == PPMLR_BC_PERIODIC &&
+           c->bc.dipole_moment == 0.0;
+}
+
+extern "C" {
+
+ppmlr_status ppmlr_create(const ppmlr_grid *grid, double gamma, const ppmlr_bc *bc, ppmlr_precision prec,
+                          void *cuda_stream, ppmlr_ctx **out)
+{
+    if (!out) return PPMLR_E_INVALID;
+    *out = nullptr;
+    if (!grid || !bc) return PPMLR_E_INVALID;
+    if (!(gamma > 1.0) || (prec != PPMLR_FP64 && prec != PPMLR_MIXED)) return PPMLR_E_INVALID;
+    for (int d = 0; d < 3; d++) {
+        if (grid->n[d] < 1 || !grid->edges[d]) return PPMLR_E_INVALID;
+        for (int i = 0; i < grid->n[d]; i++)
+            if (!(grid->edges[d][i + 1] > grid->edges[d][i])) return PPMLR_E_INVALID;
+        for (int s = 0; s < 2; s++)
+            if (bc->face[d][s] < PPMLR_BC_PERIODIC || bc->face[d][s] > PPMLR_BC_INFLOW) return PPMLR_E_INVALID;
+        if ((bc->face[d][0] == PPMLR_BC_PERIODIC) != (bc->face[d][1] == PPMLR_BC_PERIODIC)) return PPMLR_E_INVALID;
+    }
+    bool any_inflow = false;
+    for (int d = 0; d < 3; d++) any_inflow |= bc->face[d][0] == PPMLR_BC_INFLOW || bc->face[d][1] == PPMLR_BC_INFLOW;
+    if (!(bc->p_min >= 0.0)) return PPMLR_E_INVALID;
+    if (any_inflow && !(bc->inflow.rho > 0.0 && bc->inflow.p > 0.0)) return PPMLR_E_INVALID;
+    if (bc->r_inner > 0.0 && !(bc->inner.rho > 0.0 && bc->inner.p >= 0.0)) return PPMLR_E_INVALID;
+    long long ncell = (long long)grid->n[0] * grid->n[1] * grid->n[2];
+    if (ncell > (1LL << 31) - 1) return PPMLR_E_INVALID;
+
+    ppmlr_ctx *c = new ppmlr_ctx();
+    memcpy(c->n, grid->n, sizeof(c->n));
+    c->ncell = ncell;
+    c->gamma = gamma;
+    c->bc = *bc;
+    c->prec = prec;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->steps = 0;
+    c->launches = 0;
+    if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return PPMLR_E_CUDA; }
+
+    // state: 16 arrays, each padded to 256-byte multiples
+    c->stride = ((size_t)ncell + 31) / 32 * 32;
+    cudaError_t e = cudaMalloc(&c->state, sizeof(double) * c->stride * 16);
+    if (e != cudaSuccess) { delete c; return e == cudaErrorMemoryAllocation ? PPMLR_E_OOM : PPMLR_E_CUDA; }
+    for (int v = 0; v < 8; v++) { c->U[v] = c->state + v * c->stride; c->Un[v] = c->state + (8 + v) * c->stride; }
+
+    // geometry
+    std::vector<double> host;
+    size_t off[6];
+    for (int d = 0; d < 3; d++) {
+        std::vector<double> w, ce;
+        build_axis(grid->n[d], grid->edges[d], bc->face[d][0], bc->face[d][1], w, ce);
+        off[d] = host.size(); host.insert(host.end(), w.begin(), w.end());
+        off[3 + d] = host.size(); host.insert(host.end(), ce.begin(), ce.end());
+    }
+    int dev_sms = 152;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device);
+    c->cfl_blocks = dev_sms * 4;
+    long long need_blocks = (ncell + cfl_threads() - 1) / cfl_threads();
+    if (need_blocks < c->cfl_blocks) c->cfl_blocks = (int)need_blocks;
+    size_t scratch_bytes = sizeof(double) * (host.size() + 2 + c->cfl_blocks) + 64;
+    e = cudaMalloc(&c->geo, scratch_bytes);
+    if (e != cudaSuccess) { cudaFree(c->state); delete c; return PPMLR_E_OOM; }
+    for (int d = 0; d < 3; d++) { c->w[d] = c->geo + off[d]; c->c[d] = c->geo + off[3 + d]; }
+    c->dt_dev = c->geo + host.size();
+    c->partial = c->dt_dev + 2;
+    unsigned char *tail = reinterpret_cast<unsigned char *>(c->partial + c->cfl_blocks);
+    c->flags = reinterpret_cast<int *>(tail);
+    c->counter = reinterpret_cast<unsigned int *>(tail + 8);
+    c->floors = reinterpret_cast<unsigned long long *>(tail + 16);
+    e = cudaMemcpyAsync(c->geo, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->dt_dev, 0, sizeof(double) * (2 + c->cfl_blocks) + 64, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->state, 0, sizeof(double) * c->stride * 16, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) { cudaFree(c->geo); cudaFree(c->state); delete c; return PPMLR_E_CUDA; }
+    size_t rs = prec == PPMLR_FP64 ? sizeof(double) : sizeof(float);
+    for (int d = 0; d < 3; d++) c->tile[d] = choose_tile(d, c->n, rs);
+    *out = c;
+    return PPMLR_OK;
+}
+
+void ppmlr_destroy(ppmlr_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->geo);
+    cudaFree(c->state);
+    delete c;
+}
+
+const char *ppmlr_last_error(const ppmlr_ctx *c) { return c ? c->err.c_str() : k_null_ctx; }
+
+long long ppmlr_launch_count(const ppmlr_ctx *c) { return c ? c->launches : 0; }
+
+ppmlr_status ppmlr_set_stream(ppmlr_ctx *c, void *stream)
+{
+    if (!c) return PPMLR_E_INVALID;
+    c->stream = (cudaStream_t)stream;
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_set_state(ppmlr_ctx *c, const double *const U[8], int on_device)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (!U) return fail(c, PPMLR_E_INVALID, "set_state: null array list");
+    for (int v = 0; v < 8; v++)
+        if (!U[v]) return fail(c, PPMLR_E_INVALID, "set_state: null array");
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int v = 0; v < 8; v++)
+        CK(c, cudaMemcpyAsync(c->U[v], U[v], sizeof(double) * c->ncell, kind, c->stream), "set_state copy");
+    CK(c, cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream), "set_state flags");
+    if (!on_device) CK(c, cudaStreamSynchronize(c->stream), "set_state sync");
+    return PPMLR_OK;
+}
+
+static ppmlr_status read_flags(ppmlr_ctx *c)
+{
+    int f = 0;
+    CK(c, cudaMemcpyAsync(&f, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flags copy");
+    CK(c, cudaStreamSynchronize(c->stream), "stream sync");
+    if (f) {
+        CK(c, cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream), "flags reset");
+        if (f & FLAG_NONFINITE) return fail(c, PPMLR_E_NONFINITE, "a sweep produced a non-finite state");
+        return fail(c, PPMLR_E_CFL, "time step too large for the CFL condition");
+    }
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_check(ppmlr_ctx *c)
+{
+    if (!c) return PPMLR_E_INVALID;
+    CK(c, cudaStreamSynchronize(c->stream), "stream sync");
+    return read_flags(c);
+}
+
+ppmlr_status ppmlr_get_state(ppmlr_ctx *c, double *const U[8], int on_device)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (!U) return fail(c, PPMLR_E_INVALID, "get_state: null array list");
+    for (int v = 0; v < 8; v++)
+        if (!U[v]) return fail(c, PPMLR_E_INVALID, "get_state: null array");
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    for (int v = 0; v < 8; v++)
+        CK(c, cudaMemcpyAsync(U[v], c->U[v], sizeof(double) * c->ncell, kind, c->stream), "get_state copy");
+    return read_flags(c);
+}
+
+static ppmlr_status launch_one_sweep(ppmlr_ctx *c, int d, double dt, const double *dt_dev)
+{
+    if (is_sweep_noop(c, d)) return PPMLR_OK;
+    SweepArgs a;
+    memset(&a, 0, sizeof(a));
+    for (int v = 0; v < 8; v++) { a.U[v] = c->U[v]; a.Un[v] = c->Un[v]; }
+    for (int k = 0; k < 3; k++) a.n[k] = c->n[k];
+    const Tile &t = c->tile[d];
+    a.N = c->n[d];
+    a.C = t.C; a.L = t.L; a.NP = t.NP; a.nchunk = t.nchunk; a.ngx = t.ngx;
+    a.w = c->w[d]; a.c = c->c[d];
+    a.cx = c->c[0]; a.cy = c->c[1]; a.cz = c->c[2];
+    a.bc_lo = c->bc.face[d][0]; a.bc_hi = c->bc.face[d][1];
+    const ppmlr_prim &f = c->bc.inflow;
+    double infl[8] = {f.rho, f.v[0], f.v[1], f.v[2], f.B[0], f.B[1], f.B[2], f.p};
+    memcpy(a.inflow, infl, sizeof(infl));
+    const ppmlr_prim &q = c->bc.inner;
+    double inn[8] = {q.rho, q.v[0], q.v[1], q.v[2], 0.0, 0.0, 0.0, q.p};
+    memcpy(a.inner, inn, sizeof(inn));
+    a.gamma = c->gamma; a.p_min = c->bc.p_min; a.M = c->bc.dipole_moment; a.r_inner = c->bc.r_inner;
+    a.powell = c->bc.powell ? 1 : 0;
+    a.do_src = (a.M != 0.0 || a.powell) ? 1 : 0;
+    a.dt = dt; a.dt_dev = dt_dev;
+    a.flags = c->flags; a.floors = c->floors;
+    cudaError_t e = c->prec == PPMLR_FP64 ? launch_sweep_fp64(d, a, t, c->stream)
+                                          : launch_sweep_mixed(d, a, t, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
+    c->launches++;
+    for (int v = 0; v < 8; v++) { double *tmp = c->U[v]; c->U[v] = c->Un[v]; c->Un[v] = tmp; }
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_sweep(ppmlr_ctx *c, int axis, double dt)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (axis < 0 || axis > 2) return fail(c, PPMLR_E_INVALID, "sweep: axis must be 0, 1 or 2");
+    if (!(dt > 0.0) || !isfinite(dt)) return fail(c, PPMLR_E_INVALID, "sweep: dt must be finite and > 0");
+    return launch_one_sweep(c, axis, dt, nullptr);
+}
+
+static ppmlr_status do_step(ppmlr_ctx *c, double dt, const double *dt_dev)
+{
+    const int order_even[3] = {0, 1, 2}, order_odd[3] = {2, 1, 0};
+    const int *ord = (c->steps & 1) ? order_odd : order_even;
+    for (int k = 0; k < 3; k++) {
+        ppmlr_status s = launch_one_sweep(c, ord[k], dt, dt_dev);
+        if (s != PPMLR_OK) return s;
+    }
+    c->steps++;
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_step(ppmlr_ctx *c, double dt)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (!(dt > 0.0) || !isfinite(dt)) return fail(c, PPMLR_E_INVALID, "step: dt must be finite and > 0");
+    return do_step(c, dt, nullptr);
+}
+
+static ppmlr_status launch_cfl_kernel(ppmlr_ctx *c, double cfl)
+{
+    CflArgs a;
+    memset(&a, 0, sizeof(a));
+    for (int v = 0; v < 8; v++) a.U[v] = c->U[v];
+    for (int d = 0; d < 3; d++) { a.n[d] = c->n[d]; a.w[d] = c->w[d]; a.c[d] = c->c[d]; }
+    a.gamma = c->gamma; a.p_min = c->bc.p_min; a.M = c->bc.dipole_moment; a.r_inner = c->bc.r_inner;
+    a.cfl = cfl;
+    a.partial = c->partial; a.counter = c->counter; a.dt_out = c->dt_dev;
+    cudaError_t e = launch_cfl(a, c->cfl_blocks, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cfl launch");
+    c->launches++;
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_cfl_dt(ppmlr_ctx *c, double cfl, double *dt_out)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (!dt_out || !(cfl > 0.0)) return fail(c, PPMLR_E_INVALID, "cfl_dt: need cfl > 0 and an output pointer");
+    ppmlr_status s = launch_cfl_kernel(c, cfl);
+    if (s != PPMLR_OK) return s;
+    CK(c, cudaMemcpyAsync(dt_out, c->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "dt copy");
+    return read_flags(c);
+}
+
+ppmlr_status ppmlr_step_cfl(ppmlr_ctx *c, double cfl, int nsteps)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (!(cfl > 0.0) || nsteps < 0) return fail(c, PPMLR_E_INVALID, "step_cfl: need cfl > 0, nsteps >= 0");
+    for (int k = 0; k < nsteps; k++) {
+        ppmlr_status s = launch_cfl_kernel(c, cfl);
+        if (s != PPMLR_OK) return s;
+        s = do_step(c, 0.0, c->dt_dev);
+        if (s != PPMLR_OK) return s;
+    }
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_get_dt(ppmlr_ctx *c, double *dt_out)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (!dt_out) return fail(c, PPMLR_E_INVALID, "get_dt: null output");
+    CK(c, cudaMemcpyAsync(dt_out, c->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "dt copy");
+    CK(c, cudaStreamSynchronize(c->stream), "stream sync");
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_get_diagnostics(ppmlr_ctx *c, long long *step, long long *floor_hits, int *order_parity)
+{
+    if (!c) return PPMLR_E_INVALID;
+    unsigned long long fl = 0;
+    CK(c, cudaMemcpyAsync(&fl, c->floors, sizeof(fl), cudaMemcpyDeviceToHost, c->stream), "floors copy");
+    CK(c, cudaStreamSynchronize(c->stream), "stream sync");
+    if (step) *step = c->steps;
+    if (floor_hits) *floor_hits = (long long)fl;
+    if (order_parity) *order_parity = (int)(c->steps & 1);
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_set_step_count(ppmlr_ctx *c, long long step)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (step < 0) return fail(c, PPMLR_E_INVALID, "set_step_count: negative");
+    c->steps = step;
+    return PPMLR_OK;
+}
+
+}  // extern "C"

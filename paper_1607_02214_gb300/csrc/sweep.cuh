@@ -1,0 +1,554 @@
+// One directional PPMLR sweep on sm_103a: PPM reconstruction with its limiter,
+// characteristic domain-of-dependence states, a linearised Lagrangian MHD
+// Riemann solve per interface, the Lagrangian update, the conservative remap to
+// the Eulerian grid, the directional dipole/Powell sources, the inner-sphere
+// reset and the boundary ghosts -- all fused in one kernel (Sec. II scheme,
+// Sec. III-A split, Secs. II / IV-A boundaries).
+//
+// Thread layout: a tile is L pencils ("lanes") x NP = C + 2*GH positions along
+// the sweep axis; one thread owns one (position, lane) for the whole kernel
+// and keeps its own cell's values in registers between phases.  Only what a
+// neighbour needs crosses threads, through NSM shared-memory arrays of NP*L
+// entries that are reused from phase to phase (barrier-separated).  The thread
+// index is the shared-memory slot: x sweeps run positions fastest (contiguous
+// global rows), y and z sweeps run lanes fastest (consecutive x cells, so every
+// global access of a warp is a set of contiguous row segments: coalesced, no
+// transpose).  A neighbour at position offset k is slot + k*PS.
+//
+// R is the arithmetic type of reconstruction, Riemann, remap and sources:
+// double for the FP64 path (expression trees identical to the CPU reference,
+// compiled without contraction), float for the mixed path (pressure recovery
+// and the state accumulation stay in double).
+#pragma once
+#include <type_traits>
+
+#include "ppmlr_internal.h"
+
+namespace ppmlr {
+
+template <typename R> struct K;
+template <> struct K<double> {
+    static __device__ __forceinline__ double sq(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double ab(double x) { return fabs(x); }
+};
+template <> struct K<float> {
+    static __device__ __forceinline__ float sq(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float ab(float x) { return fabsf(x); }
+};
+
+// Fast magnetosonic speed squared along the normal (mu0 = 1).
+template <typename R>
+__device__ __forceinline__ R fast2(R rho, R p, R Bn, R B1, R B2, R gam)
+{
+    R a2 = gam * p / rho;
+    R b2 = (Bn * Bn + B1 * B1 + B2 * B2) / rho;
+    R bn2 = Bn * Bn / rho;
+    R s = a2 + b2;
+    R disc = s * s - R(4) * a2 * bn2;
+    if (disc < R(0)) disc = R(0);
+    return R(0.5) * (s + K<R>::sq(disc));
+}
+
+// Earth dipole along -z: B_d = M [3 (m.r) r - m r^2] / r^5, m = -z.
+__device__ __forceinline__ void dipole(double M, double x, double y, double z, double *B)
+{
+    double r2 = x * x + y * y + z * z;
+    if (M == 0.0 || r2 == 0.0) { B[0] = B[1] = B[2] = 0.0; return; }
+    double r = sqrt(r2);
+    double r5 = r2 * r2 * r;
+    double mr = -z;
+    B[0] = M * (3.0 * mr * x) / r5;
+    B[1] = M * (3.0 * mr * y) / r5;
+    B[2] = M * (3.0 * mr * z + r2) / r5;
+}
+
+// Limited PPM slope of zone i from its neighbours (Colella & Woodward 1984).
+template <typename R>
+__device__ __forceinline__ R limit_slope(R am, R a0, R ap, R c1, R c2, R c3)
+{
+    R dp = ap - a0;
+    R dm = a0 - am;
+    R da = c1 * (c2 * dp + c3 * dm);
+    if (dp * dm > R(0)) {
+        R m = K<R>::ab(da);
+        R lim_m = R(2) * K<R>::ab(dm), lim_p = R(2) * K<R>::ab(dp);
+        if (lim_m < m) m = lim_m;
+        if (lim_p < m) m = lim_p;
+        return da > R(0) ? m : (da < R(0) ? -m : R(0));
+    }
+    return R(0);
+}
+
+// Monotonicity constraint of the parabola; returns a6 and updates l, r.
+template <typename R>
+__device__ __forceinline__ R monotone(R ai, R &l, R &r)
+{
+    if ((r - ai) * (ai - l) <= R(0)) {
+        l = ai; r = ai;
+    } else {
+        R da = r - l;
+        R m6 = R(6) * (ai - R(0.5) * (l + r));
+        if (da * m6 > da * da) l = R(3) * ai - R(2) * r;
+        else if (-(da * da) > da * m6) r = R(3) * ai - R(2) * l;
+    }
+    return R(6) * (ai - R(0.5) * (l + r));
+}
+
+template <typename R>
+__device__ __forceinline__ R avg_right(R l, R r, R a6, R y)
+{
+    return r - R(0.5) * y * ((r - l) - (R(1) - R(2.0 / 3.0) * y) * a6);
+}
+template <typename R>
+__device__ __forceinline__ R avg_left(R l, R r, R a6, R y)
+{
+    return l + R(0.5) * y * ((r - l) + (R(1) - R(2.0 / 3.0) * y) * a6);
+}
+
+// Coefficients of the PPM slope and interface formulas on a non-uniform
+// coordinate (they depend only on the zone widths, so they are shared by all
+// reconstructed variables).
+template <typename R> struct SlopeCoef { R c1, c2, c3; };
+template <typename R>
+__device__ __forceinline__ SlopeCoef<R> slope_coef(R xm, R x0, R xp)
+{
+    R s3 = xm + x0 + xp;
+    SlopeCoef<R> k;
+    k.c1 = x0 / s3;
+    k.c2 = (R(2) * xm + x0) / (xp + x0);
+    k.c3 = (x0 + R(2) * xp) / (xm + x0);
+    return k;
+}
+template <typename R> struct EdgeCoef { R k1, k2, k3, k4, k5; };
+template <typename R>
+__device__ __forceinline__ EdgeCoef<R> edge_coef(R x0, R x1, R x2, R x3)
+{
+    R z1 = (x0 + x1) / (R(2) * x1 + x2);
+    R z2 = (x3 + x2) / (R(2) * x2 + x1);
+    R s4 = x0 + x1 + x2 + x3;
+    EdgeCoef<R> k;
+    k.k1 = x1 / (x1 + x2);
+    k.k2 = R(1) / s4;
+    k.k3 = R(2) * x2 * x1 / (x1 + x2) * (z1 - z2);
+    k.k4 = x1 * z1;
+    k.k5 = x2 * z2;
+    return k;
+}
+template <typename R>
+__device__ __forceinline__ R edge_value(const EdgeCoef<R> &k, R a0, R a1, R dmi, R dmi1)
+{
+    R d = a1 - a0;
+    return a0 + k.k1 * d + k.k2 * (k.k3 * d - k.k4 * dmi1 + k.k5 * dmi);
+}
+
+// Shared-memory array indices.  Phase by phase (barrier between phases):
+//  P1 writes A (primitives of every position, mass width, total pressure,
+//     normal field, v x B_d);
+//  P2 reads A, writes B (7 limited slopes, flattening indicator);
+//  P3 reads A, B, writes C (7 interface values);
+//  P4 reads C, writes A[0..8] (traced state right of each zone's left edge);
+//  P5 reads A[0..8], A_BN, writes C (Riemann output per interface);
+//  P6 reads C, writes B (7 Lagrangian densities, Lagrangian width);
+//  P7 reads B, writes A[0..6] (7 remap slopes);
+//  P8 reads A, B, writes C (7 remap interface values);
+//  P9 reads C, writes B[0..6] (remap flux through each Eulerian edge);
+//  P10 reads B and writes the new state.
+enum : int {
+    A_RHO = 0, A_U, A_V1, A_V2, A_B1, A_B2, A_P, A_DM, A_PT, A_BN, A_AX, A_AY, A_AZ,
+    SB0 = 13, SC0 = 21
+};
+
+template <int DIR, typename R>
+__global__ void __launch_bounds__(MAXT) sweep_kernel(SweepArgs a)
+{
+    constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
+    constexpr bool F64 = std::is_same<R, double>::value;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *sm = reinterpret_cast<R *>(smem_raw);
+    const int L = a.L, NP = a.NP, NT = NP * L;
+    const int PS = DIR == 0 ? 1 : L;
+    const int s = threadIdx.x;
+#define SM(k, slot) sm[(k) * NT + (slot)]
+
+    // ---- tile decode ----
+    const int chunk = blockIdx.x % a.nchunk;
+    const int grp = blockIdx.x / a.nchunk;
+    int p, l;
+    if (DIR == 0) { l = s / NP; p = s - l * NP; }
+    else { p = s / L; l = s - p * L; }
+    const int g0 = chunk * a.C;
+    const int Ce = min(a.C, a.N - g0);           // output cells of this chunk
+    const int NPe = Ce + 2 * GH;                 // positions in use
+    int ix = 0, iy = 0, iz = 0;
+    bool lane_ok;
+    if (DIR == 0) {
+        int q = grp * L + l;
+        lane_ok = q < a.n[1] * a.n[2];
+        if (lane_ok) { iy = q % a.n[1]; iz = q / a.n[1]; }
+    } else {
+        int xg = grp % a.ngx, t = grp / a.ngx;
+        ix = xg * L + l;
+        lane_ok = ix < a.n[0];
+        if (DIR == 1) iz = t; else iy = t;
+    }
+    const bool act = (s < NT) && lane_ok && (p < NPe);
+    const int g = g0 - GH + p;                   // cell index along the axis (ghosts < 0 or >= N)
+    const double dt = a.dt_dev ? *a.dt_dev : a.dt;
+    const R dtr = R(dt);
+    const R gam = R(a.gamma);
+
+    // base offset and stride of this lane's pencil
+    long long base, stride;
+    if (DIR == 0) { base = ((long long)iz * a.n[1] + iy) * a.n[0]; stride = 1; }
+    else if (DIR == 1) { base = (long long)iz * a.n[1] * a.n[0] + ix; stride = a.n[0]; }
+    else { base = (long long)iy * a.n[0] + ix; stride = (long long)a.n[0] * a.n[1]; }
+
+    // ---------------- P1: load, ghosts, primitives ----------------
+    double dx = 0.0, pos[3] = {0.0, 0.0, 0.0}, Bdg[3] = {0.0, 0.0, 0.0};
+    R rho = 0, u = 0, v1 = 0, v2 = 0, Bn = 0, B1 = 0, B2 = 0, pr = 0, W = 0, dm = 0, e = 0;
+    R Bd0 = 0, Bd1 = 0, Bd2 = 0;
+    bool floored = false;
+    const bool out_cell = act && p >= GH && p < GH + Ce;
+    if (act) {
+        dx = a.w[g + GH];
+        pos[0] = a.cx[(DIR == 0 ? g : ix) + GH];
+        pos[1] = a.cy[(DIR == 1 ? g : iy) + GH];
+        pos[2] = a.cz[(DIR == 2 ? g : iz) + GH];
+        dipole(a.M, pos[0], pos[1], pos[2], Bdg);
+        double Uc[8];
+        int src = g;
+        bool fixed = false;
+        if (g < 0 || g >= a.N) {
+            int kind = g < 0 ? a.bc_lo : a.bc_hi;
+            if (kind == PPMLR_BC_PERIODIC) src = ((g % a.N) + a.N) % a.N;
+            else if (kind == PPMLR_BC_OUTFLOW) src = g < 0 ? 0 : a.N - 1;
+            else {
+                fixed = true;
+                const double *f = a.inflow;
+                double Bp0 = f[4] - Bdg[0], Bp1 = f[5] - Bdg[1], Bp2 = f[6] - Bdg[2];
+                double rh = f[0];
+                Uc[0] = rh;
+                Uc[1] = rh * f[1]; Uc[2] = rh * f[2]; Uc[3] = rh * f[3];
+                Uc[4] = Bp0; Uc[5] = Bp1; Uc[6] = Bp2;
+                Uc[7] = f[7] / (a.gamma - 1.0) + 0.5 * rh * (f[1] * f[1] + f[2] * f[2] + f[3] * f[3])
+                        + 0.5 * (Bp0 * Bp0 + Bp1 * Bp1 + Bp2 * Bp2);
+            }
+        }
+        if (!fixed) {
+            const long long gi = base + (long long)src * stride;
+#pragma unroll
+            for (int v = 0; v < 8; v++) Uc[v] = __ldg(a.U[v] + gi);
+        }
+        // pressure recovery in double on both paths
+        double rd = Uc[0];
+        double mn = Uc[1 + DIR], m1 = Uc[1 + T1], m2 = Uc[1 + T2];
+        double bn = Uc[4 + DIR], b1 = Uc[4 + T1], b2 = Uc[4 + T2];
+        double E = Uc[7];
+        double prd = (a.gamma - 1.0) * (E - 0.5 * (mn * mn + m1 * m1 + m2 * m2) / rd
+                                        - 0.5 * (bn * bn + b1 * b1 + b2 * b2));
+        if (prd < a.p_min) { prd = a.p_min; floored = out_cell; }
+        Bd0 = R(Bdg[DIR]); Bd1 = R(Bdg[T1]); Bd2 = R(Bdg[T2]);
+        if constexpr (F64) {
+            rho = rd; u = mn / rd; v1 = m1 / rd; v2 = m2 / rd;
+            Bn = bn; B1 = b1; B2 = b2; pr = prd;
+            e = E / rd;
+            dm = rd * dx;
+        } else {
+            rho = float(rd);
+            u = float(mn) / rho; v1 = float(m1) / rho; v2 = float(m2) / rho;
+            Bn = float(bn); B1 = float(b1); B2 = float(b2); pr = float(prd);
+            e = float(E) / rho;
+            dm = rho * float(dx);
+        }
+        R Pt = pr + R(0.5) * (Bn * Bn + B1 * B1 + B2 * B2);
+        W = rho * K<R>::sq(fast2<R>(rho, pr, Bn, B1, B2, gam));
+        SM(A_RHO, s) = rho; SM(A_U, s) = u; SM(A_V1, s) = v1; SM(A_V2, s) = v2;
+        SM(A_B1, s) = B1; SM(A_B2, s) = B2; SM(A_P, s) = pr; SM(A_DM, s) = dm;
+        SM(A_PT, s) = Pt; SM(A_BN, s) = Bn;
+        if (a.do_src) {   // v x B_d in the local frame
+            SM(A_AX, s) = v1 * Bd2 - v2 * Bd1;
+            SM(A_AY, s) = v2 * Bd0 - u * Bd2;
+            SM(A_AZ, s) = u * Bd1 - v1 * Bd0;
+        }
+    }
+    {
+        int nf = __syncthreads_count(floored);
+        if (s == 0 && nf) atomicAdd(a.floors, (unsigned long long)nf);
+    }
+
+    // ---------------- P2: slopes, flattening indicator, sources ----------------
+    R dmv[7];
+    R src_m[3] = {0, 0, 0}, src_b[3] = {0, 0, 0}, src_e = 0;
+    if (act && p >= 1 && p <= NPe - 2) {
+        SlopeCoef<R> k = slope_coef<R>(SM(A_DM, s - PS), dm, SM(A_DM, s + PS));
+        const R own[7] = {rho, u, v1, v2, B1, B2, pr};
+#pragma unroll
+        for (int v = 0; v < 7; v++) {
+            dmv[v] = limit_slope<R>(SM(A_RHO + v, s - PS), own[v], SM(A_RHO + v, s + PS), k.c1, k.c2, k.c3);
+            SM(SB0 + v, s) = dmv[v];
+        }
+        R ft = 0;
+        if (p >= 2 && p <= NPe - 3) {
+            R Pp = SM(A_PT, s + PS), Pm = SM(A_PT, s - PS);
+            R dP = Pp - Pm;
+            R pmin = Pp < Pm ? Pp : Pm;
+            if (K<R>::ab(dP) > R(0.33) * pmin && SM(A_U, s - PS) - SM(A_U, s + PS) > R(0)) {
+                R den = SM(A_PT, s + 2 * PS) - SM(A_PT, s - 2 * PS);
+                R steep = den != R(0) ? dP / den : R(1);
+                R f = (steep - R(0.75)) * R(10);
+                if (f < R(0)) f = R(0);
+                if (f > R(1)) f = R(1);
+                ft = f;
+            }
+        }
+        SM(SB0 + 7, s) = ft;
+        if (a.do_src && out_cell) {
+            R h = R(0.5) * R(a.w[g + GH - 1]) + R(dx) + R(0.5) * R(a.w[g + GH + 1]);
+            R DB0 = (SM(A_BN, s + PS) - SM(A_BN, s - PS)) / h;
+            R DB1 = (SM(A_B1, s + PS) - SM(A_B1, s - PS)) / h;
+            R DB2 = (SM(A_B2, s + PS) - SM(A_B2, s - PS)) / h;
+            R DA1 = (SM(A_AY, s + PS) - SM(A_AY, s - PS)) / h;
+            R DA2 = (SM(A_AZ, s + PS) - SM(A_AZ, s - PS)) / h;
+            R J0 = 0, J1 = -DB2, J2 = DB1;
+            R cA0 = 0, cA1 = -DA2, cA2 = DA1;
+            src_m[0] = J1 * Bd2 - J2 * Bd1;
+            src_m[1] = J2 * Bd0 - J0 * Bd2;
+            src_m[2] = J0 * Bd1 - J1 * Bd0;
+            R divB = DB0;
+            R pw = a.powell ? R(1) : R(0);
+            src_b[0] = cA0 - pw * u * divB;
+            src_b[1] = cA1 - pw * v1 * divB;
+            src_b[2] = cA2 - pw * v2 * divB;
+            src_e = u * src_m[0] + v1 * src_m[1] + v2 * src_m[2] + Bn * cA0 + B1 * cA1 + B2 * cA2;
+        }
+    }
+    __syncthreads();
+
+    // ---------------- P3: interface values, flattening coefficient ----------------
+    R edg[7];
+    R flat = 0;
+    if (act && p >= 1 && p <= NPe - 3) {
+        EdgeCoef<R> k = edge_coef<R>(SM(A_DM, s - PS), dm, SM(A_DM, s + PS), SM(A_DM, s + 2 * PS));
+        const R own[7] = {rho, u, v1, v2, B1, B2, pr};
+#pragma unroll
+        for (int v = 0; v < 7; v++) {
+            edg[v] = edge_value<R>(k, own[v], SM(A_RHO + v, s + PS), dmv[v], SM(SB0 + v, s + PS));
+            SM(SC0 + v, s) = edg[v];
+        }
+        if (p >= 3 && p <= NPe - 4) {
+            R up = SM(A_PT, s + PS) - SM(A_PT, s - PS) < R(0) ? SM(SB0 + 7, s + PS) : SM(SB0 + 7, s - PS);
+            R ft = SM(SB0 + 7, s);
+            flat = ft > up ? ft : up;
+        }
+    }
+    __syncthreads();
+
+    // ---------------- P4: parabolas and characteristic tracing ----------------
+    // left state of interface p+1/2 (this zone, right end): kept in registers;
+    // right state of interface p-1/2 (this zone, left end): to A[0..8] for p-1.
+    R sl[9];
+    if (act && p >= 3 && p <= NPe - 4) {
+        R yf = W * dtr / dm;
+        R ya = K<R>::sq(rho) * K<R>::ab(Bn) * dtr / dm;
+        const R own[7] = {rho, u, v1, v2, B1, B2, pr};
+        R srv[9];
+#pragma unroll
+        for (int v = 0; v < 7; v++) {
+            R lft = flat * own[v] + (R(1) - flat) * SM(SC0 + v, s - PS);
+            R rgt = flat * own[v] + (R(1) - flat) * edg[v];
+            R a6 = monotone<R>(own[v], lft, rgt);
+            R y = (v == 2 || v == 3) ? ya : yf;
+            sl[v] = avg_right<R>(lft, rgt, a6, y);
+            srv[v] = avg_left<R>(lft, rgt, a6, y);
+            if (v == 4 || v == 5) {
+                sl[v + 3] = avg_right<R>(lft, rgt, a6, ya);
+                srv[v + 3] = avg_left<R>(lft, rgt, a6, ya);
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 9; v++) SM(v, s) = srv[v];
+    }
+    __syncthreads();
+
+    // ---------------- P5: Riemann problem at p+1/2 ----------------
+    R rs_u = 0, rs_S = 0, rs_s1 = 0, rs_s2 = 0, rs_b1 = 0, rs_b2 = 0, rs_fe = 0;
+    if (act && p >= 3 && p <= NPe - 5) {
+        R Rs[9];
+#pragma unroll
+        for (int v = 0; v < 9; v++) Rs[v] = SM(v, s + PS);
+        R Bnf = R(0.5) * (Bn + SM(A_BN, s + PS));
+        R PL = sl[6] + R(0.5) * (sl[4] * sl[4] + sl[5] * sl[5]);
+        R PR = Rs[6] + R(0.5) * (Rs[4] * Rs[4] + Rs[5] * Rs[5]);
+        R WL = sl[0] * K<R>::sq(fast2<R>(sl[0], sl[6], Bnf, sl[4], sl[5], gam));
+        R WR = Rs[0] * K<R>::sq(fast2<R>(Rs[0], Rs[6], Bnf, Rs[4], Rs[5], gam));
+        R us = (WL * sl[1] + WR * Rs[1] + PL - PR) / (WL + WR);
+        R Ps = (WR * PL + WL * PR + WL * WR * (sl[1] - Rs[1])) / (WL + WR);
+        R Ss = Ps - R(0.5) * Bnf * Bnf;
+        R ZL = K<R>::sq(sl[0]) * K<R>::ab(Bnf);
+        R ZR = K<R>::sq(Rs[0]) * K<R>::ab(Bnf);
+        R vs[2], ss[2];
+#pragma unroll
+        for (int t = 0; t < 2; t++) {
+            R vL = sl[2 + t], vR = Rs[2 + t];
+            R sL = Bnf * sl[7 + t], sR = Bnf * Rs[7 + t];
+            if (ZL + ZR == R(0)) {
+                vs[t] = R(0.5) * (vL + vR);
+                ss[t] = R(0);
+            } else {
+                vs[t] = (ZL * vL + ZR * vR + sR - sL) / (ZL + ZR);
+                ss[t] = (ZR * sL + ZL * sR + ZL * ZR * (vR - vL)) / (ZL + ZR);
+            }
+        }
+        rs_u = us; rs_S = Ss; rs_s1 = ss[0]; rs_s2 = ss[1];
+        rs_b1 = Bnf * vs[0]; rs_b2 = Bnf * vs[1];
+        rs_fe = Ss * us - ss[0] * vs[0] - ss[1] * vs[1];
+        SM(SC0 + 0, s) = rs_u; SM(SC0 + 1, s) = rs_S; SM(SC0 + 2, s) = rs_s1; SM(SC0 + 3, s) = rs_s2;
+        SM(SC0 + 4, s) = rs_b1; SM(SC0 + 5, s) = rs_b2; SM(SC0 + 6, s) = rs_fe;
+    }
+    __syncthreads();
+
+    // ---------------- P6: Lagrangian update ----------------
+    R dC[6], qL[7], dxL = 0, del_p = 0, del_m = 0;
+    if (act && p >= 4 && p <= NPe - 5) {
+        R lu = SM(SC0 + 0, s - PS), lS = SM(SC0 + 1, s - PS), ls1 = SM(SC0 + 2, s - PS), ls2 = SM(SC0 + 3, s - PS);
+        R lb1 = SM(SC0 + 4, s - PS), lb2 = SM(SC0 + 5, s - PS), lfe = SM(SC0 + 6, s - PS);
+        R dxr = R(dx);
+        dxL = dxr + dtr * (rs_u - lu);
+        if (!(dxL > R(0))) atomicOr(a.flags, FLAG_CFL);
+        R uL = u - dtr * (rs_S - lS) / dm;
+        R v1L = v1 + dtr * (rs_s1 - ls1) / dm;
+        R v2L = v2 + dtr * (rs_s2 - ls2) / dm;
+        R bv1 = dtr * (rs_b1 - lb1);
+        R bv2 = dtr * (rs_b2 - lb2);
+        R B1dx = B1 * dxr + bv1;
+        R B2dx = B2 * dxr + bv2;
+        R eL = e - dtr * (rs_fe - lfe) / dm;
+        R rhoL = dm / dxL;
+        qL[0] = rhoL; qL[1] = rhoL * uL; qL[2] = rhoL * v1L; qL[3] = rhoL * v2L;
+        qL[4] = B1dx / dxL; qL[5] = B2dx / dxL; qL[6] = rhoL * eL;
+        dC[0] = -dtr * (rs_S - lS);
+        dC[1] = dtr * (rs_s1 - ls1);
+        dC[2] = dtr * (rs_s2 - ls2);
+        dC[3] = bv1;
+        dC[4] = bv2;
+        dC[5] = -dtr * (rs_fe - lfe);
+        del_p = dtr * rs_u;
+        del_m = dtr * lu;
+#pragma unroll
+        for (int v = 0; v < 7; v++) SM(SB0 + v, s) = qL[v];
+        SM(SB0 + 7, s) = dxL;
+    }
+    __syncthreads();
+
+    // ---------------- P7: remap slopes ----------------
+    R rmv[7];
+    if (act && p >= 5 && p <= NPe - 6) {
+        SlopeCoef<R> k = slope_coef<R>(SM(SB0 + 7, s - PS), dxL, SM(SB0 + 7, s + PS));
+#pragma unroll
+        for (int v = 0; v < 7; v++) {
+            rmv[v] = limit_slope<R>(SM(SB0 + v, s - PS), qL[v], SM(SB0 + v, s + PS), k.c1, k.c2, k.c3);
+            SM(v, s) = rmv[v];
+        }
+    }
+    __syncthreads();
+
+    // ---------------- P8: remap interface values ----------------
+    R red[7];
+    if (act && p >= 5 && p <= NPe - 7) {
+        EdgeCoef<R> k = edge_coef<R>(SM(SB0 + 7, s - PS), dxL, SM(SB0 + 7, s + PS), SM(SB0 + 7, s + 2 * PS));
+#pragma unroll
+        for (int v = 0; v < 7; v++) {
+            red[v] = edge_value<R>(k, qL[v], SM(SB0 + v, s + PS), rmv[v], SM(v, s + PS));
+            SM(SC0 + v, s) = red[v];
+        }
+    }
+    __syncthreads();
+
+    // ---------------- P9: remap parabolas and donor fluxes ----------------
+    if (act && p >= 6 && p <= NPe - 7) {
+        R pl[7], pr_[7], p6[7];
+#pragma unroll
+        for (int v = 0; v < 7; v++) {
+            pl[v] = SM(SC0 + v, s - PS);
+            pr_[v] = red[v];
+            p6[v] = monotone<R>(qL[v], pl[v], pr_[v]);
+        }
+        if (p <= NPe - 8) {                       // edge p+1/2: donor is this zone when del >= 0
+            if (del_p > R(0)) {
+                R y = del_p / dxL;
+                if (y >= R(1)) atomicOr(a.flags, FLAG_CFL);
+#pragma unroll
+                for (int v = 0; v < 7; v++) SM(SB0 + v, s) = del_p * avg_right<R>(pl[v], pr_[v], p6[v], y);
+            } else if (!(del_p < R(0))) {
+#pragma unroll
+                for (int v = 0; v < 7; v++) SM(SB0 + v, s) = R(0);
+            }
+        }
+        if (p >= 7 && del_m < R(0)) {             // edge p-1/2: donor is this zone when del < 0
+            R y = -del_m / dxL;
+            if (y >= R(1)) atomicOr(a.flags, FLAG_CFL);
+#pragma unroll
+            for (int v = 0; v < 7; v++) SM(SB0 + v, s - PS) = del_m * avg_left<R>(pl[v], pr_[v], p6[v], y);
+        }
+    }
+    __syncthreads();
+
+    // ---------------- P10: new state, sources, inner sphere, store ----------------
+    if (out_cell) {
+        const long long gi = base + (long long)g * stride;
+        double Un[8];
+#pragma unroll
+        for (int v = 0; v < 8; v++) Un[v] = __ldg(a.U[v] + gi);
+        const int cmap[7] = {0, 1 + DIR, 1 + T1, 1 + T2, 4 + T1, 4 + T2, 7};
+        const R dCv[7] = {R(0), dC[0], dC[1], dC[2], dC[3], dC[4], dC[5]};
+        if constexpr (F64) {
+#pragma unroll
+            for (int v = 0; v < 7; v++) {
+                double dU = (dCv[v] + SM(SB0 + v, s - PS) - SM(SB0 + v, s)) / dx;
+                Un[cmap[v]] = Un[cmap[v]] + dU;
+            }
+            if (a.do_src) {
+                const int mi[3] = {1 + DIR, 1 + T1, 1 + T2}, bi[3] = {4 + DIR, 4 + T1, 4 + T2};
+#pragma unroll
+                for (int m = 0; m < 3; m++) {
+                    Un[mi[m]] = Un[mi[m]] + dt * src_m[m];
+                    Un[bi[m]] = Un[bi[m]] + dt * src_b[m];
+                }
+                Un[7] = Un[7] + dt * src_e;
+            }
+        } else {
+            const R dxr = R(dx);
+            R dU[8];
+#pragma unroll
+            for (int v = 0; v < 7; v++) dU[cmap[v]] = (dCv[v] + SM(SB0 + v, s - PS) - SM(SB0 + v, s)) / dxr;
+            dU[4 + DIR] = R(0);
+            if (a.do_src) {
+                dU[1 + DIR] += dtr * src_m[0]; dU[1 + T1] += dtr * src_m[1]; dU[1 + T2] += dtr * src_m[2];
+                dU[4 + DIR] += dtr * src_b[0]; dU[4 + T1] += dtr * src_b[1]; dU[4 + T2] += dtr * src_b[2];
+                dU[7] += dtr * src_e;
+            }
+#pragma unroll
+            for (int v = 0; v < 8; v++) Un[v] = Un[v] + double(dU[v]);
+        }
+        if (a.r_inner > 0.0 &&
+            pos[0] * pos[0] + pos[1] * pos[1] + pos[2] * pos[2] < a.r_inner * a.r_inner) {
+            const double *q = a.inner;
+            double rh = q[0];
+            Un[0] = rh;
+            Un[1] = rh * q[1]; Un[2] = rh * q[2]; Un[3] = rh * q[3];
+            Un[4] = 0.0; Un[5] = 0.0; Un[6] = 0.0;
+            Un[7] = q[7] / (a.gamma - 1.0) + 0.5 * rh * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3])
+                    + 0.5 * (0.0 * 0.0 + 0.0 * 0.0 + 0.0 * 0.0);
+        }
+        bool bad = false;
+#pragma unroll
+        for (int v = 0; v < 8; v++) {
+            bad |= !isfinite(Un[v]);
+            a.Un[v][gi] = Un[v];
+        }
+        if (bad) atomicOr(a.flags, FLAG_NONFINITE);
+    }
+#undef SM
+}
+
+}  // namespace ppmlr

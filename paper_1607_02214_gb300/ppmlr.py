@@ -1,0 +1,242 @@
+"""ctypes binding of the C ABI in include/ppmlr.h (argument marshalling only).
+
+Every function of the ABI is exposed under its own name; ``Context`` bundles
+them for torch tensors and numpy arrays.  All arithmetic runs in the CUDA
+library libppmlr_gb300.so; there is no CPU fallback: loading fails loudly if
+the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_longlong, c_void_p
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libppmlr_gb300.so")
+
+PPMLR_OK, PPMLR_E_INVALID, PPMLR_E_CUDA, PPMLR_E_OOM, PPMLR_E_NONFINITE, PPMLR_E_CFL, PPMLR_E_TIMEOUT = range(7)
+PPMLR_FP64, PPMLR_MIXED = 0, 1
+PPMLR_BC_PERIODIC, PPMLR_BC_OUTFLOW, PPMLR_BC_INFLOW = 0, 1, 2
+STATUS_NAMES = {0: "PPMLR_OK", 1: "PPMLR_E_INVALID", 2: "PPMLR_E_CUDA", 3: "PPMLR_E_OOM",
+                4: "PPMLR_E_NONFINITE", 5: "PPMLR_E_CFL", 6: "PPMLR_E_TIMEOUT"}
+
+
+class ppmlr_grid(ctypes.Structure):
+    _fields_ = [("n", c_int * 3), ("edges", POINTER(c_double) * 3)]
+
+
+class ppmlr_prim(ctypes.Structure):
+    _fields_ = [("rho", c_double), ("v", c_double * 3), ("B", c_double * 3), ("p", c_double)]
+
+
+class ppmlr_bc(ctypes.Structure):
+    _fields_ = [("face", (c_int * 2) * 3), ("inflow", ppmlr_prim), ("dipole_moment", c_double),
+                ("r_inner", c_double), ("inner", ppmlr_prim), ("p_min", c_double), ("powell", c_int)]
+
+
+DPTR8 = POINTER(c_double) * 8
+
+# (name, restype, argtypes) of every exported function
+SIGNATURES = [
+    ("ppmlr_create", c_int, [POINTER(ppmlr_grid), c_double, POINTER(ppmlr_bc), c_int, c_void_p, POINTER(c_void_p)]),
+    ("ppmlr_set_stream", c_int, [c_void_p, c_void_p]),
+    ("ppmlr_set_state", c_int, [c_void_p, DPTR8, c_int]),
+    ("ppmlr_get_state", c_int, [c_void_p, DPTR8, c_int]),
+    ("ppmlr_cfl_dt", c_int, [c_void_p, c_double, POINTER(c_double)]),
+    ("ppmlr_step", c_int, [c_void_p, c_double]),
+    ("ppmlr_step_cfl", c_int, [c_void_p, c_double, c_int]),
+    ("ppmlr_sweep", c_int, [c_void_p, c_int, c_double]),
+    ("ppmlr_check", c_int, [c_void_p]),
+    ("ppmlr_get_diagnostics", c_int, [c_void_p, POINTER(c_longlong), POINTER(c_longlong), POINTER(c_int)]),
+    ("ppmlr_set_step_count", c_int, [c_void_p, c_longlong]),
+    ("ppmlr_get_dt", c_int, [c_void_p, POINTER(c_double)]),
+    ("ppmlr_last_error", ctypes.c_char_p, [c_void_p]),
+    ("ppmlr_destroy", None, [c_void_p]),
+    ("ppmlr_launch_count", c_longlong, [c_void_p]),
+]
+
+_lib = None
+
+
+def load():
+    """Load libppmlr_gb300.so (raises if it is missing: no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def __getattr__(name):          # module-level access to the raw ABI functions
+    if name.startswith("ppmlr_"):
+        return getattr(load(), name)
+    raise AttributeError(name)
+
+
+class PPMLRError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _prim(vals):
+    p = ppmlr_prim()
+    p.rho = vals[0]
+    for k in range(3):
+        p.v[k] = vals[1 + k]
+        p.B[k] = vals[4 + k]
+    p.p = vals[7]
+    return p
+
+
+def make_bc(spec) -> ppmlr_bc:
+    """ppmlr_bc from an inputs.BoundarySpec-like object."""
+    bc = ppmlr_bc()
+    for d in range(3):
+        for s in range(2):
+            bc.face[d][s] = int(spec.face[d][s])
+    bc.inflow = _prim(spec.inflow)
+    bc.dipole_moment = float(spec.dipole_moment)
+    bc.r_inner = float(spec.r_inner)
+    bc.inner = _prim(spec.inner)
+    bc.p_min = float(spec.p_min)
+    bc.powell = int(spec.powell)
+    return bc
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return c_void_p(stream)
+    return c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """One grid + boundary spec + state on the current CUDA device."""
+
+    def __init__(self, edges, gamma, bc_spec, precision=PPMLR_FP64, stream=None):
+        L = load()
+        self._edges = [np.ascontiguousarray(e, dtype=np.float64) for e in edges]
+        self.n = tuple(len(e) - 1 for e in self._edges)
+        g = ppmlr_grid()
+        for d in range(3):
+            g.n[d] = self.n[d]
+            g.edges[d] = self._edges[d].ctypes.data_as(POINTER(c_double))
+        self._bc = make_bc(bc_spec)
+        h = c_void_p()
+        st = L.ppmlr_create(ctypes.byref(g), float(gamma), ctypes.byref(self._bc), int(precision),
+                            _stream_handle(stream), ctypes.byref(h))
+        if st != PPMLR_OK:
+            raise PPMLRError(st, "ppmlr_create failed")
+        self._h = h
+        self.precision = precision
+
+    @classmethod
+    def from_problem(cls, prob, precision=PPMLR_FP64, stream=None):
+        return cls(prob.edges, prob.gamma, prob.bc, precision, stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ppmlr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (8, self.n[2], self.n[1], self.n[0])
+
+    def _check(self, st):
+        if st != PPMLR_OK:
+            raise PPMLRError(st, load().ppmlr_last_error(self._h).decode())
+        return st
+
+    def status(self, st):
+        """Return the status code without raising."""
+        return st
+
+    @staticmethod
+    def _ptrs(arr):
+        arr8 = DPTR8()
+        if hasattr(arr, "data_ptr"):
+            assert arr.is_contiguous() and arr.dtype.__str__() == "torch.float64"
+            step = arr[0].numel() * 8
+            base = arr.data_ptr()
+            for v in range(8):
+                arr8[v] = ctypes.cast(c_void_p(base + v * step), POINTER(c_double))
+            return arr8, 1
+        assert arr.flags["C_CONTIGUOUS"] and arr.dtype == np.float64
+        for v in range(8):
+            arr8[v] = arr[v].ctypes.data_as(POINTER(c_double))
+        return arr8, 0
+
+    def set_state(self, U, raise_on_error=True):
+        if not hasattr(U, "data_ptr"):
+            U = np.ascontiguousarray(U, dtype=np.float64)
+        assert tuple(U.shape) == self.shape
+        p, dev = self._ptrs(U)
+        st = load().ppmlr_set_state(self._h, p, dev)
+        return self._check(st) if raise_on_error else st
+
+    def get_state(self, out=None, raise_on_error=True):
+        if out is None:
+            out = np.empty(self.shape, dtype=np.float64)
+        p, dev = self._ptrs(out)
+        st = load().ppmlr_get_state(self._h, p, dev)
+        if raise_on_error:
+            self._check(st)
+            return out
+        return out, st
+
+    def cfl_dt(self, cfl):
+        dt = c_double()
+        self._check(load().ppmlr_cfl_dt(self._h, float(cfl), ctypes.byref(dt)))
+        return dt.value
+
+    def step(self, dt, raise_on_error=True):
+        st = load().ppmlr_step(self._h, float(dt))
+        return self._check(st) if raise_on_error else st
+
+    def step_cfl(self, cfl, nsteps=1):
+        return self._check(load().ppmlr_step_cfl(self._h, float(cfl), int(nsteps)))
+
+    def sweep(self, axis, dt):
+        return self._check(load().ppmlr_sweep(self._h, int(axis), float(dt)))
+
+    def check(self, raise_on_error=True):
+        st = load().ppmlr_check(self._h)
+        return self._check(st) if raise_on_error else st
+
+    def diagnostics(self):
+        s, f, o = c_longlong(), c_longlong(), c_int()
+        self._check(load().ppmlr_get_diagnostics(self._h, ctypes.byref(s), ctypes.byref(f), ctypes.byref(o)))
+        return {"step": s.value, "floor_hits": f.value, "order_parity": o.value}
+
+    def set_step_count(self, step):
+        return self._check(load().ppmlr_set_step_count(self._h, int(step)))
+
+    def last_dt(self):
+        dt = c_double()
+        self._check(load().ppmlr_get_dt(self._h, ctypes.byref(dt)))
+        return dt.value
+
+    @property
+    def launch_count(self):
+        return load().ppmlr_launch_count(self._h)
+
+    def set_stream(self, stream):
+        return self._check(load().ppmlr_set_stream(self._h, _stream_handle(stream)))

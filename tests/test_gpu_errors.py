@@ -1,0 +1,46 @@
+"""Failure detection, made on the host: a NaN written into the state, a time
+step far above the CFL limit, invalid arguments.  The kernels raise flags that
+the next synchronising call reports; nothing traps or hangs."""
+import numpy as np
+import pytest
+
+from gpu_util import make_gpu
+from paper_1607_02214_gb300 import inputs, ppmlr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1607_02214_gb300 import build
+    build.build()
+
+
+def test_nonfinite_state_reported():
+    pr = inputs.brio_wu_3d((16, 8, 8))
+    U = pr.U0.copy()
+    U[7, 3, 4, 5] = np.nan
+    g = ppmlr.Context.from_problem(pr)
+    g.set_state(U)
+    g.step(1e-3)
+    assert g.check(raise_on_error=False) == ppmlr.PPMLR_E_NONFINITE
+    assert g.check(raise_on_error=False) == ppmlr.PPMLR_OK          # reported once
+
+
+def test_cfl_violation_reported():
+    pr = inputs.brio_wu_3d((16, 8, 8))
+    g = make_gpu(pr)
+    dt = g.cfl_dt(0.4)
+    g.step(40 * dt)
+    assert g.check(raise_on_error=False) in (ppmlr.PPMLR_E_CFL, ppmlr.PPMLR_E_NONFINITE)
+
+
+def test_invalid_arguments():
+    pr = inputs.brio_wu_3d((16, 8, 8))
+    g = make_gpu(pr)
+    assert g.step(-1.0, raise_on_error=False) == ppmlr.PPMLR_E_INVALID
+    assert g.step(float("nan"), raise_on_error=False) == ppmlr.PPMLR_E_INVALID
+    with pytest.raises(ppmlr.PPMLRError):
+        g.sweep(3, 1e-3)
+    with pytest.raises(ppmlr.PPMLRError):
+        g.step_cfl(-0.4, 1)
