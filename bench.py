@@ -1,0 +1,402 @@
+"""Benchmark: cell-updates/s of full x/y/z steps of the split PPMLR-MHD sweep.
+
+Default workload: the magnetosphere-shaped stretched grid 256x192x192
+(x in [-100, 30] R_E, y, z in [-60, 60] R_E, finest 0.4 R_E), Earth dipole,
+inner sphere r = 3 R_E, solar-wind inflow at x = +30 R_E (n = 5 cm^-3,
+vx = -400 km/s, T = 1e5 K, IMF Bz = -5 nT), outflow elsewhere, FP64, CFL 0.4.
+A step is the device CFL reduction plus the three sweeps; the state (604 MB)
+is larger than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line on rank 0.  With N > 1 (torchrun, one process per GPU)
+every rank advances its own replica of the workload: the method has no
+exchange step between independent domains here ("replicas only", weak
+scaling), so there is no data-path collective; ranks meet only at the timing
+barriers and the max-over-ranks reduction.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per full xyz step"
+UNIT = "cell-updates/s"
+HBM_FALLBACK_GBS = 6800.0
+# FP64 pipe throughput of a GB300 measured with a dependent-free DFMA/DADD/DMUL
+# loop over all 152 SMs: 502 G instructions/s (each a +, -, x or FMA).  The FP64
+# sweeps compile without contraction, so one algorithmic flop is one pipe op;
+# a division or square root occupies the pipe for ~6 and ~9 ops.
+FP64_PIPE_GOPS = 502.4
+# Algorithmic FP64 flops (+, -, x, /, sqrt) per interior cell of one sweep on
+# the magnetosphere workload (PPM coefficients counted once per zone), counted
+# by an instrumented build of the reference; and per cell of the CFL pass.
+FLOPS_PER_CELL = {"x": 1189.1, "y": 1241.9, "z": 1243.7, "cfl": 208.0}
+BYTES_PER_CELL_SWEEP = 128      # read 8 FP64 + write 8 FP64
+# DRAM bytes per cell of one launch measured by ncu for each kernel, with the
+# sha256 prefix of the kernel source they were taken on (null once it changes).
+NCU_TRAFFIC = {
+    "fp64:x": {"bytes_per_cell": 123.8, "src": "52c7ac4d69c1abd8"},
+    "fp64:y": {"bytes_per_cell": 123.8, "src": "52c7ac4d69c1abd8"},
+    "fp64:z": {"bytes_per_cell": 124.4, "src": "52c7ac4d69c1abd8"},
+    "mixed:x": {"bytes_per_cell": 123.0, "src": "52c7ac4d69c1abd8"},
+    "mixed:y": {"bytes_per_cell": 123.3, "src": "52c7ac4d69c1abd8"},
+    "mixed:z": {"bytes_per_cell": 124.1, "src": "52c7ac4d69c1abd8"},
+}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("sweep.cuh", "sweep_fp64.cu", "sweep_mixed.cu", "cfl.cu"):
+        with open(os.path.join(ROOT, "paper_1607_02214_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------- clocks ------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.samples = []
+        self.proc = None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            sel = ["-i", uuid if uuid.startswith("GPU-") else "GPU-" + uuid]
+        except Exception:
+            sel = ["-i", str(device_index)]
+        self.cmd = ["nvidia-smi", *sel, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[4 + k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------- workloads ------
+
+def workload(args):
+    from paper_1607_02214_gb300 import inputs
+    n = tuple(args.grid)
+    h0 = 0.4 * 256 / n[0] if args.h0 is None else args.h0
+    prob = inputs.magnetosphere(n=n, h0=h0)
+    name = f"magnetosphere_{n[0]}x{n[1]}x{n[2]}_h0_{h0:g}_{args.precision}"
+    return prob, name
+
+
+def config_dict(prob, name, args, world):
+    return {"workload": name, "grid": list(prob.n), "cells": prob.cells, "cfl": prob.cfl,
+            "x_range_re": [-100, 30], "yz_range_re": [-60, 60], "dipole": True, "r_inner_re": 3.0,
+            "inflow": "n=5 cm^-3, vx=-400 km/s, T=1e5 K, Bz=-5 nT", "precision": args.precision,
+            "l2": "state 604 MB per copy > 129 MB L2: inputs larger than L2, no flush",
+            "parallelism": f"replicas x{world}"}
+
+
+# ------------------------------------------------------------ reference -------
+
+def oracle_sample(prob, steps, threads=0):
+    """Time the oracle on the host cores: `steps` steps of prob with its CFL dt."""
+    import oracle
+    cores = oracle.set_threads(threads)
+    bc = prob.bc
+    o = oracle.Oracle(prob.edges, prob.gamma, bc.flat_faces(), inflow=bc.inflow, dipole_moment=bc.dipole_moment,
+                      r_inner=bc.r_inner, inner=bc.inner, p_min=bc.p_min, powell=bc.powell)
+    o.set_state(prob.U0)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.step(o.cfl_dt(prob.cfl))
+    t = time.perf_counter() - t0
+    return prob.cells * steps / t, t, cores
+
+
+def run_reference(args, rank, world):
+    """The oracle, as it stands, timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return None
+    from paper_1607_02214_gb300 import inputs
+    prob, name = workload(args)
+    # one step of the full grid per timed step when it fits the time budget,
+    # else the same workload at half resolution per axis (same extent)
+    small = inputs.magnetosphere(n=(64, 48, 48), h0=1.6)
+    rate_small, _, _ = oracle_sample(small, 1)
+    est = (args.steps + args.warmup) * prob.cells / rate_small
+    sample_prob, sample_desc = prob, f"one full step of {name} per timed step"
+    if est > 150.0:
+        n2 = tuple(max(16, k // 2) for k in prob.n)
+        sample_prob = inputs.magnetosphere(n=n2, h0=0.4 * 256 / n2[0] * (prob.n[0] / 256))
+        sample_desc = f"one step of the same workload at {n2[0]}x{n2[1]}x{n2[2]} per timed step"
+    import oracle
+    cores = oracle.set_threads(0)
+    bc = sample_prob.bc
+    o = oracle.Oracle(sample_prob.edges, sample_prob.gamma, bc.flat_faces(), inflow=bc.inflow,
+                      dipole_moment=bc.dipole_moment, r_inner=bc.r_inner, inner=bc.inner, p_min=bc.p_min,
+                      powell=bc.powell)
+    o.set_state(sample_prob.U0)
+    for _ in range(args.warmup):
+        o.step(o.cfl_dt(sample_prob.cfl))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(o.cfl_dt(sample_prob.cfl))
+    t = time.perf_counter() - t0
+    value = sample_prob.cells * args.steps / t
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": config_dict(prob, name, args, world),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample_desc},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return out
+
+
+# ------------------------------------------------------------------ ours ------
+
+def run_ours(args, rank, world, dist):
+    import torch
+    from paper_1607_02214_gb300 import build, ppmlr
+
+    build.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    prob, name = workload(args)
+    prec = ppmlr.PPMLR_FP64 if args.precision == "fp64" else ppmlr.PPMLR_MIXED
+    cells = prob.cells
+    U0 = torch.from_numpy(prob.U0).cuda()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed_run(precision, steps, warmup, with_clocks=False):
+        ctx = ppmlr.Context.from_problem(prob, precision)
+        ctx.set_state(U0)
+        ctx.step_cfl(prob.cfl, warmup)
+        ctx.check()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        n0 = ctx.launch_count
+        ctx.enable_timing(True)
+        sampler = ClockSampler(local) if with_clocks else None
+        if sampler:
+            sampler.__enter__()
+            time.sleep(0.3)
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.step_cfl(prob.cfl, 1)
+        e1.record(stream)
+        e1.synchronize()
+        barrier()
+        if sampler:
+            sampler.__exit__(None, None, None)
+        ms = e0.elapsed_time(e1)
+        kern = ctx.read_timing()
+        launches = ctx.launch_count - n0
+        ctx.enable_timing(False)
+        ctx.check()
+        return ctx, ms, kern, launches, (sampler.summary() if sampler else None)
+
+    # ---- main measurement
+    ctx, ms, kern, launches, clocks = timed_run(prec, args.steps, args.warmup, with_clocks=True)
+    ms = max_over_ranks(ms)
+    value = world * cells * args.steps / (ms * 1e-3)
+    log(f"[bench] {name}: {ms / args.steps:.3f} ms/step, {value:.4e} cell-updates/s, kernels {kern}")
+
+    # ---- roofline of the dominant kernel (largest total time)
+    dom = max(kern, key=lambda k: kern[k][0])
+    avg_ms = kern[dom][0] / max(kern[dom][1], 1)
+    traffic = None
+    src_hash = kernel_source_hash()
+    tr = NCU_TRAFFIC.get(f"{args.precision}:{dom}")
+    if tr and tr["src"] == src_hash:
+        traffic = tr["bytes_per_cell"] * cells
+    if args.precision == "fp64":
+        ach = FLOPS_PER_CELL[dom] * cells / (avg_ms * 1e-3) / 1e9
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PIPE_GOPS, "unit": "GFLOP/s",
+                "frac": ach / FP64_PIPE_GOPS, "traffic": traffic, "kernel": f"sweep_{dom}" if dom != "cfl" else "cfl",
+                "avg_launch_ms": avg_ms,
+                "peak_source": "measured FP64 pipe rate (DFMA/DADD/DMUL loop, 152 SMs)"}
+    else:
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                hbm, src = float(json.load(f)["hbm_gbs"]), "measured"
+        except Exception:
+            hbm, src = HBM_FALLBACK_GBS, "fallback"
+        ach = BYTES_PER_CELL_SWEEP * cells / (avg_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": traffic, "kernel": f"sweep_{dom}", "avg_launch_ms": avg_ms, "peak_source": src}
+    per_kernel = {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1],
+                      "hbm_frac_of_measured": BYTES_PER_CELL_SWEEP * cells / (v[0] / max(v[1], 1) * 1e-3) / 1e9 / 6787.2
+                      if k != "cfl" else None} for k, v in kern.items()}
+
+    # ---- the other precision, and its error against the FP64 path
+    extra = {}
+    if not args.quick:
+        other = ppmlr.PPMLR_MIXED if prec == ppmlr.PPMLR_FP64 else ppmlr.PPMLR_FP64
+        octx, oms, okern, _, _ = timed_run(other, args.steps, args.warmup)
+        oms = max_over_ranks(oms)
+        ovalue = world * cells * args.steps / (oms * 1e-3)
+        # accuracy: both precisions from the same state with the FP64 path's dt
+        a = ppmlr.Context.from_problem(prob, ppmlr.PPMLR_FP64)
+        b = ppmlr.Context.from_problem(prob, ppmlr.PPMLR_MIXED)
+        a.set_state(U0)
+        b.set_state(U0)
+        for _ in range(args.accuracy_steps):
+            dt = a.cfl_dt(prob.cfl)
+            a.step(dt)
+            b.step(dt)
+        ua, ub = torch.empty_like(U0), torch.empty_like(U0)
+        a.get_state(ua)
+        b.get_state(ub)
+        diff = (ub - ua).abs().reshape(8, -1)
+        ref = ua.abs().reshape(8, -1).sum(dim=1)
+        grp = torch.stack([ref[0], ref[1:4].sum(), ref[1:4].sum(), ref[1:4].sum(), ref[4:7].sum(), ref[4:7].sum(),
+                           ref[4:7].sum(), ref[7]])
+        l1 = (diff.sum(dim=1) / grp).cpu().tolist()
+        linf = diff.max(dim=1).values.cpu().tolist()
+        names = ["rho", "mx", "my", "mz", "Bx", "By", "Bz", "E"]
+        key = "mixed" if other == ppmlr.PPMLR_MIXED else "fp64"
+        extra[key] = {"value": ovalue, "ms_per_step": oms / args.steps,
+                      "speedup_vs_fp64": (ovalue / value) if key == "mixed" else (value / ovalue),
+                      "kernels_avg_ms": {k: v[0] / max(v[1], 1) for k, v in okern.items()},
+                      "error_vs_fp64": {"steps": args.accuracy_steps,
+                                        "rel_l1": dict(zip(names, l1)), "linf": dict(zip(names, linf))}}
+        del a, b, octx, ua, ub
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.quick:
+        host_in = torch.from_numpy(prob.U0).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        ectx = ppmlr.Context.from_problem(prob, prec)
+        hin, hout = host_in.numpy(), host_out.numpy()
+        ectx.set_state(hin)
+        ectx.step_cfl(prob.cfl, 1)
+        ectx.get_state(hout)
+        ksteps = max(2, min(args.steps, 5))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ksteps):
+            ectx.set_state(hin)            # host -> device, pinned, synchronous
+            ectx.step_cfl(prob.cfl, 1)
+            ectx.get_state(hout)           # device -> host, synchronises
+        barrier()
+        t = max_over_ranks(time.perf_counter() - t0)
+        nbytes = 8 * 8 * cells
+        e2e = {"value": world * cells * ksteps / t, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": ksteps}
+        del ectx
+
+    # ---- CPU baseline: the oracle on this host's cores, bounded sample
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from paper_1607_02214_gb300 import inputs
+        small = inputs.magnetosphere(n=(64, 48, 48), h0=1.6)
+        r_small, _, _ = oracle_sample(small, 1)
+        steps = max(1, min(3, int(20.0 * r_small / cells)))
+        rate, t, cores = oracle_sample(prob, steps)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{steps} full step(s) of {name}, OpenMP over pencils, {t:.1f} s"}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config_dict(prob, name, args, world), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+           "clocks": clocks, "gpu_launches": launches, "kernels": per_kernel, "kernel_src": src_hash}
+    out.update(extra)
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--grid", type=int, nargs=3, default=[256, 192, 192])
+    ap.add_argument("--h0", type=float, default=None)
+    ap.add_argument("--accuracy-steps", type=int, default=50)
+    ap.add_argument("--quick", action="store_true", help="main measurement only")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("[bench] warm-up raised to 3 steps")
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as tdist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group(backend)
+        dist = tdist
+
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, dist)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -160,6 +160,15 @@ void ppmlr_destroy(ppmlr_ctx *ctx);
 /* Kernel launches issued by this context so far (all kinds). */
 long long ppmlr_launch_count(const ppmlr_ctx *ctx);
 
+/* Per-kernel timing.  While enabled, CUDA events are recorded on the context
+ * stream immediately before and after every kernel the context launches
+ * (no synchronisation is added).  ppmlr_read_timing synchronises, returns the
+ * summed device time in milliseconds and the launch count per kind since the
+ * last read, and clears the records.  Kinds: 0, 1, 2 = x, y, z sweep;
+ * 3 = CFL reduction.  total_ms and launches point to 4 entries each. */
+ppmlr_status ppmlr_enable_timing(ppmlr_ctx *ctx, int on);
+ppmlr_status ppmlr_read_timing(ppmlr_ctx *ctx, double *total_ms, long long *launches);
+
 #ifdef __cplusplus
 }
 #endif

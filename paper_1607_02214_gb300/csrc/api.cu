@@ -37,7 +37,39 @@ struct ppmlr_ctx {
     long long steps;
     long long launches;
     std::string err;
+    // per-kernel timing records (kind, start, stop) and a pool of spare events
+    bool timing;
+    struct Rec { int kind; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
 };
+
+static cudaEvent_t take_event(ppmlr_ctx *c)
+{
+    if (!c->pool.empty()) { cudaEvent_t e = c->pool.back(); c->pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Records the start event of a timed launch; returns the record index or -1.
+static int timing_begin(ppmlr_ctx *c, int kind)
+{
+    if (!c->timing) return -1;
+    ppmlr_ctx::Rec r{kind, take_event(c), take_event(c)};
+    if (!r.a || !r.b || cudaEventRecord(r.a, c->stream) != cudaSuccess) {
+        if (r.a) c->pool.push_back(r.a);
+        if (r.b) c->pool.push_back(r.b);
+        return -1;
+    }
+    c->recs.push_back(r);
+    return (int)c->recs.size() - 1;
+}
+
+static void timing_end(ppmlr_ctx *c, int idx)
+{
+    if (idx >= 0) cudaEventRecord(c->recs[idx].b, c->stream);
+}
 
 static const char *k_null_ctx = "null context";
 
@@ -160,6 +192,7 @@ ppmlr_status ppmlr_create(const ppmlr_grid *grid, double gamma, const ppmlr_bc *
     c->stream = (cudaStream_t)cuda_stream;
     c->steps = 0;
     c->launches = 0;
+    c->timing = false;
     if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return PPMLR_E_CUDA; }
 
     // state: 16 arrays, each padded to 256-byte multiples
@@ -207,6 +240,8 @@ void ppmlr_destroy(ppmlr_ctx *c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    for (auto &r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : c->pool) cudaEventDestroy(e);
     cudaFree(c->geo);
     cudaFree(c->state);
     delete c;
@@ -293,8 +328,10 @@ static ppmlr_status launch_one_sweep(ppmlr_ctx *c, int d, double dt, const doubl
     a.do_src = (a.M != 0.0 || a.powell) ? 1 : 0;
     a.dt = dt; a.dt_dev = dt_dev;
     a.flags = c->flags; a.floors = c->floors;
+    int rec = timing_begin(c, d);
     cudaError_t e = c->prec == PPMLR_FP64 ? launch_sweep_fp64(d, a, t, c->stream)
                                           : launch_sweep_mixed(d, a, t, c->stream);
+    timing_end(c, rec);
     if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
     c->launches++;
     for (int v = 0; v < 8; v++) { double *tmp = c->U[v]; c->U[v] = c->Un[v]; c->Un[v] = tmp; }
@@ -337,7 +374,9 @@ static ppmlr_status launch_cfl_kernel(ppmlr_ctx *c, double cfl)
     a.gamma = c->gamma; a.p_min = c->bc.p_min; a.M = c->bc.dipole_moment; a.r_inner = c->bc.r_inner;
     a.cfl = cfl;
     a.partial = c->partial; a.counter = c->counter; a.dt_out = c->dt_dev;
+    int rec = timing_begin(c, 3);
     cudaError_t e = launch_cfl(a, c->cfl_blocks, c->stream);
+    timing_end(c, rec);
     if (e != cudaSuccess) return cuda_fail(c, e, "cfl launch");
     c->launches++;
     return PPMLR_OK;
@@ -384,6 +423,32 @@ ppmlr_status ppmlr_get_diagnostics(ppmlr_ctx *c, long long *step, long long *flo
     if (step) *step = c->steps;
     if (floor_hits) *floor_hits = (long long)fl;
     if (order_parity) *order_parity = (int)(c->steps & 1);
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_enable_timing(ppmlr_ctx *c, int on)
+{
+    if (!c) return PPMLR_E_INVALID;
+    c->timing = on != 0;
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_read_timing(ppmlr_ctx *c, double *total_ms, long long *launches)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (!total_ms || !launches) return fail(c, PPMLR_E_INVALID, "read_timing: null output");
+    for (int k = 0; k < 4; k++) { total_ms[k] = 0.0; launches[k] = 0; }
+    CK(c, cudaStreamSynchronize(c->stream), "stream sync");
+    for (auto &r : c->recs) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            total_ms[r.kind] += ms;
+            launches[r.kind] += 1;
+        }
+        c->pool.push_back(r.a);
+        c->pool.push_back(r.b);
+    }
+    c->recs.clear();
     return PPMLR_OK;
 }
 

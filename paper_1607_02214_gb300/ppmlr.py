@@ -55,6 +55,8 @@ SIGNATURES = [
     ("ppmlr_last_error", ctypes.c_char_p, [c_void_p]),
     ("ppmlr_destroy", None, [c_void_p]),
     ("ppmlr_launch_count", c_longlong, [c_void_p]),
+    ("ppmlr_enable_timing", c_int, [c_void_p, c_int]),
+    ("ppmlr_read_timing", c_int, [c_void_p, POINTER(c_double), POINTER(c_longlong)]),
 ]
 
 _lib = None
@@ -237,6 +239,16 @@ class Context:
     @property
     def launch_count(self):
         return load().ppmlr_launch_count(self._h)
+
+    def enable_timing(self, on=True):
+        return self._check(load().ppmlr_enable_timing(self._h, int(bool(on))))
+
+    def read_timing(self):
+        """{kind: (total_ms, launches)} for kinds x, y, z, cfl since the last read."""
+        ms = (c_double * 4)()
+        n = (c_longlong * 4)()
+        self._check(load().ppmlr_read_timing(self._h, ms, n))
+        return {k: (ms[i], n[i]) for i, k in enumerate(("x", "y", "z", "cfl"))}
 
     def set_stream(self, stream):
         return self._check(load().ppmlr_set_stream(self._h, _stream_handle(stream)))
