@@ -169,6 +169,34 @@ long long ppmlr_launch_count(const ppmlr_ctx *ctx);
 ppmlr_status ppmlr_enable_timing(ppmlr_ctx *ctx, int on);
 ppmlr_status ppmlr_read_timing(ppmlr_ctx *ctx, double *total_ms, long long *launches);
 
+/* Allocation-free CFL time step.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory -- a host
+ * solver whose device memory belongs to another allocator that forbids raw
+ * cudaMalloc, a coupling loop that cannot afford the device synchronisation
+ * an allocation may cause, or a program with a fixed device-memory budget.
+ * It needs no context: every input and the output are caller-owned device
+ * memory, and it performs no cudaMalloc, cudaFree or other allocation.
+ *   U: 8 device arrays of the state (layout above); n: cells per axis;
+ *   width[d], centre[d]: device arrays of the n[d] cell widths and centres of
+ *   each axis (no ghost cells); gamma, p_min, dipole_moment, r_inner: as in
+ *   ppmlr_bc; cfl > 0; blocks: reduction blocks, 0 = automatic, at most 1024
+ *   (the size of the static scratch; larger values return PPMLR_E_INVALID);
+ *   dt_out: device pointer that receives dt; cuda_stream: stream (NULL =
+ *   default).  Asynchronous.  Same formula and same double arithmetic as
+ *   ppmlr_cfl_dt, so both give the same dt for the same state.
+ * Scratch: a static device array of 1056 doubles (8.4 KB) that every GPU that
+ * loads the library holds until the process exits.  All calls on a device
+ * share it and it keeps the last call's contents (its ticket counter is
+ * cleared at the start of each call); calls whose kernels overlap on the GPU
+ * race on it and must be serialised by the caller.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) and
+ * caches it; make that first call before capturing any stream work.
+ * Errors: PPMLR_E_INVALID (NULL pointer, n < 1, too many cells or blocks,
+ * gamma <= 1, cfl <= 0), PPMLR_E_CUDA. */
+ppmlr_status ppmlr_cfl_dt_noalloc(const double *const U[8], const int n[3], const double *const width[3],
+                                  const double *const centre[3], double gamma, double p_min, double dipole_moment,
+                                  double r_inner, double cfl, int blocks, double *dt_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

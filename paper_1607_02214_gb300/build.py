@@ -22,6 +22,7 @@ COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcom
 UNITS = {
     "api.cu": ["-fmad=false"],
     "cfl.cu": ["-fmad=false"],
+    "cfl_noalloc.cu": ["-fmad=false"],
     "sweep_fp64.cu": ["-fmad=false"],
     "sweep_mixed.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
 }

@@ -57,6 +57,9 @@ SIGNATURES = [
     ("ppmlr_launch_count", c_longlong, [c_void_p]),
     ("ppmlr_enable_timing", c_int, [c_void_p, c_int]),
     ("ppmlr_read_timing", c_int, [c_void_p, POINTER(c_double), POINTER(c_longlong)]),
+    ("ppmlr_cfl_dt_noalloc", c_int, [DPTR8, POINTER(c_int), POINTER(c_double) * 3, POINTER(c_double) * 3,
+                                     c_double, c_double, c_double, c_double, c_double, c_int, POINTER(c_double),
+                                     c_void_p]),
 ]
 
 _lib = None
