@@ -12,7 +12,7 @@
  *     terms on the right-hand side and gamma = 5/3 (Sec. II, the MHD equations
  *     and their closure), in code units with mu0 = 1;
  *   - the PPMLR scheme outlined in Sec. II: zone-centred volume averages,
- *     piecewise-parabolic profiles, edge states from a characteristic method,
+ *     piecewise-parabolic profiles, edge states traced along characteristics,
  *     a Lagrangian update, then a remap to the fixed Eulerian grid.  The paper
  *     defers the formulas to Colella & Woodward (1984); the PPM interface
  *     formula, slope limiter, flattening, monotonicity constraint and
