@@ -25,6 +25,7 @@ UNITS = {
     "cfl_noalloc.cu": ["-fmad=false"],
     "sweep_fp64.cu": ["-fmad=false"],
     "sweep_mixed.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
+    "cfl_mixed.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
 }
 
 

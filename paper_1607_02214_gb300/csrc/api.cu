@@ -27,6 +27,8 @@ struct ppmlr_ctx {
     double *U[8], *Un[8];
     double *geo;                 // w[3], c[3]
     double *w[3], *c[3];
+    float *geof;                 // float copies of w[3], c[3] (mixed path)
+    float *wf[3], *cf[3];
     int *flags;
     unsigned long long *floors;
     double *dt_dev;
@@ -230,6 +232,16 @@ ppmlr_status ppmlr_create(const ppmlr_grid *grid, double gamma, const ppmlr_bc *
     if (e == cudaSuccess) e = cudaMemsetAsync(c->state, 0, sizeof(double) * c->stride * 16, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) { cudaFree(c->geo); cudaFree(c->state); delete c; return PPMLR_E_CUDA; }
+    {
+        std::vector<float> hf(host.size());
+        for (size_t k = 0; k < host.size(); k++) hf[k] = (float)host[k];
+        e = cudaMalloc(&c->geof, sizeof(float) * hf.size());
+        if (e != cudaSuccess) { cudaFree(c->geo); cudaFree(c->state); delete c; return PPMLR_E_OOM; }
+        for (int d = 0; d < 3; d++) { c->wf[d] = c->geof + off[d]; c->cf[d] = c->geof + off[3 + d]; }
+        e = cudaMemcpyAsync(c->geof, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) { cudaFree(c->geof); cudaFree(c->geo); cudaFree(c->state); delete c; return PPMLR_E_CUDA; }
+    }
     size_t rs = prec == PPMLR_FP64 ? sizeof(double) : sizeof(float);
     for (int d = 0; d < 3; d++) c->tile[d] = choose_tile(d, c->n, rs);
     *out = c;
@@ -242,6 +254,7 @@ void ppmlr_destroy(ppmlr_ctx *c)
     cudaStreamSynchronize(c->stream);
     for (auto &r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->pool) cudaEventDestroy(e);
+    cudaFree(c->geof);
     cudaFree(c->geo);
     cudaFree(c->state);
     delete c;
@@ -328,6 +341,10 @@ static ppmlr_status launch_one_sweep(ppmlr_ctx *c, int d, double dt, const doubl
     a.do_src = (a.M != 0.0 || a.powell) ? 1 : 0;
     a.dt = dt; a.dt_dev = dt_dev;
     a.flags = c->flags; a.floors = c->floors;
+    a.wf = c->wf[d];
+    a.cxf = c->cf[0]; a.cyf = c->cf[1]; a.czf = c->cf[2];
+    a.gammaf = (float)a.gamma; a.p_minf = (float)a.p_min; a.Mf = (float)a.M; a.r_innerf = (float)a.r_inner;
+    for (int k = 0; k < 8; k++) a.inflowf[k] = (float)a.inflow[k];
     int rec = timing_begin(c, d);
     cudaError_t e = c->prec == PPMLR_FP64 ? launch_sweep_fp64(d, a, t, c->stream)
                                           : launch_sweep_mixed(d, a, t, c->stream);
@@ -374,8 +391,11 @@ static ppmlr_status launch_cfl_kernel(ppmlr_ctx *c, double cfl)
     a.gamma = c->gamma; a.p_min = c->bc.p_min; a.M = c->bc.dipole_moment; a.r_inner = c->bc.r_inner;
     a.cfl = cfl;
     a.partial = c->partial; a.counter = c->counter; a.dt_out = c->dt_dev;
+    for (int d = 0; d < 3; d++) { a.wf[d] = c->wf[d]; a.cf[d] = c->cf[d]; }
+    a.gammaf = (float)a.gamma; a.p_minf = (float)a.p_min; a.Mf = (float)a.M; a.r_innerf = (float)a.r_inner;
     int rec = timing_begin(c, 3);
-    cudaError_t e = launch_cfl(a, c->cfl_blocks, c->stream);
+    cudaError_t e = c->prec == PPMLR_FP64 ? launch_cfl(a, c->cfl_blocks, c->stream)
+                                          : launch_cfl_mixed(a, c->cfl_blocks, c->stream);
     timing_end(c, rec);
     if (e != cudaSuccess) return cuda_fail(c, e, "cfl launch");
     c->launches++;

@@ -1,0 +1,95 @@
+// CFL time step of the mixed-precision path: the same rule as cfl.cu,
+//   dt = cfl * min over non-inner cells and axes of dx_d / (|v_d| + max(c_f(B'), c_f(B' + B_d))),
+// with float wave speeds, the double-float pressure recovery of the mixed
+// sweep and no FP64 instructions in the per-cell work.  Block minima and the
+// last-block combine (atomic ticket, no float atomics) as in cfl.cu.
+#include "sweep.cuh"
+
+namespace ppmlr {
+
+constexpr int CFLM_THREADS = 256;
+
+__device__ __forceinline__ float block_min_f(float v)
+{
+    __shared__ float red[CFLM_THREADS / 32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fminf(v, __shfl_down_sync(0xffffffffu, v, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < CFLM_THREADS / 32 ? red[threadIdx.x] : INFINITY;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v = fminf(v, __shfl_down_sync(0xffffffffu, v, off));
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(CFLM_THREADS) cfl_mixed_kernel(CflArgs a)
+{
+    const long long nx = a.n[0], ny = a.n[1], nz = a.n[2];
+    const long long ncell = nx * ny * nz;
+    const float gm1 = a.gammaf - 1.0f;
+    float best = INFINITY;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ncell;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / (nx * ny));
+        const float x = a.cf[0][ix + GH], y = a.cf[1][iy + GH], z = a.cf[2][iz + GH];
+        if (a.r_innerf > 0.0f) {
+            const float r2 = x * x + y * y + z * z, ri2 = a.r_innerf * a.r_innerf;
+            if (r2 < ri2 * (1.0f - 1e-5f)) continue;
+            if (r2 < ri2 * (1.0f + 1e-5f)) {
+                const double xd = a.c[0][ix + GH], yd = a.c[1][iy + GH], zd = a.c[2][iz + GH];
+                if (xd * xd + yd * yd + zd * zd < a.r_inner * a.r_inner) continue;
+            }
+        }
+        df q[8];
+#pragma unroll
+        for (int v = 0; v < 8; v++) q[v] = split_double(__ldg(a.U[v] + i));
+        float pr = pressure_df(q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], gm1);
+        if (pr < a.p_minf) pr = a.p_minf;
+        float Bd[3];
+        dipole_f(a.Mf, x, y, z, Bd);
+        const float rho = q[0].h, ir = 1.0f / rho;
+        const int idx[3] = {ix, iy, iz};
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+            const float Bn = q[4 + d].h, B1 = q[4 + t1].h, B2 = q[4 + t2].h;
+            const float c1 = fast2<float>(rho, pr, Bn, B1, B2, a.gammaf);
+            const float c2 = fast2<float>(rho, pr, Bn + Bd[d], B1 + Bd[t1], B2 + Bd[t2], a.gammaf);
+            const float cf = sqrtf(fmaxf(c1, c2));
+            const float sv = a.wf[d][idx[d] + GH] / (fabsf(q[1 + d].h * ir) + cf);
+            best = fminf(best, sv);
+        }
+    }
+    best = block_min_f(best);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        a.partial[blockIdx.x] = widen(best);
+        __threadfence();
+        unsigned int ticket = atomicAdd(a.counter, 1u);
+        last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        double m = INFINITY;
+        for (int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+            double v = __ldcg(a.partial + b);
+            m = v < m ? v : m;
+        }
+        float mf = block_min_f((float)m);   // exact: every partial is a widened float
+        if (threadIdx.x == 0) {
+            *a.dt_out = a.cfl * widen(mf);
+            *a.counter = 0u;
+        }
+    }
+}
+
+cudaError_t launch_cfl_mixed(const CflArgs &a, int blocks, cudaStream_t s)
+{
+    cfl_mixed_kernel<<<blocks, CFLM_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace ppmlr

@@ -38,6 +38,11 @@ struct SweepArgs {
     const double *dt_dev;
     int *flags;
     unsigned long long *floors;
+    // float copies for the mixed path (geometry and parameters)
+    const float *wf;           // widths along the sweep axis, ghost-extended
+    const float *cxf, *cyf, *czf;
+    float gammaf, p_minf, Mf, r_innerf;
+    float inflowf[8];
 };
 
 struct CflArgs {
@@ -47,6 +52,9 @@ struct CflArgs {
     const double *c[3];        // ghost-extended centres
     double gamma, p_min, M, r_inner;
     double cfl;
+    // float copies for the mixed path
+    const float *wf[3], *cf[3];
+    float gammaf, p_minf, Mf, r_innerf;
     double *partial;           // one entry per block
     unsigned int *counter;     // zero between launches; the last block resets it
     double *dt_out;            // device scalar
@@ -62,6 +70,7 @@ struct Tile {
 cudaError_t launch_sweep_fp64(int dir, const SweepArgs &a, const Tile &t, cudaStream_t s);
 cudaError_t launch_sweep_mixed(int dir, const SweepArgs &a, const Tile &t, cudaStream_t s);
 cudaError_t launch_cfl(const CflArgs &a, int blocks, cudaStream_t s);
+cudaError_t launch_cfl_mixed(const CflArgs &a, int blocks, cudaStream_t s);
 int cfl_threads();
 
 }  // namespace ppmlr

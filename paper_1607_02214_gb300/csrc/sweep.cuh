@@ -22,6 +22,7 @@
 #pragma once
 #include <type_traits>
 
+#include "mixed_util.cuh"
 #include "ppmlr_internal.h"
 
 namespace ppmlr {
@@ -195,7 +196,9 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(SweepArgs a)
     const int g = g0 - GH + p;                   // cell index along the axis (ghosts < 0 or >= N)
     const double dt = a.dt_dev ? *a.dt_dev : a.dt;
     const R dtr = R(dt);
-    const R gam = R(a.gamma);
+    R gam;
+    if constexpr (F64) gam = R(a.gamma);
+    else gam = a.gammaf;
 
     // base offset and stride of this lane's pencil
     long long base, stride;
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(SweepArgs a)
     R Bd0 = 0, Bd1 = 0, Bd2 = 0;
     bool floored = false;
     const bool out_cell = act && p >= GH && p < GH + Ce;
-    if (act) {
+    if (act && F64) {
         dx = a.w[g + GH];
         pos[0] = a.cx[(DIR == 0 ? g : ix) + GH];
         pos[1] = a.cy[(DIR == 1 ? g : iy) + GH];
@@ -239,7 +242,6 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(SweepArgs a)
 #pragma unroll
             for (int v = 0; v < 8; v++) Uc[v] = __ldg(a.U[v] + gi);
         }
-        // pressure recovery in double on both paths
         double rd = Uc[0];
         double mn = Uc[1 + DIR], m1 = Uc[1 + T1], m2 = Uc[1 + T2];
         double bn = Uc[4 + DIR], b1 = Uc[4 + T1], b2 = Uc[4 + T2];
@@ -248,18 +250,54 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(SweepArgs a)
                                         - 0.5 * (bn * bn + b1 * b1 + b2 * b2));
         if (prd < a.p_min) { prd = a.p_min; floored = out_cell; }
         Bd0 = R(Bdg[DIR]); Bd1 = R(Bdg[T1]); Bd2 = R(Bdg[T2]);
-        if constexpr (F64) {
-            rho = rd; u = mn / rd; v1 = m1 / rd; v2 = m2 / rd;
-            Bn = bn; B1 = b1; B2 = b2; pr = prd;
-            e = E / rd;
-            dm = rd * dx;
-        } else {
-            rho = float(rd);
-            u = float(mn) / rho; v1 = float(m1) / rho; v2 = float(m2) / rho;
-            Bn = float(bn); B1 = float(b1); B2 = float(b2); pr = float(prd);
-            e = float(E) / rho;
-            dm = rho * float(dx);
+        rho = R(rd); u = R(mn / rd); v1 = R(m1 / rd); v2 = R(m2 / rd);
+        Bn = R(bn); B1 = R(b1); B2 = R(b2); pr = R(prd);
+        e = R(E / rd);
+        dm = R(rd * dx);
+    } else if (act) {
+        // mixed path: float geometry, float dipole, integer double->float
+        // splits and a double-float pressure recovery (no FP64 instructions)
+        const float dxf = a.wf[g + GH];
+        const float px = a.cxf[(DIR == 0 ? g : ix) + GH];
+        const float py = a.cyf[(DIR == 1 ? g : iy) + GH];
+        const float pz = a.czf[(DIR == 2 ? g : iz) + GH];
+        float Bdf[3];
+        dipole_f(a.Mf, px, py, pz, Bdf);
+        Bd0 = Bdf[DIR]; Bd1 = Bdf[T1]; Bd2 = Bdf[T2];
+        int src = g;
+        bool fixed = false;
+        if (g < 0 || g >= a.N) {
+            int kind = g < 0 ? a.bc_lo : a.bc_hi;
+            if (kind == PPMLR_BC_PERIODIC) src = ((g % a.N) + a.N) % a.N;
+            else if (kind == PPMLR_BC_OUTFLOW) src = g < 0 ? 0 : a.N - 1;
+            else fixed = true;
         }
+        const float gm1 = a.gammaf - 1.0f;
+        if (fixed) {
+            const float *f = a.inflowf;
+            rho = f[0];
+            u = f[1 + DIR]; v1 = f[1 + T1]; v2 = f[1 + T2];
+            Bn = f[4 + DIR] - Bd0; B1 = f[4 + T1] - Bd1; B2 = f[4 + T2] - Bd2;
+            pr = f[7];
+            e = pr / (gm1 * rho) + 0.5f * (u * u + v1 * v1 + v2 * v2) + 0.5f * (Bn * Bn + B1 * B1 + B2 * B2) / rho;
+        } else {
+            const long long gi = base + (long long)src * stride;
+            df q[8];
+#pragma unroll
+            for (int v = 0; v < 8; v++) q[v] = split_double(__ldg(a.U[v] + gi));
+            float prf = pressure_df(q[0], q[1 + DIR], q[1 + T1], q[1 + T2], q[4 + DIR], q[4 + T1], q[4 + T2],
+                                    q[7], gm1);
+            rho = q[0].h;
+            const float ir = 1.0f / rho;
+            u = q[1 + DIR].h * ir; v1 = q[1 + T1].h * ir; v2 = q[1 + T2].h * ir;
+            Bn = q[4 + DIR].h; B1 = q[4 + T1].h; B2 = q[4 + T2].h;
+            e = q[7].h * ir;
+            pr = prf;
+        }
+        if (pr < a.p_minf) { pr = a.p_minf; floored = out_cell; }
+        dm = rho * dxf;
+    }
+    if (act) {
         R Pt = pr + R(0.5) * (Bn * Bn + B1 * B1 + B2 * B2);
         W = rho * K<R>::sq(fast2<R>(rho, pr, Bn, B1, B2, gam));
         SM(A_RHO, s) = rho; SM(A_U, s) = u; SM(A_V1, s) = v1; SM(A_V2, s) = v2;
@@ -303,7 +341,9 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(SweepArgs a)
         }
         SM(SB0 + 7, s) = ft;
         if (a.do_src && out_cell) {
-            R h = R(0.5) * R(a.w[g + GH - 1]) + R(dx) + R(0.5) * R(a.w[g + GH + 1]);
+            R h;
+            if constexpr (F64) h = R(0.5) * R(a.w[g + GH - 1]) + R(dx) + R(0.5) * R(a.w[g + GH + 1]);
+            else h = R(0.5) * a.wf[g + GH - 1] + a.wf[g + GH] + R(0.5) * a.wf[g + GH + 1];
             R DB0 = (SM(A_BN, s + PS) - SM(A_BN, s - PS)) / h;
             R DB1 = (SM(A_B1, s + PS) - SM(A_B1, s - PS)) / h;
             R DB2 = (SM(A_B2, s + PS) - SM(A_B2, s - PS)) / h;
@@ -412,7 +452,9 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(SweepArgs a)
     if (act && p >= 4 && p <= NPe - 5) {
         R lu = SM(SC0 + 0, s - PS), lS = SM(SC0 + 1, s - PS), ls1 = SM(SC0 + 2, s - PS), ls2 = SM(SC0 + 3, s - PS);
         R lb1 = SM(SC0 + 4, s - PS), lb2 = SM(SC0 + 5, s - PS), lfe = SM(SC0 + 6, s - PS);
-        R dxr = R(dx);
+        R dxr;
+        if constexpr (F64) dxr = R(dx);
+        else dxr = a.wf[g + GH];
         dxL = dxr + dtr * (rs_u - lu);
         if (!(dxL > R(0))) atomicOr(a.flags, FLAG_CFL);
         R uL = u - dtr * (rs_S - lS) / dm;
@@ -517,7 +559,7 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(SweepArgs a)
                 Un[7] = Un[7] + dt * src_e;
             }
         } else {
-            const R dxr = R(dx);
+            const R dxr = a.wf[g + GH];
             R dU[8];
 #pragma unroll
             for (int v = 0; v < 7; v++) dU[cmap[v]] = (dCv[v] + SM(SB0 + v, s - PS) - SM(SB0 + v, s)) / dxr;
@@ -528,10 +570,25 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(SweepArgs a)
                 dU[7] += dtr * src_e;
             }
 #pragma unroll
-            for (int v = 0; v < 8; v++) Un[v] = Un[v] + double(dU[v]);
+            for (int v = 0; v < 8; v++) Un[v] = Un[v] + widen(dU[v]);
         }
-        if (a.r_inner > 0.0 &&
-            pos[0] * pos[0] + pos[1] * pos[1] + pos[2] * pos[2] < a.r_inner * a.r_inner) {
+        bool inner = false;
+        if constexpr (F64) {
+            inner = a.r_inner > 0.0 &&
+                    pos[0] * pos[0] + pos[1] * pos[1] + pos[2] * pos[2] < a.r_inner * a.r_inner;
+        } else if (a.r_innerf > 0.0f) {
+            // float test with an exact double test for centres within 1e-5 of the sphere
+            const float px = a.cxf[(DIR == 0 ? g : ix) + GH], py = a.cyf[(DIR == 1 ? g : iy) + GH],
+                        pz = a.czf[(DIR == 2 ? g : iz) + GH];
+            const float r2 = px * px + py * py + pz * pz, ri2 = a.r_innerf * a.r_innerf;
+            if (r2 < ri2 * (1.0f - 1e-5f)) inner = true;
+            else if (r2 < ri2 * (1.0f + 1e-5f)) {
+                const double x = a.cx[(DIR == 0 ? g : ix) + GH], y = a.cy[(DIR == 1 ? g : iy) + GH],
+                             z = a.cz[(DIR == 2 ? g : iz) + GH];
+                inner = x * x + y * y + z * z < a.r_inner * a.r_inner;
+            }
+        }
+        if (inner) {
             const double *q = a.inner;
             double rh = q[0];
             Un[0] = rh;
@@ -542,8 +599,8 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(SweepArgs a)
         }
         bool bad = false;
 #pragma unroll
-        for (int v = 0; v < 8; v++) {
-            bad |= !isfinite(Un[v]);
+        for (int v = 0; v < 8; v++) {   // non-finite test on the exponent bits (integer pipe)
+            bad |= ((__double2hiint(Un[v]) >> 20) & 0x7FF) == 0x7FF;
             a.Un[v][gi] = Un[v];
         }
         if (bad) atomicOr(a.flags, FLAG_NONFINITE);

@@ -140,3 +140,31 @@ def test_mixed_precision(prob):
     err = rel_l1(a, b)
     assert np.all(np.isfinite(a))
     assert np.max(err) <= MIXED_TOL, err
+
+
+def test_high_mach_translation_fp64_exact_mixed_bounded():
+    # Uniform density and velocity (100, 3, 0) with smooth pressure and field
+    # perturbations: kinetic energy ~3300 x thermal energy.  The FP64 path is
+    # bit-identical to the oracle.  The mixed path's FP32 remap fluxes of
+    # momentum and energy carry absolute errors ~1e-7 of the kinetic energy, so
+    # its recovered pressure drifts by up to ~1e-2 here: the mixed path is meant
+    # for flows like the magnetosphere (kinetic/thermal ~ 50), and this bound
+    # documents how far it degrades at Mach ~100.
+    n = (24, 20, 18)
+    edges = [inputs.uniform_axis(k, 0, 1) for k in n]
+    base = inputs.random_smooth_state(n, 31, amp_v=0.0, amp_b=0.05)
+    one = np.ones_like(base[0])
+    p0 = 1.0 + 0.1 * np.sin(2 * np.pi * (base[0] - base[0].mean()))
+    U = inputs.conserved(one, (100.0 * one, 3.0 * one, 0 * one), (base[4], base[5], base[6]), p0, 5.0 / 3.0)
+    pr = inputs.Problem("mach100", edges, 5.0 / 3.0, inputs.BoundarySpec(), U)
+
+    def pressure(X):
+        return (2.0 / 3.0) * (X[7] - 0.5 * (X[1] ** 2 + X[2] ** 2 + X[3] ** 2) / X[0]
+                              - 0.5 * (X[4] ** 2 + X[5] ** 2 + X[6] ** 2))
+    o, g, dts = run_pair(pr, 5)
+    assert np.array_equal(g.get_state(), o.get_state())
+    _, gm, _ = run_pair(pr, 5, precision=ppmlr.PPMLR_MIXED, dts=dts)
+    pa, pb = pressure(gm.get_state()), pressure(o.get_state())
+    assert np.all(pb > 0.5)
+    rel = np.abs(pa - pb) / pb
+    assert rel.max() < 5e-2 and rel.mean() < 5e-3, (rel.max(), rel.mean())
