@@ -224,6 +224,8 @@ def run_ours(args, rank, world, dist):
     def timed_run(precision, steps, warmup, with_clocks=False):
         ctx = ppmlr.Context.from_problem(prob, precision)
         ctx.set_state(U0)
+        if not args.no_autotune:
+            ctx.autotune()
         ctx.step_cfl(prob.cfl, warmup)
         ctx.check()
         stream = torch.cuda.current_stream()
@@ -350,6 +352,14 @@ def run_ours(args, rank, world, dist):
                "d2h_bytes_per_step": nbytes, "steps": ksteps}
         del ectx
 
+    # ---- batched ensemble: 48 seeded instances on uneven grids (mixed path)
+    if not args.quick and not args.no_ensemble and world == 1:
+        extra["ensemble"] = run_ensemble(args, value, barrier)
+
+    # ---- large single domain 512x384x384 (finest 0.2 R_E), both precisions
+    if not args.quick and not args.no_large and world == 1:
+        extra["large"] = run_large(args, barrier)
+
     # ---- CPU baseline: the oracle on this host's cores, bounded sample
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -370,6 +380,124 @@ def run_ours(args, rank, world, dist):
     return out
 
 
+def run_ensemble(args, fp64_value, barrier):
+    """48 magnetosphere instances, grids drawn from {96^3, 128x96x96, 160x128x128},
+    seeded solar wind; one persistent launch per sweep, one CUDA graph per step."""
+    import torch
+    from paper_1607_02214_gb300 import inputs, ppmlr
+    t0 = time.perf_counter()
+    probs = inputs.ensemble(48)
+    log(f"[bench] ensemble inputs built in {time.perf_counter() - t0:.1f} s")
+    cells = sum(p.cells for p in probs)
+    out = {"workload": "ensemble_48_magnetosphere_mixed", "instances": len(probs), "cells": cells,
+           "grids": sorted({"x".join(map(str, p.n)) for p in probs})}
+    ens = ppmlr.Ensemble(probs, precision=ppmlr.PPMLR_MIXED)
+    for i, p in enumerate(probs):
+        ens.set_state(i, p.U0)
+    out["tuned_ms"] = ens.autotune()
+    out["tile_thread_budget"] = ens.tiles()
+    ens.step(0.4, args.warmup)
+    ens.check()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    n0 = ens.launch_count
+    e0.record(stream)
+    ens.step(0.4, args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    ens.check()
+    out.update({"value": cells * args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.steps,
+                "gpu_launches": ens.launch_count - n0, "graph_replay": True})
+    out["speedup_vs_fp64"] = out["value"] / fp64_value
+    kern = ens.time_kernels(0.4, 3)
+    out["kernels_avg_ms"] = kern
+    dom = max(("x", "y", "z"), key=lambda k: kern[k])
+    ach = BYTES_PER_CELL_SWEEP * cells / (kern[dom] * 1e-3) / 1e9
+    out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": 6787.2, "unit": "GB/s", "frac": ach / 6787.2,
+                       "traffic": None, "kernel": f"sweep_ensemble_{dom}", "avg_launch_ms": kern[dom],
+                       "peak_source": "measured"}
+    # the same instances advanced one context at a time (no batching)
+    ctxs = [ppmlr.Context.from_problem(p, ppmlr.PPMLR_MIXED) for p in probs]
+    for c, p in zip(ctxs, probs):
+        c.set_state(p.U0)
+        c.step_cfl(0.4, 1)
+    barrier()
+    e0.record(stream)
+    for _ in range(3):
+        for c in ctxs:
+            c.step_cfl(0.4, 1)
+    e1.record(stream)
+    e1.synchronize()
+    out["loop_of_contexts_value"] = cells * 3 / (e0.elapsed_time(e1) * 1e-3)
+    out["speedup_vs_loop_of_contexts"] = out["value"] / out["loop_of_contexts_value"]
+    for c in ctxs:
+        c.close()
+    del ctxs
+    # error against the FP64 ensemble (each with its own device dt)
+    nerr = 10
+    a = ppmlr.Ensemble(probs, precision=ppmlr.PPMLR_FP64)
+    b = ppmlr.Ensemble(probs, precision=ppmlr.PPMLR_MIXED)
+    for i, p in enumerate(probs):
+        a.set_state(i, p.U0)
+        b.set_state(i, p.U0)
+    a.step(0.4, nerr)
+    b.step(0.4, nerr)
+    worst = 0.0
+    for i in range(len(probs)):
+        ua, ub = a.get_state(i), b.get_state(i)
+        ref = np.abs(ua).reshape(8, -1).sum(axis=1)
+        grp = np.array([ref[0], *[ref[1:4].sum()] * 3, *[ref[4:7].sum()] * 3, ref[7]])
+        worst = max(worst, float((np.abs(ub - ua).reshape(8, -1).sum(axis=1) / grp).max()))
+    out["error_vs_fp64"] = {"steps": nerr, "max_rel_l1_over_instances_and_variables": worst}
+    a.close()
+    b.close()
+    ens.close()
+    return out
+
+
+def run_large(args, barrier):
+    """512x384x384 stretched grid (finest 0.2 R_E), same extent and boundaries."""
+    import torch
+    from paper_1607_02214_gb300 import inputs, ppmlr
+    prob = inputs.magnetosphere(n=(512, 384, 384), h0=0.2)
+    cells = prob.cells
+    out = {"workload": "magnetosphere_512x384x384_h0_0.2", "cells": cells}
+    U0 = torch.from_numpy(prob.U0).cuda()
+    for name, prec, steps in (("fp64", ppmlr.PPMLR_FP64, 5), ("mixed", ppmlr.PPMLR_MIXED, 20)):
+        ctx = ppmlr.Context.from_problem(prob, prec)
+        ctx.set_state(U0)
+        ctx.autotune()
+        ctx.step_cfl(prob.cfl, 3)
+        ctx.check()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        ctx.enable_timing(True)
+        e0.record(stream)
+        ctx.step_cfl(prob.cfl, steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        kern = ctx.read_timing()
+        ctx.enable_timing(False)
+        ctx.check()
+        per = {}
+        for k, (tot, n) in kern.items():
+            avg = tot / max(n, 1)
+            byts = (BYTES_PER_CELL_SWEEP if k != "cfl" else 64) * cells
+            per[k] = {"avg_ms": avg, "hbm_frac_of_measured": byts / (avg * 1e-3) / 1e9 / 6787.2}
+            if name == "fp64":
+                per[k]["fp64_gflops"] = FLOPS_PER_CELL[k] * cells / (avg * 1e-3) / 1e9
+        out[name] = {"value": cells * steps / (ms * 1e-3), "ms_per_step": ms / steps, "steps": steps,
+                     "kernels": per, "tiles": ctx.tiles()}
+        ctx.close()
+    out["mixed"]["speedup_vs_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    del U0
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -382,6 +510,9 @@ def main():
     ap.add_argument("--accuracy-steps", type=int, default=50)
     ap.add_argument("--quick", action="store_true", help="main measurement only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         log("[bench] warm-up raised to 3 steps")

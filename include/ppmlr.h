@@ -169,6 +169,60 @@ long long ppmlr_launch_count(const ppmlr_ctx *ctx);
 ppmlr_status ppmlr_enable_timing(ppmlr_ctx *ctx, int on);
 ppmlr_status ppmlr_read_timing(ppmlr_ctx *ctx, double *total_ms, long long *launches);
 
+/* Tile-shape autotuner of one context: for each sweep direction, times a set
+ * of candidate tile shapes (chunk length along the sweep axis x lanes per
+ * tile) on the current state, out of place (the state is unchanged), and keeps
+ * the fastest.  Results do not depend on the tile shape, only the speed does.
+ * Shapes are cached per process by (direction, grid, precision), so a second
+ * context of the same shape reuses them without timing.  best_ms (3 entries,
+ * may be NULL) receives the tuned sweep times.  Synchronises. */
+ppmlr_status ppmlr_autotune(ppmlr_ctx *ctx, double *best_ms);
+
+/* Tile shape in use per direction: C (cells per chunk) and L (lanes);
+ * C and L point to 3 entries each. */
+ppmlr_status ppmlr_get_tiles(ppmlr_ctx *ctx, int *C, int *L);
+
+/* ---- Batched ensemble ----------------------------------------------------
+ * count independent instances, each with its own grid and boundary
+ * specification (e.g. different solar-wind and IMF inputs, uneven grid
+ * sizes), advanced together: per step one device CFL pass giving every
+ * instance its own dt, then one persistent launch per sweep direction whose
+ * blocks take (instance, tile) work items from a global counter.  A step is
+ * captured once as a CUDA graph (x,y,z and z,y,x variants) and replayed.
+ * The results of every instance are bit-identical to a single context
+ * advanced with ppmlr_step_cfl.  The ensemble owns all its device memory. */
+typedef struct ppmlr_ens ppmlr_ens;
+
+ppmlr_status ppmlr_ensemble_create(int count, const ppmlr_grid *grids, const ppmlr_bc *bcs, double gamma,
+                                   ppmlr_precision prec, void *cuda_stream, ppmlr_ens **out);
+ppmlr_status ppmlr_ensemble_set_stream(ppmlr_ens *ens, void *cuda_stream);
+/* State of instance i (layout as for a context). */
+ppmlr_status ppmlr_ensemble_set_state(ppmlr_ens *ens, int i, const double *const U[8], int on_device);
+ppmlr_status ppmlr_ensemble_get_state(ppmlr_ens *ens, int i, double *const U[8], int on_device);
+/* nsteps graph-replayed steps with per-instance device dt (asynchronous). */
+ppmlr_status ppmlr_ensemble_step(ppmlr_ens *ens, double cfl, int nsteps);
+/* The same steps with direct launches and CUDA events around every kernel;
+ * avg_ms (4 entries) receives the mean time per launch of the x, y, z sweeps
+ * and the CFL pass.  Synchronises. */
+ppmlr_status ppmlr_ensemble_time_kernels(ppmlr_ens *ens, double cfl, int nsteps, double *avg_ms);
+/* Tile-shape autotuner of the ensemble: per direction, the thread budget of
+ * the tiles of all instances and the launch form (0: persistent blocks taking
+ * tiles from a work counter; 1: one block per tile, arguments from a device
+ * table; 2: one block per tile, arguments of all instances in the kernel
+ * parameter, up to 64 instances), timed out of place; best_ms: 3 entries or
+ * NULL. */
+ppmlr_status ppmlr_ensemble_autotune(ppmlr_ens *ens, double *best_ms);
+/* Launch form and thread budget per direction in use: 1000 * form + budget
+ * (3 entries). */
+ppmlr_status ppmlr_ensemble_get_tiles(ppmlr_ens *ens, int *maxt);
+/* dt of the last step of every instance (count entries; synchronises). */
+ppmlr_status ppmlr_ensemble_get_dt(ppmlr_ens *ens, double *dt_out);
+ppmlr_status ppmlr_ensemble_check(ppmlr_ens *ens);
+ppmlr_status ppmlr_ensemble_get_diagnostics(ppmlr_ens *ens, long long *step, long long *floor_hits);
+const char *ppmlr_ensemble_last_error(const ppmlr_ens *ens);
+long long ppmlr_ensemble_launch_count(const ppmlr_ens *ens);
+void ppmlr_ensemble_destroy(ppmlr_ens *ens);
+
 /* Allocation-free CFL time step.  The paper has no counterpart: this entry
  * point exists for callers that must not allocate device memory -- a host
  * solver whose device memory belongs to another allocator that forbids raw

@@ -21,6 +21,7 @@ COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcom
                  "-I", os.path.join(HERE, "..", "include")]
 UNITS = {
     "api.cu": ["-fmad=false"],
+    "ensemble.cu": ["-fmad=false"],
     "cfl.cu": ["-fmad=false"],
     "cfl_noalloc.cu": ["-fmad=false"],
     "sweep_fp64.cu": ["-fmad=false"],

@@ -7,7 +7,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "ppmlr_internal.h"
@@ -96,7 +99,7 @@ static ppmlr_status cuda_fail(ppmlr_ctx *c, cudaError_t e, const char *what)
 // Ghost-extended widths and centres of one axis (same rules and arithmetic as
 // the CPU reference): periodic faces wrap, other faces mirror the edge widths
 // (clamped to the axis); centres extend the grid by the ghost widths.
-static void build_axis(int n, const double *edges, int bc_lo, int bc_hi, std::vector<double> &w,
+void ppmlr::build_axis(int n, const double *edges, int bc_lo, int bc_hi, std::vector<double> &w,
                        std::vector<double> &ce)
 {
     w.assign(n + 2 * GH, 0.0);
@@ -121,18 +124,13 @@ static void build_axis(int n, const double *edges, int bc_lo, int bc_hi, std::ve
 // Tile shape for a sweep along an axis of N cells: whole pencils when they fit
 // in MAXT positions, else equal chunks; as many lanes as fit (powers of two
 // for the y/z sweeps, whose lanes are consecutive x cells).
-static Tile choose_tile(int dir, const int n[3], size_t real_size)
+Tile ppmlr::make_tile(int dir, const int n[3], size_t real_size, int C, int L)
 {
     Tile t;
     const int N = n[dir];
-    t.nchunk = 1;
-    t.C = N;
-    while (t.C + 2 * GH > MAXT) {
-        t.nchunk++;
-        t.C = (N + t.nchunk - 1) / t.nchunk;
-    }
+    t.C = C < 1 ? 1 : (C > N ? N : C);
+    t.nchunk = (N + t.C - 1) / t.C;
     t.NP = t.C + 2 * GH;
-    int L = MAXT / t.NP;
     if (L < 1) L = 1;
     if (dir == 0) {
         long long pencils = (long long)n[1] * n[2];
@@ -141,10 +139,7 @@ static Tile choose_tile(int dir, const int n[3], size_t real_size)
         t.ngx = (int)((pencils + L - 1) / L);
         t.ntiles = t.ngx * t.nchunk;
     } else {
-        int p2 = 1;
-        while (p2 * 2 <= L && p2 * 2 <= 16) p2 *= 2;
-        while (p2 > 1 && p2 / 2 >= n[0]) p2 /= 2;
-        t.L = p2;
+        t.L = L;
         t.ngx = (n[0] + t.L - 1) / t.L;
         int other = dir == 1 ? n[2] : n[1];
         t.ntiles = t.ngx * other * t.nchunk;
@@ -152,6 +147,49 @@ static Tile choose_tile(int dir, const int n[3], size_t real_size)
     t.threads = ((t.NP * t.L + 31) / 32) * 32;
     t.smem = (size_t)NSM * t.NP * t.L * real_size;
     return t;
+}
+
+// Default tile policy: whole pencils when they fit the thread budget, else
+// equal chunks; as many lanes as fit (powers of two for the y/z sweeps, whose
+// lanes are consecutive x cells).
+Tile ppmlr::choose_tile(int dir, const int n[3], size_t real_size)
+{
+    const int N = n[dir];
+    const int maxt = real_size == sizeof(double) ? MAXT_F64 : MAXT;
+    int nchunk = 1, C = N;
+    while (C + 2 * GH > maxt) {
+        nchunk++;
+        C = (N + nchunk - 1) / nchunk;
+    }
+    int L = maxt / (C + 2 * GH);
+    if (L < 1) L = 1;
+    if (dir != 0) {
+        int p2 = 1;
+        while (p2 * 2 <= L && p2 * 2 <= 16) p2 *= 2;
+        while (p2 > 1 && p2 / 2 >= n[0]) p2 /= 2;
+        L = p2;
+    }
+    return make_tile(dir, n, real_size, C, L);
+}
+
+bool ppmlr::validate_grid_bc(const ppmlr_grid *grid, const ppmlr_bc *bc)
+{
+    if (!grid || !bc) return false;
+    for (int d = 0; d < 3; d++) {
+        if (grid->n[d] < 1 || !grid->edges[d]) return false;
+        for (int i = 0; i < grid->n[d]; i++)
+            if (!(grid->edges[d][i + 1] > grid->edges[d][i])) return false;
+        for (int s = 0; s < 2; s++)
+            if (bc->face[d][s] < PPMLR_BC_PERIODIC || bc->face[d][s] > PPMLR_BC_INFLOW) return false;
+        if ((bc->face[d][0] == PPMLR_BC_PERIODIC) != (bc->face[d][1] == PPMLR_BC_PERIODIC)) return false;
+    }
+    bool any_inflow = false;
+    for (int d = 0; d < 3; d++) any_inflow |= bc->face[d][0] == PPMLR_BC_INFLOW || bc->face[d][1] == PPMLR_BC_INFLOW;
+    if (!(bc->p_min >= 0.0)) return false;
+    if (any_inflow && !(bc->inflow.rho > 0.0 && bc->inflow.p > 0.0)) return false;
+    if (bc->r_inner > 0.0 && !(bc->inner.rho > 0.0 && bc->inner.p >= 0.0)) return false;
+    long long ncell = (long long)grid->n[0] * grid->n[1] * grid->n[2];
+    return ncell <= (1LL << 31) - 1;
 }
 
 static bool is_sweep_noop(const ppmlr_ctx *c, int d)
@@ -169,21 +207,8 @@ ppmlr_status ppmlr_create(const ppmlr_grid *grid, double gamma, const ppmlr_bc *
     *out = nullptr;
     if (!grid || !bc) return PPMLR_E_INVALID;
     if (!(gamma > 1.0) || (prec != PPMLR_FP64 && prec != PPMLR_MIXED)) return PPMLR_E_INVALID;
-    for (int d = 0; d < 3; d++) {
-        if (grid->n[d] < 1 || !grid->edges[d]) return PPMLR_E_INVALID;
-        for (int i = 0; i < grid->n[d]; i++)
-            if (!(grid->edges[d][i + 1] > grid->edges[d][i])) return PPMLR_E_INVALID;
-        for (int s = 0; s < 2; s++)
-            if (bc->face[d][s] < PPMLR_BC_PERIODIC || bc->face[d][s] > PPMLR_BC_INFLOW) return PPMLR_E_INVALID;
-        if ((bc->face[d][0] == PPMLR_BC_PERIODIC) != (bc->face[d][1] == PPMLR_BC_PERIODIC)) return PPMLR_E_INVALID;
-    }
-    bool any_inflow = false;
-    for (int d = 0; d < 3; d++) any_inflow |= bc->face[d][0] == PPMLR_BC_INFLOW || bc->face[d][1] == PPMLR_BC_INFLOW;
-    if (!(bc->p_min >= 0.0)) return PPMLR_E_INVALID;
-    if (any_inflow && !(bc->inflow.rho > 0.0 && bc->inflow.p > 0.0)) return PPMLR_E_INVALID;
-    if (bc->r_inner > 0.0 && !(bc->inner.rho > 0.0 && bc->inner.p >= 0.0)) return PPMLR_E_INVALID;
+    if (!validate_grid_bc(grid, bc)) return PPMLR_E_INVALID;
     long long ncell = (long long)grid->n[0] * grid->n[1] * grid->n[2];
-    if (ncell > (1LL << 31) - 1) return PPMLR_E_INVALID;
 
     ppmlr_ctx *c = new ppmlr_ctx();
     memcpy(c->n, grid->n, sizeof(c->n));
@@ -322,7 +347,7 @@ static ppmlr_status launch_one_sweep(ppmlr_ctx *c, int d, double dt, const doubl
     if (is_sweep_noop(c, d)) return PPMLR_OK;
     SweepArgs a;
     memset(&a, 0, sizeof(a));
-    for (int v = 0; v < 8; v++) { a.U[v] = c->U[v]; a.Un[v] = c->Un[v]; }
+    a.U = c->U[0]; a.Un = c->Un[0]; a.vs = (long long)c->stride;
     for (int k = 0; k < 3; k++) a.n[k] = c->n[k];
     const Tile &t = c->tile[d];
     a.N = c->n[d];
@@ -443,6 +468,92 @@ ppmlr_status ppmlr_get_diagnostics(ppmlr_ctx *c, long long *step, long long *flo
     if (step) *step = c->steps;
     if (floor_hits) *floor_hits = (long long)fl;
     if (order_parity) *order_parity = (int)(c->steps & 1);
+    return PPMLR_OK;
+}
+
+// Per-process cache of tuned tile shapes: (dir, nx, ny, nz, prec) -> (C, L).
+static std::mutex g_tune_mutex;
+static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
+
+ppmlr_status ppmlr_autotune(ppmlr_ctx *c, double *best_ms)
+{
+    if (!c) return PPMLR_E_INVALID;
+    const size_t rs = c->prec == PPMLR_FP64 ? sizeof(double) : sizeof(float);
+    const int maxt = c->prec == PPMLR_FP64 ? MAXT_F64 : MAXT;
+    unsigned long long floors_before = 0;
+    CK(c, cudaMemcpyAsync(&floors_before, c->floors, sizeof(floors_before), cudaMemcpyDeviceToHost, c->stream),
+       "floors copy");
+    ppmlr_status st = launch_cfl_kernel(c, 0.4);      // a valid device dt for the timing runs
+    if (st != PPMLR_OK) return st;
+    cudaEvent_t t0, t1;
+    CK(c, cudaEventCreate(&t0), "event");
+    CK(c, cudaEventCreate(&t1), "event");
+    const bool was_timing = c->timing;
+    c->timing = false;
+    for (int d = 0; d < 3; d++) {
+        if (best_ms) best_ms[d] = 0.0;
+        if (is_sweep_noop(c, d)) continue;
+        auto key = std::make_tuple(d, c->n[0], c->n[1], c->n[2], (int)c->prec);
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mutex);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) {
+                c->tile[d] = make_tile(d, c->n, rs, it->second.first, it->second.second);
+                continue;
+            }
+        }
+        const int N = c->n[d];
+        std::vector<std::pair<int, int>> cands;
+        for (int nchunk = 1; nchunk <= 4; nchunk++) {
+            const int C = (N + nchunk - 1) / nchunk;
+            if (C + 2 * GH > maxt) continue;
+            if (nchunk > 1 && C < 48) break;
+            for (int L = 1; L <= 16; L *= 2) {
+                if ((C + 2 * GH) * L > maxt) break;
+                if (d != 0 && L > 1 && L / 2 >= c->n[0]) break;
+                if (d == 0 && L > 1 && (long long)L > (long long)c->n[1] * c->n[2]) break;
+                cands.push_back({C, L});
+            }
+        }
+        float best = 1e30f;
+        std::pair<int, int> pick = {c->tile[d].C, c->tile[d].L};
+        const Tile keep = c->tile[d];
+        for (auto &cl : cands) {
+            c->tile[d] = make_tile(d, c->n, rs, cl.first, cl.second);
+            float tot = 0.0f;
+            for (int rep = 0; rep < 3; rep++) {
+                CK(c, cudaEventRecord(t0, c->stream), "event");
+                st = launch_one_sweep(c, d, 0.0, c->dt_dev);
+                if (st != PPMLR_OK) { c->tile[d] = keep; return st; }
+                CK(c, cudaEventRecord(t1, c->stream), "event");
+                CK(c, cudaEventSynchronize(t1), "event sync");
+                // undo the buffer swap of launch_one_sweep: the state stays in place
+                for (int v = 0; v < 8; v++) { double *tmp = c->U[v]; c->U[v] = c->Un[v]; c->Un[v] = tmp; }
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, t0, t1);
+                if (rep > 0) tot += ms;
+            }
+            if (tot < best) { best = tot; pick = cl; }
+        }
+        c->tile[d] = make_tile(d, c->n, rs, pick.first, pick.second);
+        if (best_ms) best_ms[d] = best / 2.0f;
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tune_cache[key] = pick;
+    }
+    c->timing = was_timing;
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    CK(c, cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream), "flags reset");
+    CK(c, cudaMemcpyAsync(c->floors, &floors_before, sizeof(floors_before), cudaMemcpyHostToDevice, c->stream),
+       "floors restore");
+    CK(c, cudaStreamSynchronize(c->stream), "sync");
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_get_tiles(ppmlr_ctx *c, int *C, int *L)
+{
+    if (!c || !C || !L) return PPMLR_E_INVALID;
+    for (int d = 0; d < 3; d++) { C[d] = c->tile[d].C; L[d] = c->tile[d].L; }
     return PPMLR_OK;
 }
 

@@ -46,13 +46,14 @@ __device__ __forceinline__ double block_min(double v)
     return v;
 }
 
-__global__ void __launch_bounds__(CFL_THREADS) cfl_kernel(CflArgs a)
+// Block `bid` of `nb` blocks working on the domain described by `a`.
+__device__ __forceinline__ void cfl_body(const CflArgs &a, const int bid, const int nb)
 {
     const long long nx = a.n[0], ny = a.n[1], nz = a.n[2];
     const long long ncell = nx * ny * nz;
     double best = INFINITY;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ncell;
-         i += (long long)gridDim.x * blockDim.x) {
+    for (long long i = (long long)bid * blockDim.x + threadIdx.x; i < ncell;
+         i += (long long)nb * blockDim.x) {
         const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / (nx * ny));
         const double x = a.c[0][ix + GH], y = a.c[1][iy + GH], z = a.c[2][iz + GH];
         if (a.r_inner > 0.0 && x * x + y * y + z * z < a.r_inner * a.r_inner) continue;
@@ -91,16 +92,16 @@ __global__ void __launch_bounds__(CFL_THREADS) cfl_kernel(CflArgs a)
     best = block_min(best);
     __shared__ bool last;
     if (threadIdx.x == 0) {
-        a.partial[blockIdx.x] = best;
+        a.partial[bid] = best;
         __threadfence();
         unsigned int ticket = atomicAdd(a.counter, 1u);
-        last = (ticket == gridDim.x - 1);
+        last = (ticket == (unsigned int)nb - 1u);
     }
     __syncthreads();
     if (last) {
         __threadfence();
         double m = INFINITY;
-        for (int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
             double v = __ldcg(a.partial + b);
             m = v < m ? v : m;
         }
@@ -112,9 +113,30 @@ __global__ void __launch_bounds__(CFL_THREADS) cfl_kernel(CflArgs a)
     }
 }
 
+__global__ void __launch_bounds__(CFL_THREADS) cfl_kernel(CflArgs a) { cfl_body(a, blockIdx.x, gridDim.x); }
+
+// Ensemble: block b works for the last instance i with first_block[i] <= b.
+__global__ void __launch_bounds__(CFL_THREADS) cfl_ensemble_kernel(EnsCflArgs e)
+{
+    const int b = blockIdx.x;
+    int lo = 0, hi = e.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (e.first_block[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    const int nb = (lo + 1 < e.count ? e.first_block[lo + 1] : (int)gridDim.x) - e.first_block[lo];
+    cfl_body(e.args[lo], b - e.first_block[lo], nb);
+}
+
 cudaError_t launch_cfl(const CflArgs &a, int blocks, cudaStream_t s)
 {
     cfl_kernel<<<blocks, CFL_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cfl_ensemble_fp64(const EnsCflArgs &e, int blocks, cudaStream_t s)
+{
+    cfl_ensemble_kernel<<<blocks, CFL_THREADS, 0, s>>>(e);
     return cudaGetLastError();
 }
 

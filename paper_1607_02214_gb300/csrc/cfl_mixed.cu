@@ -24,14 +24,14 @@ __device__ __forceinline__ float block_min_f(float v)
     return v;
 }
 
-__global__ void __launch_bounds__(CFLM_THREADS) cfl_mixed_kernel(CflArgs a)
+__device__ __forceinline__ void cfl_mixed_body(const CflArgs &a, const int bid, const int nb)
 {
     const long long nx = a.n[0], ny = a.n[1], nz = a.n[2];
     const long long ncell = nx * ny * nz;
     const float gm1 = a.gammaf - 1.0f;
     float best = INFINITY;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ncell;
-         i += (long long)gridDim.x * blockDim.x) {
+    for (long long i = (long long)bid * blockDim.x + threadIdx.x; i < ncell;
+         i += (long long)nb * blockDim.x) {
         const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / (nx * ny));
         const float x = a.cf[0][ix + GH], y = a.cf[1][iy + GH], z = a.cf[2][iz + GH];
         if (a.r_innerf > 0.0f) {
@@ -65,16 +65,16 @@ __global__ void __launch_bounds__(CFLM_THREADS) cfl_mixed_kernel(CflArgs a)
     best = block_min_f(best);
     __shared__ bool last;
     if (threadIdx.x == 0) {
-        a.partial[blockIdx.x] = widen(best);
+        a.partial[bid] = widen(best);
         __threadfence();
         unsigned int ticket = atomicAdd(a.counter, 1u);
-        last = (ticket == gridDim.x - 1);
+        last = (ticket == (unsigned int)nb - 1u);
     }
     __syncthreads();
     if (last) {
         __threadfence();
         double m = INFINITY;
-        for (int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
             double v = __ldcg(a.partial + b);
             m = v < m ? v : m;
         }
@@ -86,9 +86,29 @@ __global__ void __launch_bounds__(CFLM_THREADS) cfl_mixed_kernel(CflArgs a)
     }
 }
 
+__global__ void __launch_bounds__(CFLM_THREADS) cfl_mixed_kernel(CflArgs a) { cfl_mixed_body(a, blockIdx.x, gridDim.x); }
+
+__global__ void __launch_bounds__(CFLM_THREADS) cfl_mixed_ensemble_kernel(EnsCflArgs e)
+{
+    const int b = blockIdx.x;
+    int lo = 0, hi = e.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (e.first_block[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    const int nb = (lo + 1 < e.count ? e.first_block[lo + 1] : (int)gridDim.x) - e.first_block[lo];
+    cfl_mixed_body(e.args[lo], b - e.first_block[lo], nb);
+}
+
 cudaError_t launch_cfl_mixed(const CflArgs &a, int blocks, cudaStream_t s)
 {
     cfl_mixed_kernel<<<blocks, CFLM_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cfl_ensemble_mixed(const EnsCflArgs &e, int blocks, cudaStream_t s)
+{
+    cfl_mixed_ensemble_kernel<<<blocks, CFLM_THREADS, 0, s>>>(e);
     return cudaGetLastError();
 }
 

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/ppmlr.h"
 
@@ -11,14 +12,16 @@ namespace ppmlr {
 
 constexpr int GH = 7;          // ghost cells per pencil end: the stencil radius of one sweep
 constexpr int NSM = 28;        // shared-memory exchange arrays per tile (see sweep.cuh)
-constexpr int MAXT = 512;      // threads per tile (one thread per cell position and lane)
+constexpr int MAXT = 512;      // threads per tile (one thread per cell position and lane), mixed path
+constexpr int MAXT_F64 = 448;  // FP64 path: fewer threads, up to 146 registers each
 
 enum : int { FLAG_CFL = 1, FLAG_NONFINITE = 2 };
 
 // Arguments of one sweep launch (passed by value).
 struct SweepArgs {
-    const double *U[8];        // input state, 8 SoA arrays
-    double *Un[8];             // output state
+    const double *U;           // input state: array v at U + v * vs
+    double *Un;                // output state: array v at Un + v * vs
+    long long vs;              // element stride between the 8 arrays of a state
     int n[3];                  // nx, ny, nz
     int N;                     // cells along the sweep axis
     int C;                     // output cells per chunk along the axis
@@ -45,6 +48,28 @@ struct SweepArgs {
     float inflowf[8];
 };
 
+// Persistent ensemble sweep: per-instance arguments (input state = U, output
+// = Un; flip = 1 swaps them), the first global tile of every instance and a
+// work counter that must be zero at launch.
+struct EnsSweepArgs {
+    const SweepArgs *__restrict__ args;   // device array, one entry per instance (this direction)
+    const int *first_tile;     // device array, count entries, ascending
+    int count;
+    int total_tiles;
+    int flip;
+    unsigned int *queue;
+};
+
+// Ensembles of up to ENS_PARAM_MAX instances also travel as one by-value
+// kernel parameter (constant bank) for the one-block-per-tile launch form.
+constexpr int ENS_PARAM_MAX = 64;
+struct EnsSweepParams {
+    SweepArgs args[ENS_PARAM_MAX];
+    int first_tile[ENS_PARAM_MAX];
+    int count;
+    int flip;
+};
+
 struct CflArgs {
     const double *U[8];
     int n[3];
@@ -66,11 +91,35 @@ struct Tile {
     size_t smem;
 };
 
+// host helpers shared by the single-domain and ensemble code (api.cu)
+void build_axis(int n, const double *edges, int bc_lo, int bc_hi, std::vector<double> &w, std::vector<double> &ce);
+Tile choose_tile(int dir, const int n[3], size_t real_size);
+Tile make_tile(int dir, const int n[3], size_t real_size, int C, int L);   // C cells per chunk, L lanes
+bool validate_grid_bc(const ppmlr_grid *grid, const ppmlr_bc *bc);
+
 // launchers (defined in the kernel translation units)
 cudaError_t launch_sweep_fp64(int dir, const SweepArgs &a, const Tile &t, cudaStream_t s);
 cudaError_t launch_sweep_mixed(int dir, const SweepArgs &a, const Tile &t, cudaStream_t s);
 cudaError_t launch_cfl(const CflArgs &a, int blocks, cudaStream_t s);
 cudaError_t launch_cfl_mixed(const CflArgs &a, int blocks, cudaStream_t s);
+cudaError_t launch_sweep_ensemble_fp64(int dir, const EnsSweepArgs &e, int blocks, int threads, size_t smem,
+                                       cudaStream_t s);
+cudaError_t launch_sweep_ensemble_mixed(int dir, const EnsSweepArgs &e, int blocks, int threads, size_t smem,
+                                        cudaStream_t s);
+cudaError_t launch_sweep_ensemble_param_fp64(int dir, const EnsSweepParams &p, int blocks, int threads,
+                                             size_t smem, cudaStream_t s);
+cudaError_t launch_sweep_ensemble_param_mixed(int dir, const EnsSweepParams &p, int blocks, int threads,
+                                              size_t smem, cudaStream_t s);
+// Ensemble CFL: block b belongs to the last instance i with first_block[i] <= b.
+struct EnsCflArgs {
+    const CflArgs *args;       // device array, one entry per instance
+    const int *first_block;
+    int count;
+};
+cudaError_t launch_cfl_ensemble_fp64(const EnsCflArgs &e, int blocks, cudaStream_t s);
+cudaError_t launch_cfl_ensemble_mixed(const EnsCflArgs &e, int blocks, cudaStream_t s);
+int sweep_blocks_per_sm_fp64(int dir, int threads, size_t smem);
+int sweep_blocks_per_sm_mixed(int dir, int threads, size_t smem);
 int cfl_threads();
 
 }  // namespace ppmlr

@@ -159,12 +159,19 @@ enum : int {
     SB0 = 13, SC0 = 21
 };
 
-template <int DIR, typename R>
-__global__ void __launch_bounds__(MAXT) sweep_kernel(SweepArgs a)
+// One tile of one sweep, processed by the calling block.  `a` describes the
+// domain (the single-domain kernel passes its launch argument, the ensemble
+// kernel a per-instance copy in shared memory); `tile` is the tile index
+// within that domain; `smem_raw` holds NSM * NP * L values of type R.
+template <int DIR, typename R, typename ARGS>
+__device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned char *smem_raw, const int flip)
 {
+    // input and output state (flip = 1 exchanges them); array v at base + v * vs
+    const double *Uin = flip ? a.Un : a.U;
+    double *Uout = flip ? const_cast<double *>(a.U) : a.Un;
+    const long long vs = a.vs;
     constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
     constexpr bool F64 = std::is_same<R, double>::value;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sm = reinterpret_cast<R *>(smem_raw);
     const int L = a.L, NP = a.NP, NT = NP * L;
     const int PS = DIR == 0 ? 1 : L;
@@ -172,8 +179,8 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(SweepArgs a)
 #define SM(k, slot) sm[(k) * NT + (slot)]
 
     // ---- tile decode ----
-    const int chunk = blockIdx.x % a.nchunk;
-    const int grp = blockIdx.x / a.nchunk;
+    const int chunk = tile % a.nchunk;
+    const int grp = tile / a.nchunk;
     int p, l;
     if (DIR == 0) { l = s / NP; p = s - l * NP; }
     else { p = s / L; l = s - p * L; }
@@ -227,7 +234,7 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(SweepArgs a)
             else if (kind == PPMLR_BC_OUTFLOW) src = g < 0 ? 0 : a.N - 1;
             else {
                 fixed = true;
-                const double *f = a.inflow;
+                const auto *f = a.inflow;
                 double Bp0 = f[4] - Bdg[0], Bp1 = f[5] - Bdg[1], Bp2 = f[6] - Bdg[2];
                 double rh = f[0];
                 Uc[0] = rh;
@@ -240,7 +247,7 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(SweepArgs a)
         if (!fixed) {
             const long long gi = base + (long long)src * stride;
 #pragma unroll
-            for (int v = 0; v < 8; v++) Uc[v] = __ldg(a.U[v] + gi);
+            for (int v = 0; v < 8; v++) Uc[v] = __ldg(Uin + v * vs + gi);
         }
         double rd = Uc[0];
         double mn = Uc[1 + DIR], m1 = Uc[1 + T1], m2 = Uc[1 + T2];
@@ -274,7 +281,7 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(SweepArgs a)
         }
         const float gm1 = a.gammaf - 1.0f;
         if (fixed) {
-            const float *f = a.inflowf;
+            const auto *f = a.inflowf;
             rho = f[0];
             u = f[1 + DIR]; v1 = f[1 + T1]; v2 = f[1 + T2];
             Bn = f[4 + DIR] - Bd0; B1 = f[4 + T1] - Bd1; B2 = f[4 + T2] - Bd2;
@@ -284,7 +291,7 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(SweepArgs a)
             const long long gi = base + (long long)src * stride;
             df q[8];
 #pragma unroll
-            for (int v = 0; v < 8; v++) q[v] = split_double(__ldg(a.U[v] + gi));
+            for (int v = 0; v < 8; v++) q[v] = split_double(__ldg(Uin + v * vs + gi));
             float prf = pressure_df(q[0], q[1 + DIR], q[1 + T1], q[1 + T2], q[4 + DIR], q[4 + T1], q[4 + T2],
                                     q[7], gm1);
             rho = q[0].h;
@@ -540,7 +547,7 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(SweepArgs a)
         const long long gi = base + (long long)g * stride;
         double Un[8];
 #pragma unroll
-        for (int v = 0; v < 8; v++) Un[v] = __ldg(a.U[v] + gi);
+        for (int v = 0; v < 8; v++) Un[v] = __ldg(Uin + v * vs + gi);
         const int cmap[7] = {0, 1 + DIR, 1 + T1, 1 + T2, 4 + T1, 4 + T2, 7};
         const R dCv[7] = {R(0), dC[0], dC[1], dC[2], dC[3], dC[4], dC[5]};
         if constexpr (F64) {
@@ -589,7 +596,7 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(SweepArgs a)
             }
         }
         if (inner) {
-            const double *q = a.inner;
+            const auto *q = a.inner;
             double rh = q[0];
             Un[0] = rh;
             Un[1] = rh * q[1]; Un[2] = rh * q[2]; Un[3] = rh * q[3];
@@ -601,11 +608,99 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(SweepArgs a)
 #pragma unroll
         for (int v = 0; v < 8; v++) {   // non-finite test on the exponent bits (integer pipe)
             bad |= ((__double2hiint(Un[v]) >> 20) & 0x7FF) == 0x7FF;
-            a.Un[v][gi] = Un[v];
+            Uout[v * vs + gi] = Un[v];
         }
         if (bad) atomicOr(a.flags, FLAG_NONFINITE);
     }
 #undef SM
+}
+
+template <typename R> struct MaxThreads { static constexpr int value = MAXT; };
+template <> struct MaxThreads<double> { static constexpr int value = MAXT_F64; };
+
+// Single domain: one block per tile.
+template <int DIR, typename R>
+__global__ void __launch_bounds__(MaxThreads<R>::value) sweep_kernel(SweepArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    sweep_tile<DIR, R, const SweepArgs>(a, blockIdx.x, smem_raw, 0);
+}
+
+// Ensemble: a persistent kernel.  Each block repeatedly takes the next tile
+// from a global work counter (one atomic per tile, no waiting), finds the
+// instance that owns it from the per-instance first-tile table and processes
+// the tile with that instance's arguments (read-only device table).
+// Instances of different sizes and boundary data share the launch.
+template <int DIR, typename R>
+__global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_kernel(EnsSweepArgs e)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ SweepArgs args;
+    __shared__ int next, inst_cur;
+    if (threadIdx.x == 0) inst_cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) next = (int)atomicAdd(e.queue, 1u);
+        __syncthreads();
+        const int t = next;
+        const int cur = inst_cur;
+        __syncthreads();
+        if (t >= e.total_tiles) break;
+        // instance owning tile t: last i with first_tile[i] <= t
+        int lo = 0, hi = e.count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(e.first_tile + mid) <= t) lo = mid; else hi = mid - 1;
+        }
+        if (lo != cur) {   // uniform across the block
+            const int *src = reinterpret_cast<const int *>(e.args + lo);
+            int *dst = reinterpret_cast<int *>(&args);
+            for (int k = threadIdx.x; k < (int)(sizeof(SweepArgs) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
+            if (threadIdx.x == 0) inst_cur = lo;
+            __syncthreads();
+        }
+        // read through a volatile view: each use is a shared-memory load
+        // rather than a register held across the tile's phases
+        const volatile SweepArgs &va = args;
+        sweep_tile<DIR, R, const volatile SweepArgs>(va, t - __ldg(e.first_tile + lo), smem_raw, e.flip);
+        __syncthreads();
+    }
+}
+
+// Ensemble, one block per tile: the block scheduler hands out (instance,
+// tile) items in order; the block finds its instance from the first-tile
+// table and copies that instance's arguments to shared memory.
+template <int DIR, typename R>
+__global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_grid_kernel(EnsSweepArgs e)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ SweepArgs args;
+    const int t = blockIdx.x;
+    int lo = 0, hi = e.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(e.first_tile + mid) <= t) lo = mid; else hi = mid - 1;
+    }
+    const int *src = reinterpret_cast<const int *>(e.args + lo);
+    int *dst = reinterpret_cast<int *>(&args);
+    for (int k = threadIdx.x; k < (int)(sizeof(SweepArgs) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+    sweep_tile<DIR, R, const SweepArgs>(args, t - __ldg(e.first_tile + lo), smem_raw, e.flip);
+}
+
+// Ensemble, one block per tile, arguments of all instances in the kernel
+// parameter (constant bank): the block finds its instance from the first-tile
+// table and reads that instance's fields straight from the parameter space.
+template <int DIR, typename R>
+__global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_param_kernel(const __grid_constant__ EnsSweepParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int t = blockIdx.x;
+    int lo = 0, hi = p.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.first_tile[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    sweep_tile<DIR, R, const SweepArgs>(p.args[lo], t - p.first_tile[lo], smem_raw, p.flip);
 }
 
 }  // namespace ppmlr

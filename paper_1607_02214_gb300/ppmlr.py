@@ -57,6 +57,23 @@ SIGNATURES = [
     ("ppmlr_launch_count", c_longlong, [c_void_p]),
     ("ppmlr_enable_timing", c_int, [c_void_p, c_int]),
     ("ppmlr_read_timing", c_int, [c_void_p, POINTER(c_double), POINTER(c_longlong)]),
+    ("ppmlr_autotune", c_int, [c_void_p, POINTER(c_double)]),
+    ("ppmlr_get_tiles", c_int, [c_void_p, POINTER(c_int), POINTER(c_int)]),
+    ("ppmlr_ensemble_create", c_int, [c_int, POINTER(ppmlr_grid), POINTER(ppmlr_bc), c_double, c_int, c_void_p,
+                                      POINTER(c_void_p)]),
+    ("ppmlr_ensemble_set_stream", c_int, [c_void_p, c_void_p]),
+    ("ppmlr_ensemble_set_state", c_int, [c_void_p, c_int, DPTR8, c_int]),
+    ("ppmlr_ensemble_get_state", c_int, [c_void_p, c_int, DPTR8, c_int]),
+    ("ppmlr_ensemble_step", c_int, [c_void_p, c_double, c_int]),
+    ("ppmlr_ensemble_time_kernels", c_int, [c_void_p, c_double, c_int, POINTER(c_double)]),
+    ("ppmlr_ensemble_autotune", c_int, [c_void_p, POINTER(c_double)]),
+    ("ppmlr_ensemble_get_tiles", c_int, [c_void_p, POINTER(c_int)]),
+    ("ppmlr_ensemble_get_dt", c_int, [c_void_p, POINTER(c_double)]),
+    ("ppmlr_ensemble_check", c_int, [c_void_p]),
+    ("ppmlr_ensemble_get_diagnostics", c_int, [c_void_p, POINTER(c_longlong), POINTER(c_longlong)]),
+    ("ppmlr_ensemble_last_error", ctypes.c_char_p, [c_void_p]),
+    ("ppmlr_ensemble_launch_count", c_longlong, [c_void_p]),
+    ("ppmlr_ensemble_destroy", None, [c_void_p]),
     ("ppmlr_cfl_dt_noalloc", c_int, [DPTR8, POINTER(c_int), POINTER(c_double) * 3, POINTER(c_double) * 3,
                                      c_double, c_double, c_double, c_double, c_double, c_int, POINTER(c_double),
                                      c_void_p]),
@@ -255,3 +272,113 @@ class Context:
 
     def set_stream(self, stream):
         return self._check(load().ppmlr_set_stream(self._h, _stream_handle(stream)))
+
+    def autotune(self):
+        ms = (c_double * 3)()
+        self._check(load().ppmlr_autotune(self._h, ms))
+        return list(ms)
+
+    def tiles(self):
+        C, L = (c_int * 3)(), (c_int * 3)()
+        self._check(load().ppmlr_get_tiles(self._h, C, L))
+        return list(C), list(L)
+
+
+class Ensemble:
+    """count independent instances (own grid and boundary spec each) advanced
+    together: per-instance device dt, one persistent launch per sweep, one
+    CUDA graph per step."""
+
+    def __init__(self, problems_or_specs, gamma=None, precision=PPMLR_MIXED, stream=None):
+        L = load()
+        items = list(problems_or_specs)
+        self.count = len(items)
+        self._edges, grids, bcs = [], (ppmlr_grid * self.count)(), (ppmlr_bc * self.count)()
+        self.n = []
+        for i, it in enumerate(items):
+            edges, spec = (it.edges, it.bc) if hasattr(it, "edges") else it
+            ee = [np.ascontiguousarray(e, dtype=np.float64) for e in edges]
+            self._edges.append(ee)
+            self.n.append(tuple(len(e) - 1 for e in ee))
+            for d in range(3):
+                grids[i].n[d] = self.n[i][d]
+                grids[i].edges[d] = ee[d].ctypes.data_as(POINTER(c_double))
+            bcs[i] = make_bc(spec)
+        if gamma is None:
+            gamma = items[0].gamma
+        h = c_void_p()
+        st = L.ppmlr_ensemble_create(self.count, grids, bcs, float(gamma), int(precision), _stream_handle(stream),
+                                     ctypes.byref(h))
+        if st != PPMLR_OK:
+            raise PPMLRError(st, "ppmlr_ensemble_create failed")
+        self._h = h
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ppmlr_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != PPMLR_OK:
+            raise PPMLRError(st, load().ppmlr_ensemble_last_error(self._h).decode())
+        return st
+
+    def shape(self, i):
+        n = self.n[i]
+        return (8, n[2], n[1], n[0])
+
+    def set_state(self, i, U):
+        if not hasattr(U, "data_ptr"):
+            U = np.ascontiguousarray(U, dtype=np.float64)
+        assert tuple(U.shape) == self.shape(i)
+        p, dev = Context._ptrs(U)
+        return self._check(load().ppmlr_ensemble_set_state(self._h, int(i), p, dev))
+
+    def get_state(self, i, out=None):
+        if out is None:
+            out = np.empty(self.shape(i), dtype=np.float64)
+        p, dev = Context._ptrs(out)
+        self._check(load().ppmlr_ensemble_get_state(self._h, int(i), p, dev))
+        return out
+
+    def step(self, cfl, nsteps=1):
+        return self._check(load().ppmlr_ensemble_step(self._h, float(cfl), int(nsteps)))
+
+    def time_kernels(self, cfl, nsteps):
+        ms = (c_double * 4)()
+        self._check(load().ppmlr_ensemble_time_kernels(self._h, float(cfl), int(nsteps), ms))
+        return dict(zip(("x", "y", "z", "cfl"), list(ms)))
+
+    def autotune(self):
+        ms = (c_double * 3)()
+        self._check(load().ppmlr_ensemble_autotune(self._h, ms))
+        return list(ms)
+
+    def tiles(self):
+        t = (c_int * 3)()
+        self._check(load().ppmlr_ensemble_get_tiles(self._h, t))
+        return list(t)
+
+    def dt(self):
+        out = (c_double * self.count)()
+        self._check(load().ppmlr_ensemble_get_dt(self._h, out))
+        return list(out)
+
+    def check(self):
+        return self._check(load().ppmlr_ensemble_check(self._h))
+
+    def diagnostics(self):
+        s, f = c_longlong(), c_longlong()
+        self._check(load().ppmlr_ensemble_get_diagnostics(self._h, ctypes.byref(s), ctypes.byref(f)))
+        return {"step": s.value, "floor_hits": f.value}
+
+    @property
+    def launch_count(self):
+        return load().ppmlr_ensemble_launch_count(self._h)

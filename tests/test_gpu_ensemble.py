@@ -1,0 +1,94 @@
+"""Batched ensemble and autotuners on the GPU.
+
+Every ensemble instance must evolve bit for bit like a single context
+advanced with ppmlr_step_cfl from the same state (the same per-cell
+arithmetic, per-instance device dt); graph replay must equal direct launches;
+tuned tile shapes must not change any result.  FP64 instances also match the
+oracle."""
+import numpy as np
+import pytest
+
+from gpu_util import make_oracle, rel_l1
+from paper_1607_02214_gb300 import inputs, ppmlr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1607_02214_gb300 import build
+    build.build()
+
+
+def small_ensemble(seed=7):
+    rng = np.random.default_rng(seed)
+    shapes = [(40, 32, 32), (48, 32, 28), (36, 30, 30), (44, 34, 26), (40, 28, 36)]
+    out = []
+    for i, n in enumerate(shapes):
+        out.append(inputs.magnetosphere(n=n, h0=1.0, n_cc=float(rng.uniform(2, 20)),
+                                        vx_kms=float(rng.uniform(-800, -300)), bz_nt=float(rng.uniform(-10, 10)),
+                                        name=f"m{i}"))
+    return out
+
+
+@pytest.mark.parametrize("precision", [ppmlr.PPMLR_MIXED, ppmlr.PPMLR_FP64])
+def test_ensemble_equals_independent_contexts(precision):
+    probs = small_ensemble()
+    ens = ppmlr.Ensemble(probs, precision=precision)
+    for i, p in enumerate(probs):
+        ens.set_state(i, p.U0)
+    nsteps = 5
+    ens.step(0.4, nsteps)
+    ens.check()
+    dts = ens.dt()
+    for i, p in enumerate(probs):
+        ctx = ppmlr.Context.from_problem(p, precision)
+        ctx.set_state(p.U0)
+        ctx.step_cfl(0.4, nsteps)
+        assert np.array_equal(ens.get_state(i), ctx.get_state()), i
+        assert dts[i] == ctx.last_dt()
+    assert ens.diagnostics()["step"] == nsteps
+
+
+def test_ensemble_graph_equals_direct_launches_and_autotune_is_neutral():
+    probs = small_ensemble(11)
+    a = ppmlr.Ensemble(probs, precision=ppmlr.PPMLR_MIXED)
+    b = ppmlr.Ensemble(probs, precision=ppmlr.PPMLR_MIXED)
+    for i, p in enumerate(probs):
+        a.set_state(i, p.U0)
+        b.set_state(i, p.U0)
+    b.autotune()
+    a.step(0.4, 4)                     # graph replay
+    ms = b.time_kernels(0.4, 4)        # direct launches, tuned tiles
+    assert all(v > 0 for v in ms.values())
+    for i in range(len(probs)):
+        assert np.array_equal(a.get_state(i), b.get_state(i)), i
+
+
+def test_ensemble_fp64_instance_matches_oracle():
+    probs = small_ensemble(3)[:2]
+    ens = ppmlr.Ensemble(probs, precision=ppmlr.PPMLR_FP64)
+    for i, p in enumerate(probs):
+        ens.set_state(i, p.U0)
+    ens.step(0.4, 3)
+    for i, p in enumerate(probs):
+        o = make_oracle(p)
+        for _ in range(3):
+            assert o.step(o.cfl_dt(0.4)) == 0
+        err = rel_l1(ens.get_state(i), o.get_state())
+        assert np.max(err) <= 1e-11, err
+
+
+@pytest.mark.parametrize("precision", [ppmlr.PPMLR_FP64, ppmlr.PPMLR_MIXED])
+def test_autotune_changes_speed_not_results(precision):
+    p = inputs.magnetosphere(n=(56, 44, 40), h0=1.0)
+    a = ppmlr.Context.from_problem(p, precision)
+    b = ppmlr.Context.from_problem(p, precision)
+    a.set_state(p.U0)
+    b.set_state(p.U0)
+    ms = b.autotune()
+    assert all(m > 0 for m in ms)
+    a.step_cfl(0.4, 3)
+    b.step_cfl(0.4, 3)
+    assert np.array_equal(a.get_state(), b.get_state())
+    assert a.diagnostics()["floor_hits"] == b.diagnostics()["floor_hits"]
