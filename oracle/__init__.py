@@ -48,6 +48,9 @@ def lib():
         L.orc_step_count.restype = ctypes.c_longlong
         L.orc_step_count.argtypes = [ctypes.c_void_p]
         L.orc_set_step_count.argtypes = [ctypes.c_void_p, ctypes.c_longlong]
+        L.orc_sweep_sampled.restype = ctypes.c_int
+        L.orc_sweep_sampled.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dp]
         L.orc_set_threads.restype = ctypes.c_int
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_dipole.argtypes = [ctypes.c_double] * 4 + [_dp]
@@ -119,6 +122,17 @@ class Oracle:
 
     def sweep(self, axis, dt):
         return lib().orc_sweep(self._h, int(axis), float(dt))
+
+    def sweep_sampled(self, axis, dt, j, k):
+        """One sweep of the listed pencils only (state unchanged); returns
+        (npencil, 8, n[axis]) and the flags."""
+        j = np.ascontiguousarray(j, dtype=np.int32)
+        k = np.ascontiguousarray(k, dtype=np.int32)
+        out = np.empty((len(j), 8, self.n[axis]))
+        ip = ctypes.POINTER(ctypes.c_int)
+        fl = lib().orc_sweep_sampled(self._h, int(axis), float(dt), len(j), j.ctypes.data_as(ip),
+                                     k.ctypes.data_as(ip), _ptr(out))
+        return out, fl
 
     @property
     def floor_hits(self):

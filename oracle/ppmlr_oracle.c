@@ -658,6 +658,38 @@ int orc_sweep(orc_ctx *c, int d, double dt)
     return flags;
 }
 
+/* One sweep of only the listed pencils (j[p], k[p]: the two transverse
+ * indices in increasing axis order), for sampled comparisons on grids too
+ * large to sweep whole.  The state is not modified; out receives, per pencil,
+ * the 8 conserved arrays of its n[axis] cells ([pencil][var][cell]). */
+int orc_sweep_sampled(orc_ctx *c, int d, double dt, int npencil, const int *j, const int *k, double *out)
+{
+    const int N = c->n[d];
+    long long floors = 0;
+    int flags = 0;
+    if (sweep_is_noop(c, d)) {
+        for (int q = 0; q < npencil; q++)
+            for (int v = 0; v < NVAR; v++)
+                for (int i = 0; i < N; i++)
+                    out[((size_t)q * NVAR + v) * N + i] = c->U[(size_t)v * ncell(c) + gidx(c, d, i, j[q], k[q])];
+        return 0;
+    }
+#pragma omp parallel reduction(+ : floors) reduction(| : flags)
+    {
+        pencil_buf b;
+        pb_alloc(&b, N + 2 * G);
+#pragma omp for schedule(static)
+        for (int q = 0; q < npencil; q++) {
+            sweep_pencil(c, d, j[q], k[q], dt, &b, &floors, &flags);
+            for (int v = 0; v < NVAR; v++)
+                for (int i = 0; i < N; i++)
+                    out[((size_t)q * NVAR + v) * N + i] = c->Unew[(size_t)v * ncell(c) + gidx(c, d, i, j[q], k[q])];
+        }
+        pb_free(&b);
+    }
+    return flags;
+}
+
 /* One full step [R: sweep order alternates x,y,z / z,y,x with step parity]. */
 int orc_step(orc_ctx *c, double dt)
 {

@@ -1,0 +1,120 @@
+"""Parity at the full benchmark sizes, in the launch configuration bench.py
+times (autotuned tiles, device CFL dt, graph replay for the ensemble).
+
+* magnetosphere 256x192x192, FP64: whole state after 10 steps vs the oracle
+  (relative L1 <= 1e-11 per variable; the kernels are expected bit-exact);
+* the same grid, mixed: whole state after 50 steps vs the oracle (<= 1e-5);
+* 48-instance ensemble (mixed): one instance of each grid shape vs the oracle;
+* 512x384x384: sampled pencils of one sweep along each axis vs the oracle's
+  sampled sweep (FP64 <= 1e-11, mixed <= 1e-5).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import make_oracle, rel_l1
+from paper_1607_02214_gb300 import inputs, ppmlr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1607_02214_gb300 import build
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def c2_reference():
+    """Oracle states of the 256x192x192 magnetosphere after 10 and 50 steps."""
+    oracle.set_threads(0)
+    pr = inputs.magnetosphere(n=(256, 192, 192), h0=0.4)
+    o = make_oracle(pr)
+    snaps = {}
+    for k in range(1, 51):
+        assert o.step(o.cfl_dt(pr.cfl)) == 0
+        if k in (10, 50):
+            snaps[k] = o.get_state()
+    return pr, snaps
+
+
+def gpu_run(pr, precision, nsteps):
+    import torch
+    ctx = ppmlr.Context.from_problem(pr, precision)
+    U0 = torch.from_numpy(pr.U0).cuda()
+    ctx.set_state(U0)
+    ctx.autotune()
+    ctx.step_cfl(pr.cfl, nsteps)
+    out = torch.empty_like(U0)
+    ctx.get_state(out)
+    return out.cpu().numpy()
+
+
+def test_c2_fp64_10_steps(c2_reference):
+    pr, snaps = c2_reference
+    err = rel_l1(gpu_run(pr, ppmlr.PPMLR_FP64, 10), snaps[10])
+    assert np.max(err) <= 1e-11, err
+
+
+def test_c2_mixed_50_steps(c2_reference):
+    pr, snaps = c2_reference
+    err = rel_l1(gpu_run(pr, ppmlr.PPMLR_MIXED, 50), snaps[50])
+    print("mixed vs oracle after 50 steps, rel L1 per variable:", err)
+    assert np.max(err) <= 1e-5, err
+
+
+def test_ensemble_48_sampled_instances():
+    probs = inputs.ensemble(48)
+    ens = ppmlr.Ensemble(probs, precision=ppmlr.PPMLR_MIXED)
+    for i, p in enumerate(probs):
+        ens.set_state(i, p.U0)
+    ens.autotune()
+    nsteps = 5
+    ens.step(0.4, nsteps)
+    ens.check()
+    picked = {}
+    for i, p in enumerate(probs):
+        picked.setdefault(p.n, i)
+    for shape, i in picked.items():
+        o = make_oracle(probs[i])
+        for _ in range(nsteps):
+            assert o.step(o.cfl_dt(0.4)) == 0
+        err = rel_l1(ens.get_state(i), o.get_state())
+        assert np.max(err) <= 1e-5, (shape, err)
+
+
+@pytest.mark.parametrize("precision,tol", [(ppmlr.PPMLR_FP64, 1e-11), (ppmlr.PPMLR_MIXED, 1e-5)])
+def test_c5_sampled_pencils_one_sweep_per_axis(precision, tol):
+    import torch
+    oracle.set_threads(0)
+    pr = inputs.magnetosphere(n=(512, 384, 384), h0=0.2)
+    o = make_oracle(pr)
+    dt = o.cfl_dt(pr.cfl)
+    U0 = torch.from_numpy(pr.U0).cuda()
+    ctx = ppmlr.Context.from_problem(pr, precision)
+    ctx.set_state(U0)
+    ctx.autotune()
+    rng = np.random.default_rng(2)
+    out = torch.empty_like(U0)
+    for axis in range(3):
+        ctx.set_state(U0)
+        ctx.sweep(axis, dt)
+        ctx.get_state(out)
+        a1, a2 = [d for d in range(3) if d != axis]
+        j = rng.integers(0, pr.n[a1], size=24)
+        k = rng.integers(0, pr.n[a2], size=24)
+        # include pencils through the inner sphere and near the inflow face
+        j[0], k[0] = pr.n[a1] // 2, pr.n[a2] // 2
+        ref, fl = o.sweep_sampled(axis, dt, j, k)
+        assert fl == 0
+        got = np.empty_like(ref)
+        for q in range(len(j)):
+            idx = [slice(None)] * 3
+            idx[2 - a1] = int(j[q])
+            idx[2 - a2] = int(k[q])
+            got[q] = out[(slice(None),) + tuple(idx)].cpu().numpy()
+        d = np.abs(got - ref).sum(axis=(0, 2))
+        s = np.abs(ref).sum(axis=(0, 2))
+        grp = np.array([s[0], *[s[1:4].sum()] * 3, *[s[4:7].sum()] * 3, s[7]])
+        err = d / grp
+        assert np.max(err) <= tol, (axis, err)
