@@ -328,6 +328,16 @@ def run_ours(args, rank, world, dist):
                                         "rel_l1": dict(zip(names, l1)), "linf": dict(zip(names, linf))}}
         del a, b, octx, ua, ub
 
+    # ---- the bit-exact FP64 form (same expression trees as the CPU reference)
+    if not args.quick and args.precision == "fp64":
+        xctx, xms, xkern, _, _ = timed_run(ppmlr.PPMLR_FP64_EXACT, max(3, args.steps // 2), args.warmup)
+        xms = max_over_ranks(xms)
+        nx = max(3, args.steps // 2)
+        extra["fp64_exact"] = {"value": world * cells * nx / (xms * 1e-3), "ms_per_step": xms / nx,
+                               "kernels_avg_ms": {k: v[0] / max(v[1], 1) for k, v in xkern.items()},
+                               "note": "bit-identical to the CPU reference"}
+        xctx.close()
+
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.quick:

@@ -44,9 +44,12 @@ typedef enum {
 } ppmlr_status;
 
 typedef enum {
-    PPMLR_FP64 = 0,         /* every stage in IEEE double, no fused multiply-add */
-    PPMLR_MIXED = 1         /* FP32 reconstruction, Riemann, remap and sources; FP64 pressure
-                               recovery and FP64 state accumulation */
+    PPMLR_FP64 = 0,         /* every stage in IEEE double; fused multiply-add and one reciprocal
+                               per shared denominator (agrees with the CPU reference to roundoff) */
+    PPMLR_MIXED = 1,        /* FP32 reconstruction, Riemann, remap and sources; pressure recovered
+                               in double-float arithmetic; FP64 state accumulation */
+    PPMLR_FP64_EXACT = 2    /* every stage in IEEE double with the CPU reference's expression
+                               trees and no contraction: bit-identical to it */
 } ppmlr_precision;
 
 typedef enum { PPMLR_BC_PERIODIC = 0, PPMLR_BC_OUTFLOW = 1, PPMLR_BC_INFLOW = 2 } ppmlr_bc_kind;

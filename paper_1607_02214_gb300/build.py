@@ -1,10 +1,11 @@
 """Build the in-tree CUDA library libppmlr_gb300.so for sm_103a.
 
 Each translation unit is compiled in parallel with one -gencode target; the
-objects are linked with nvcc into a shared library next to this file.  The
-FP64 sweep, CFL and host units are compiled without floating-point
-contraction (-fmad=false, -ffp-contract=off); the mixed-precision sweep unit
-uses contraction and fast FP32 division/square root.
+objects are linked with nvcc into a shared library next to this file.  The exact
+FP64 sweep and CFL units and the host units are compiled without
+floating-point contraction (-fmad=false, -ffp-contract=off); the default FP64
+units use contraction; the mixed-precision units use contraction and fast
+FP32 division/square root.
 """
 import os
 import subprocess
@@ -23,8 +24,10 @@ UNITS = {
     "api.cu": ["-fmad=false"],
     "ensemble.cu": ["-fmad=false"],
     "cfl.cu": ["-fmad=false"],
+    "cfl_fp64.cu": ["-fmad=true"],
     "cfl_noalloc.cu": ["-fmad=false"],
-    "sweep_fp64.cu": ["-fmad=false"],
+    "sweep_fp64.cu": ["-fmad=true"],
+    "sweep_fp64_exact.cu": ["-fmad=false"],
     "sweep_mixed.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "cfl_mixed.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
 }

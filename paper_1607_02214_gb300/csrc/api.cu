@@ -206,7 +206,8 @@ ppmlr_status ppmlr_create(const ppmlr_grid *grid, double gamma, const ppmlr_bc *
     if (!out) return PPMLR_E_INVALID;
     *out = nullptr;
     if (!grid || !bc) return PPMLR_E_INVALID;
-    if (!(gamma > 1.0) || (prec != PPMLR_FP64 && prec != PPMLR_MIXED)) return PPMLR_E_INVALID;
+    if (!(gamma > 1.0) || (prec != PPMLR_FP64 && prec != PPMLR_MIXED && prec != PPMLR_FP64_EXACT))
+        return PPMLR_E_INVALID;
     if (!validate_grid_bc(grid, bc)) return PPMLR_E_INVALID;
     long long ncell = (long long)grid->n[0] * grid->n[1] * grid->n[2];
 
@@ -267,7 +268,7 @@ ppmlr_status ppmlr_create(const ppmlr_grid *grid, double gamma, const ppmlr_bc *
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) { cudaFree(c->geof); cudaFree(c->geo); cudaFree(c->state); delete c; return PPMLR_E_CUDA; }
     }
-    size_t rs = prec == PPMLR_FP64 ? sizeof(double) : sizeof(float);
+    size_t rs = prec == PPMLR_MIXED ? sizeof(float) : sizeof(double);
     for (int d = 0; d < 3; d++) c->tile[d] = choose_tile(d, c->n, rs);
     *out = c;
     return PPMLR_OK;
@@ -371,8 +372,7 @@ static ppmlr_status launch_one_sweep(ppmlr_ctx *c, int d, double dt, const doubl
     a.gammaf = (float)a.gamma; a.p_minf = (float)a.p_min; a.Mf = (float)a.M; a.r_innerf = (float)a.r_inner;
     for (int k = 0; k < 8; k++) a.inflowf[k] = (float)a.inflow[k];
     int rec = timing_begin(c, d);
-    cudaError_t e = c->prec == PPMLR_FP64 ? launch_sweep_fp64(d, a, t, c->stream)
-                                          : launch_sweep_mixed(d, a, t, c->stream);
+    cudaError_t e = sweep_launchers(c->prec).single(d, a, t, c->stream);
     timing_end(c, rec);
     if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
     c->launches++;
@@ -419,8 +419,7 @@ static ppmlr_status launch_cfl_kernel(ppmlr_ctx *c, double cfl)
     for (int d = 0; d < 3; d++) { a.wf[d] = c->wf[d]; a.cf[d] = c->cf[d]; }
     a.gammaf = (float)a.gamma; a.p_minf = (float)a.p_min; a.Mf = (float)a.M; a.r_innerf = (float)a.r_inner;
     int rec = timing_begin(c, 3);
-    cudaError_t e = c->prec == PPMLR_FP64 ? launch_cfl(a, c->cfl_blocks, c->stream)
-                                          : launch_cfl_mixed(a, c->cfl_blocks, c->stream);
+    cudaError_t e = cfl_launchers(c->prec).single(a, c->cfl_blocks, c->stream);
     timing_end(c, rec);
     if (e != cudaSuccess) return cuda_fail(c, e, "cfl launch");
     c->launches++;
@@ -478,8 +477,8 @@ static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune
 ppmlr_status ppmlr_autotune(ppmlr_ctx *c, double *best_ms)
 {
     if (!c) return PPMLR_E_INVALID;
-    const size_t rs = c->prec == PPMLR_FP64 ? sizeof(double) : sizeof(float);
-    const int maxt = c->prec == PPMLR_FP64 ? MAXT_F64 : MAXT;
+    const size_t rs = c->prec == PPMLR_MIXED ? sizeof(float) : sizeof(double);
+    const int maxt = c->prec == PPMLR_MIXED ? MAXT : MAXT_F64;
     unsigned long long floors_before = 0;
     CK(c, cudaMemcpyAsync(&floors_before, c->floors, sizeof(floors_before), cudaMemcpyDeviceToHost, c->stream),
        "floors copy");

@@ -1,143 +1,7 @@
-// CFL time step (the paper states no rule; the reading used here):
-//   dt = cfl * min over non-inner interior cells and axes d of
-//        dx_d / (|v_d| + max(c_f,d(B'), c_f,d(B' + B_d))).
-// Grid-stride pass, warp-shuffle and block min, then the last block to finish
-// (atomic ticket, no floating-point atomics) combines the per-block minima and
-// resets the ticket.  Compiled without contraction: the result matches the
-// CPU reference bit for bit.
-#include <math.h>
-
-#include "ppmlr_internal.h"
+// CFL kernels of the exact FP64 path (bit-identical to the CPU reference).
+#include "cfl.cuh"
 
 namespace ppmlr {
-
-constexpr int CFL_THREADS = 256;
 int cfl_threads() { return CFL_THREADS; }
-
-__device__ __forceinline__ double fast2d(double rho, double p, double Bn, double B1, double B2, double gam)
-{
-    double a2 = gam * p / rho;
-    double b2 = (Bn * Bn + B1 * B1 + B2 * B2) / rho;
-    double bn2 = Bn * Bn / rho;
-    double s = a2 + b2;
-    double disc = s * s - 4.0 * a2 * bn2;
-    if (disc < 0.0) disc = 0.0;
-    return 0.5 * (s + sqrt(disc));
-}
-
-__device__ __forceinline__ double block_min(double v)
-{
-    __shared__ double red[CFL_THREADS / 32];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        double o = __shfl_down_sync(0xffffffffu, v, off);
-        v = o < v ? o : v;
-    }
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        v = threadIdx.x < CFL_THREADS / 32 ? red[threadIdx.x] : INFINITY;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            double o = __shfl_down_sync(0xffffffffu, v, off);
-            v = o < v ? o : v;
-        }
-    }
-    return v;
-}
-
-// Block `bid` of `nb` blocks working on the domain described by `a`.
-__device__ __forceinline__ void cfl_body(const CflArgs &a, const int bid, const int nb)
-{
-    const long long nx = a.n[0], ny = a.n[1], nz = a.n[2];
-    const long long ncell = nx * ny * nz;
-    double best = INFINITY;
-    for (long long i = (long long)bid * blockDim.x + threadIdx.x; i < ncell;
-         i += (long long)nb * blockDim.x) {
-        const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / (nx * ny));
-        const double x = a.c[0][ix + GH], y = a.c[1][iy + GH], z = a.c[2][iz + GH];
-        if (a.r_inner > 0.0 && x * x + y * y + z * z < a.r_inner * a.r_inner) continue;
-        double U[8];
-#pragma unroll
-        for (int v = 0; v < 8; v++) U[v] = __ldg(a.U[v] + i);
-        double Bd[3] = {0.0, 0.0, 0.0};
-        {
-            double r2 = x * x + y * y + z * z;
-            if (a.M != 0.0 && r2 != 0.0) {
-                double r = sqrt(r2);
-                double r5 = r2 * r2 * r;
-                double mr = -z;
-                Bd[0] = a.M * (3.0 * mr * x) / r5;
-                Bd[1] = a.M * (3.0 * mr * y) / r5;
-                Bd[2] = a.M * (3.0 * mr * z + r2) / r5;
-            }
-        }
-        const int idx[3] = {ix, iy, iz};
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-            double rho = U[0];
-            double mn = U[1 + d], m1 = U[1 + t1], m2 = U[1 + t2];
-            double Bn = U[4 + d], B1 = U[4 + t1], B2 = U[4 + t2];
-            double pr = (a.gamma - 1.0) * (U[7] - 0.5 * (mn * mn + m1 * m1 + m2 * m2) / rho
-                                           - 0.5 * (Bn * Bn + B1 * B1 + B2 * B2));
-            if (pr < a.p_min) pr = a.p_min;
-            double c1 = fast2d(rho, pr, Bn, B1, B2, a.gamma);
-            double c2 = fast2d(rho, pr, Bn + Bd[d], B1 + Bd[t1], B2 + Bd[t2], a.gamma);
-            double cf = sqrt(c1 > c2 ? c1 : c2);
-            double s = a.w[d][idx[d] + GH] / (fabs(mn / rho) + cf);
-            if (s < best) best = s;
-        }
-    }
-    best = block_min(best);
-    __shared__ bool last;
-    if (threadIdx.x == 0) {
-        a.partial[bid] = best;
-        __threadfence();
-        unsigned int ticket = atomicAdd(a.counter, 1u);
-        last = (ticket == (unsigned int)nb - 1u);
-    }
-    __syncthreads();
-    if (last) {
-        __threadfence();
-        double m = INFINITY;
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-            double v = __ldcg(a.partial + b);
-            m = v < m ? v : m;
-        }
-        m = block_min(m);
-        if (threadIdx.x == 0) {
-            *a.dt_out = a.cfl * m;
-            *a.counter = 0u;
-        }
-    }
-}
-
-__global__ void __launch_bounds__(CFL_THREADS) cfl_kernel(CflArgs a) { cfl_body(a, blockIdx.x, gridDim.x); }
-
-// Ensemble: block b works for the last instance i with first_block[i] <= b.
-__global__ void __launch_bounds__(CFL_THREADS) cfl_ensemble_kernel(EnsCflArgs e)
-{
-    const int b = blockIdx.x;
-    int lo = 0, hi = e.count - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (e.first_block[mid] <= b) lo = mid; else hi = mid - 1;
-    }
-    const int nb = (lo + 1 < e.count ? e.first_block[lo + 1] : (int)gridDim.x) - e.first_block[lo];
-    cfl_body(e.args[lo], b - e.first_block[lo], nb);
-}
-
-cudaError_t launch_cfl(const CflArgs &a, int blocks, cudaStream_t s)
-{
-    cfl_kernel<<<blocks, CFL_THREADS, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_cfl_ensemble_fp64(const EnsCflArgs &e, int blocks, cudaStream_t s)
-{
-    cfl_ensemble_kernel<<<blocks, CFL_THREADS, 0, s>>>(e);
-    return cudaGetLastError();
-}
-
+const CflLaunchers k_cfl_fp64_exact = CflVariant<true>::table();
 }  // namespace ppmlr

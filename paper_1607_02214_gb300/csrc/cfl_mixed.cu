@@ -100,16 +100,18 @@ __global__ void __launch_bounds__(CFLM_THREADS) cfl_mixed_ensemble_kernel(EnsCfl
     cfl_mixed_body(e.args[lo], b - e.first_block[lo], nb);
 }
 
-cudaError_t launch_cfl_mixed(const CflArgs &a, int blocks, cudaStream_t s)
+static cudaError_t launch_single(const CflArgs &a, int blocks, cudaStream_t s)
 {
     cfl_mixed_kernel<<<blocks, CFLM_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cfl_ensemble_mixed(const EnsCflArgs &e, int blocks, cudaStream_t s)
+static cudaError_t launch_ens(const EnsCflArgs &e, int blocks, cudaStream_t s)
 {
     cfl_mixed_ensemble_kernel<<<blocks, CFLM_THREADS, 0, s>>>(e);
     return cudaGetLastError();
 }
+
+const CflLaunchers k_cfl_mixed = {launch_single, launch_ens};
 
 }  // namespace ppmlr

@@ -76,7 +76,7 @@ static ppmlr_status efail(ppmlr_ens *e, ppmlr_status s, const std::string &m)
                          std::string(what) + ": " + cudaGetErrorString(r_));                 \
     } while (0)
 
-static size_t real_size(const ppmlr_ens *e) { return e->prec == PPMLR_FP64 ? sizeof(double) : sizeof(float); }
+static size_t real_size(const ppmlr_ens *e) { return e->prec == PPMLR_MIXED ? sizeof(float) : sizeof(double); }
 
 // Tile shapes of every instance for one direction under a thread budget.
 static void plan_direction(ppmlr_ens *e, int d, int maxt, int mode)
@@ -109,7 +109,7 @@ static void plan_direction(ppmlr_ens *e, int d, int maxt, int mode)
     e->threads[d] = thr;
     e->smem[d] = sm;
     e->total_tiles[d] = total;
-    int per_sm = e->prec == PPMLR_FP64 ? sweep_blocks_per_sm_fp64(d, thr, sm) : sweep_blocks_per_sm_mixed(d, thr, sm);
+    int per_sm = sweep_launchers(e->prec).per_sm(d, thr, sm);
     int b = per_sm * e->sms;
     e->blocks[d] = (mode != 0 || b > total) ? total : b;
     if (mode == 0 && e->blocks[d] == total && total > 1) e->blocks[d] = total - 1;   // keep it persistent
@@ -168,7 +168,7 @@ static ppmlr_status upload_direction(ppmlr_ens *e, int d)
 // One ensemble sweep launch along d in the direction's launch form.
 static cudaError_t launch_dir(ppmlr_ens *e, int d, int flip, unsigned int *queue, cudaStream_t s)
 {
-    const bool f64 = e->prec == PPMLR_FP64;
+    const SweepLaunchers &L = sweep_launchers(e->prec);
     if (e->mode[d] == 2) {
         EnsSweepParams p;
         memset(&p, 0, sizeof(p));
@@ -177,12 +177,10 @@ static cudaError_t launch_dir(ppmlr_ens *e, int d, int flip, unsigned int *queue
         for (int i = 0; i < e->count; i++) { p.first_tile[i] = acc; acc += e->tiles[d][i].ntiles; }
         p.count = e->count;
         p.flip = flip;
-        return f64 ? launch_sweep_ensemble_param_fp64(d, p, e->blocks[d], e->threads[d], e->smem[d], s)
-                   : launch_sweep_ensemble_param_mixed(d, p, e->blocks[d], e->threads[d], e->smem[d], s);
+        return L.param(d, p, e->blocks[d], e->threads[d], e->smem[d], s);
     }
     EnsSweepArgs ea{e->d_args[d], e->d_first_tile[d], e->count, e->total_tiles[d], flip, queue};
-    return f64 ? launch_sweep_ensemble_fp64(d, ea, e->blocks[d], e->threads[d], e->smem[d], s)
-               : launch_sweep_ensemble_mixed(d, ea, e->blocks[d], e->threads[d], e->smem[d], s);
+    return L.ens(d, ea, e->blocks[d], e->threads[d], e->smem[d], s);
 }
 
 // Enqueue one step (parity 0: x,y,z from A; 1: z,y,x from B) on stream s.
@@ -194,8 +192,7 @@ static ppmlr_status enqueue_step(ppmlr_ens *e, int parity, double cfl, cudaStrea
     ca.first_block = e->d_first_block;
     ca.count = e->count;
     (void)cfl;   // the CFL number is part of the uploaded CflArgs tables
-    cudaError_t r = e->prec == PPMLR_FP64 ? launch_cfl_ensemble_fp64(ca, e->cfl_blocks, s)
-                                          : launch_cfl_ensemble_mixed(ca, e->cfl_blocks, s);
+    cudaError_t r = cfl_launchers(e->prec).ens(ca, e->cfl_blocks, s);
     ECK(e, r, "ensemble cfl launch");
     e->launches++;
     const int ord[2][3] = {{0, 1, 2}, {2, 1, 0}};
@@ -291,7 +288,8 @@ ppmlr_status ppmlr_ensemble_create(int count, const ppmlr_grid *grids, const ppm
 {
     if (!out) return PPMLR_E_INVALID;
     *out = nullptr;
-    if (count < 1 || !grids || !bcs || !(gamma > 1.0) || (prec != PPMLR_FP64 && prec != PPMLR_MIXED))
+    if (count < 1 || !grids || !bcs || !(gamma > 1.0) ||
+        (prec != PPMLR_FP64 && prec != PPMLR_MIXED && prec != PPMLR_FP64_EXACT))
         return PPMLR_E_INVALID;
     for (int i = 0; i < count; i++)
         if (!validate_grid_bc(&grids[i], &bcs[i])) return PPMLR_E_INVALID;
@@ -370,7 +368,7 @@ ppmlr_status ppmlr_ensemble_create(int count, const ppmlr_grid *grids, const ppm
             cudaSuccess)
         return cleanup(PPMLR_E_CUDA);
     if (cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking) != cudaSuccess) return cleanup(PPMLR_E_CUDA);
-    const int default_maxt = prec == PPMLR_FP64 ? MAXT_F64 : MAXT;
+    const int default_maxt = prec == PPMLR_MIXED ? MAXT : MAXT_F64;
     for (int d = 0; d < 3; d++) {
         plan_direction(e, d, default_maxt, count <= ENS_PARAM_MAX ? 2 : 0);
         if (upload_direction(e, d) != PPMLR_OK) return cleanup(PPMLR_E_CUDA);
@@ -496,8 +494,8 @@ ppmlr_status ppmlr_ensemble_autotune(ppmlr_ens *e, double *best_ms)
     if (!e) return PPMLR_E_INVALID;
     const int cands_mixed[] = {128, 192, 256, 320, 384, 448, 512};
     const int cands_f64[] = {128, 192, 256, 320, 384, 448};
-    const int *cands = e->prec == PPMLR_FP64 ? cands_f64 : cands_mixed;
-    const int nc = e->prec == PPMLR_FP64 ? 6 : 7;
+    const int *cands = e->prec == PPMLR_MIXED ? cands_mixed : cands_f64;
+    const int nc = e->prec == PPMLR_MIXED ? 7 : 6;
     unsigned long long floors_before = 0;
     ECK(e, cudaMemcpyAsync(&floors_before, e->floors, sizeof(floors_before), cudaMemcpyDeviceToHost, e->stream),
         "floors copy");
@@ -510,8 +508,7 @@ ppmlr_status ppmlr_ensemble_autotune(ppmlr_ens *e, double *best_ms)
         ppmlr_status st = upload_cfl(e, 0.4);
         if (st != PPMLR_OK) return st;
         EnsCflArgs ca{e->d_cfl[e->steps & 1], e->d_first_block, e->count};
-        ECK(e, e->prec == PPMLR_FP64 ? launch_cfl_ensemble_fp64(ca, e->cfl_blocks, e->stream)
-                                     : launch_cfl_ensemble_mixed(ca, e->cfl_blocks, e->stream), "cfl");
+        ECK(e, cfl_launchers(e->prec).ens(ca, e->cfl_blocks, e->stream), "cfl");
     }
     for (int d = 0; d < 3; d++) {
         float best = 1e30f;
@@ -571,8 +568,7 @@ ppmlr_status ppmlr_ensemble_time_kernels(ppmlr_ens *e, double cfl, int nsteps, d
         ECK(e, cudaMemsetAsync(e->queue, 0, 3 * sizeof(unsigned int), e->stream), "queue reset");
         EnsCflArgs ca{e->d_cfl[parity], e->d_first_block, e->count};
         ECK(e, cudaEventRecord(ev[8 * k], e->stream), "event");
-        ECK(e, e->prec == PPMLR_FP64 ? launch_cfl_ensemble_fp64(ca, e->cfl_blocks, e->stream)
-                                     : launch_cfl_ensemble_mixed(ca, e->cfl_blocks, e->stream), "cfl");
+        ECK(e, cfl_launchers(e->prec).ens(ca, e->cfl_blocks, e->stream), "cfl");
         ECK(e, cudaEventRecord(ev[8 * k + 1], e->stream), "event");
         kind[4 * k] = 3;
         for (int j = 0; j < 3; j++) {

@@ -1,0 +1,84 @@
+// Launchers of the sweep kernels for one arithmetic variant (R, EX); each
+// kernel translation unit instantiates one variant with its own compiler
+// flags and exports a SweepLaunchers table.
+#pragma once
+#include "sweep.cuh"
+
+namespace ppmlr {
+
+template <typename R, bool EX>
+struct SweepVariant {
+    template <int DIR>
+    static cudaError_t single_dir(const SweepArgs &a, const Tile &t, cudaStream_t s)
+    {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(sweep_kernel<DIR, R, EX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 227 * 1024);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        sweep_kernel<DIR, R, EX><<<t.ntiles, t.threads, t.smem, s>>>(a);
+        return cudaGetLastError();
+    }
+    template <int DIR>
+    static cudaError_t ens_dir(const EnsSweepArgs &e, int blocks, int threads, size_t smem, cudaStream_t s)
+    {
+        // (the shared-memory attribute is set by per_sm_dir, which planning always calls first)
+        if (blocks == e.total_tiles) {   // one block per tile
+            sweep_ensemble_grid_kernel<DIR, R, EX><<<blocks, threads, smem, s>>>(e);
+            return cudaGetLastError();
+        }
+        sweep_ensemble_kernel<DIR, R, EX><<<blocks, threads, smem, s>>>(e);
+        return cudaGetLastError();
+    }
+    template <int DIR>
+    static cudaError_t param_dir(const EnsSweepParams &p, int blocks, int threads, size_t smem, cudaStream_t s)
+    {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t r = cudaFuncSetAttribute(sweep_ensemble_param_kernel<DIR, R, EX>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            if (r != cudaSuccess) return r;
+            attr = true;
+        }
+        sweep_ensemble_param_kernel<DIR, R, EX><<<blocks, threads, smem, s>>>(p);
+        return cudaGetLastError();
+    }
+    template <int DIR>
+    static int per_sm_dir(int threads, size_t smem)
+    {
+        cudaFuncSetAttribute(sweep_ensemble_kernel<DIR, R, EX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+        cudaFuncSetAttribute(sweep_ensemble_grid_kernel<DIR, R, EX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_ensemble_kernel<DIR, R, EX>, threads, smem) !=
+            cudaSuccess)
+            return 1;
+        return n > 0 ? n : 1;
+    }
+    static cudaError_t single(int dir, const SweepArgs &a, const Tile &t, cudaStream_t s)
+    {
+        return dir == 0 ? single_dir<0>(a, t, s) : dir == 1 ? single_dir<1>(a, t, s) : single_dir<2>(a, t, s);
+    }
+    static cudaError_t ens(int dir, const EnsSweepArgs &e, int blocks, int threads, size_t smem, cudaStream_t s)
+    {
+        return dir == 0 ? ens_dir<0>(e, blocks, threads, smem, s)
+                        : dir == 1 ? ens_dir<1>(e, blocks, threads, smem, s) : ens_dir<2>(e, blocks, threads, smem, s);
+    }
+    static cudaError_t param(int dir, const EnsSweepParams &p, int blocks, int threads, size_t smem, cudaStream_t s)
+    {
+        return dir == 0 ? param_dir<0>(p, blocks, threads, smem, s)
+                        : dir == 1 ? param_dir<1>(p, blocks, threads, smem, s)
+                                   : param_dir<2>(p, blocks, threads, smem, s);
+    }
+    static int per_sm(int dir, int threads, size_t smem)
+    {
+        return dir == 0 ? per_sm_dir<0>(threads, smem)
+                        : dir == 1 ? per_sm_dir<1>(threads, smem) : per_sm_dir<2>(threads, smem);
+    }
+    static constexpr SweepLaunchers table() { return {single, ens, param, per_sm}; }
+};
+
+}  // namespace ppmlr

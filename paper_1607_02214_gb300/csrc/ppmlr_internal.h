@@ -97,29 +97,35 @@ Tile choose_tile(int dir, const int n[3], size_t real_size);
 Tile make_tile(int dir, const int n[3], size_t real_size, int C, int L);   // C cells per chunk, L lanes
 bool validate_grid_bc(const ppmlr_grid *grid, const ppmlr_bc *bc);
 
-// launchers (defined in the kernel translation units)
-cudaError_t launch_sweep_fp64(int dir, const SweepArgs &a, const Tile &t, cudaStream_t s);
-cudaError_t launch_sweep_mixed(int dir, const SweepArgs &a, const Tile &t, cudaStream_t s);
-cudaError_t launch_cfl(const CflArgs &a, int blocks, cudaStream_t s);
-cudaError_t launch_cfl_mixed(const CflArgs &a, int blocks, cudaStream_t s);
-cudaError_t launch_sweep_ensemble_fp64(int dir, const EnsSweepArgs &e, int blocks, int threads, size_t smem,
-                                       cudaStream_t s);
-cudaError_t launch_sweep_ensemble_mixed(int dir, const EnsSweepArgs &e, int blocks, int threads, size_t smem,
-                                        cudaStream_t s);
-cudaError_t launch_sweep_ensemble_param_fp64(int dir, const EnsSweepParams &p, int blocks, int threads,
-                                             size_t smem, cudaStream_t s);
-cudaError_t launch_sweep_ensemble_param_mixed(int dir, const EnsSweepParams &p, int blocks, int threads,
-                                              size_t smem, cudaStream_t s);
+// Launchers of one arithmetic variant (defined in the kernel translation
+// units: sweep_fp64.cu, sweep_fp64_exact.cu, sweep_mixed.cu).
+struct SweepLaunchers {
+    cudaError_t (*single)(int dir, const SweepArgs &a, const Tile &t, cudaStream_t s);
+    cudaError_t (*ens)(int dir, const EnsSweepArgs &e, int blocks, int threads, size_t smem, cudaStream_t s);
+    cudaError_t (*param)(int dir, const EnsSweepParams &p, int blocks, int threads, size_t smem, cudaStream_t s);
+    int (*per_sm)(int dir, int threads, size_t smem);
+};
+extern const SweepLaunchers k_sweep_fp64, k_sweep_fp64_exact, k_sweep_mixed;
+inline const SweepLaunchers &sweep_launchers(ppmlr_precision p)
+{
+    return p == PPMLR_MIXED ? k_sweep_mixed : p == PPMLR_FP64_EXACT ? k_sweep_fp64_exact : k_sweep_fp64;
+}
+
 // Ensemble CFL: block b belongs to the last instance i with first_block[i] <= b.
 struct EnsCflArgs {
     const CflArgs *args;       // device array, one entry per instance
     const int *first_block;
     int count;
 };
-cudaError_t launch_cfl_ensemble_fp64(const EnsCflArgs &e, int blocks, cudaStream_t s);
-cudaError_t launch_cfl_ensemble_mixed(const EnsCflArgs &e, int blocks, cudaStream_t s);
-int sweep_blocks_per_sm_fp64(int dir, int threads, size_t smem);
-int sweep_blocks_per_sm_mixed(int dir, int threads, size_t smem);
+struct CflLaunchers {
+    cudaError_t (*single)(const CflArgs &a, int blocks, cudaStream_t s);
+    cudaError_t (*ens)(const EnsCflArgs &e, int blocks, cudaStream_t s);
+};
+extern const CflLaunchers k_cfl_fp64, k_cfl_fp64_exact, k_cfl_mixed;
+inline const CflLaunchers &cfl_launchers(ppmlr_precision p)
+{
+    return p == PPMLR_MIXED ? k_cfl_mixed : p == PPMLR_FP64_EXACT ? k_cfl_fp64_exact : k_cfl_fp64;
+}
 int cfl_threads();
 
 }  // namespace ppmlr

@@ -37,10 +37,22 @@ template <> struct K<float> {
     static __device__ __forceinline__ float ab(float x) { return fabsf(x); }
 };
 
-// Fast magnetosonic speed squared along the normal (mu0 = 1).
-template <typename R>
+// Fast magnetosonic speed squared along the normal (mu0 = 1).  EX: the
+// reference's expression; otherwise one reciprocal of rho shared by the three
+// quotients.
+template <typename R, bool EX = true>
 __device__ __forceinline__ R fast2(R rho, R p, R Bn, R B1, R B2, R gam)
 {
+    if constexpr (!EX) {
+        const R ir = R(1) / rho;
+        const R a2 = gam * p * ir;
+        const R b2 = (Bn * Bn + B1 * B1 + B2 * B2) * ir;
+        const R bn2 = Bn * Bn * ir;
+        const R s = a2 + b2;
+        R disc = s * s - R(4) * a2 * bn2;
+        if (disc < R(0)) disc = R(0);
+        return R(0.5) * (s + K<R>::sq(disc));
+    }
     R a2 = gam * p / rho;
     R b2 = (Bn * Bn + B1 * B1 + B2 * B2) / rho;
     R bn2 = Bn * Bn / rho;
@@ -51,8 +63,19 @@ __device__ __forceinline__ R fast2(R rho, R p, R Bn, R B1, R B2, R gam)
 }
 
 // Earth dipole along -z: B_d = M [3 (m.r) r - m r^2] / r^5, m = -z.
+template <bool EX = true>
 __device__ __forceinline__ void dipole(double M, double x, double y, double z, double *B)
 {
+    if constexpr (!EX) {
+        const double r2 = x * x + y * y + z * z;
+        if (M == 0.0 || r2 == 0.0) { B[0] = B[1] = B[2] = 0.0; return; }
+        const double f = M / (r2 * r2 * sqrt(r2));
+        const double mr = -z;
+        B[0] = f * (3.0 * mr * x);
+        B[1] = f * (3.0 * mr * y);
+        B[2] = f * (3.0 * mr * z + r2);
+        return;
+    }
     double r2 = x * x + y * y + z * z;
     if (M == 0.0 || r2 == 0.0) { B[0] = B[1] = B[2] = 0.0; return; }
     double r = sqrt(r2);
@@ -110,9 +133,21 @@ __device__ __forceinline__ R avg_left(R l, R r, R a6, R y)
 // coordinate (they depend only on the zone widths, so they are shared by all
 // reconstructed variables).
 template <typename R> struct SlopeCoef { R c1, c2, c3; };
-template <typename R>
+// EX: three quotients as in the reference; otherwise one reciprocal of the
+// product of the three denominators.
+template <typename R, bool EX = true>
 __device__ __forceinline__ SlopeCoef<R> slope_coef(R xm, R x0, R xp)
 {
+    if constexpr (!EX) {
+        const R d1 = xm + x0 + xp, d2 = xp + x0, d3 = xm + x0;
+        const R d23 = d2 * d3;
+        const R inv = R(1) / (d1 * d23);
+        SlopeCoef<R> k;
+        k.c1 = x0 * d23 * inv;
+        k.c2 = (R(2) * xm + x0) * (d1 * d3) * inv;
+        k.c3 = (x0 + R(2) * xp) * (d1 * d2) * inv;
+        return k;
+    }
     R s3 = xm + x0 + xp;
     SlopeCoef<R> k;
     k.c1 = x0 / s3;
@@ -121,9 +156,25 @@ __device__ __forceinline__ SlopeCoef<R> slope_coef(R xm, R x0, R xp)
     return k;
 }
 template <typename R> struct EdgeCoef { R k1, k2, k3, k4, k5; };
-template <typename R>
+// EX: the reference's five quotients; otherwise one reciprocal of the
+// product of the four denominators.
+template <typename R, bool EX = true>
 __device__ __forceinline__ EdgeCoef<R> edge_coef(R x0, R x1, R x2, R x3)
 {
+    if constexpr (!EX) {
+        const R d1 = R(2) * x1 + x2, d2 = R(2) * x2 + x1, d3 = x1 + x2, d4 = x0 + x1 + x2 + x3;
+        const R d12 = d1 * d2, d34 = d3 * d4;
+        const R inv = R(1) / (d12 * d34);
+        const R r1 = d2 * d34 * inv, r2 = d1 * d34 * inv, r3 = d12 * d4 * inv, r4 = d12 * d3 * inv;
+        const R z1 = (x0 + x1) * r1, z2 = (x3 + x2) * r2;
+        EdgeCoef<R> k;
+        k.k1 = x1 * r3;
+        k.k2 = r4;
+        k.k3 = R(2) * x2 * x1 * r3 * (z1 - z2);
+        k.k4 = x1 * z1;
+        k.k5 = x2 * z2;
+        return k;
+    }
     R z1 = (x0 + x1) / (R(2) * x1 + x2);
     R z2 = (x3 + x2) / (R(2) * x2 + x1);
     R s4 = x0 + x1 + x2 + x3;
@@ -163,7 +214,9 @@ enum : int {
 // domain (the single-domain kernel passes its launch argument, the ensemble
 // kernel a per-instance copy in shared memory); `tile` is the tile index
 // within that domain; `smem_raw` holds NSM * NP * L values of type R.
-template <int DIR, typename R, typename ARGS>
+// EX (double only): every stage evaluates the reference's expression trees;
+// otherwise quotients sharing a denominator use one reciprocal.
+template <int DIR, typename R, bool EX, typename ARGS>
 __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned char *smem_raw, const int flip)
 {
     // input and output state (flip = 1 exchanges them); array v at base + v * vs
@@ -224,7 +277,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         pos[0] = a.cx[(DIR == 0 ? g : ix) + GH];
         pos[1] = a.cy[(DIR == 1 ? g : iy) + GH];
         pos[2] = a.cz[(DIR == 2 ? g : iz) + GH];
-        dipole(a.M, pos[0], pos[1], pos[2], Bdg);
+        dipole<EX>(a.M, pos[0], pos[1], pos[2], Bdg);
         double Uc[8];
         int src = g;
         bool fixed = false;
@@ -253,13 +306,22 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         double mn = Uc[1 + DIR], m1 = Uc[1 + T1], m2 = Uc[1 + T2];
         double bn = Uc[4 + DIR], b1 = Uc[4 + T1], b2 = Uc[4 + T2];
         double E = Uc[7];
-        double prd = (a.gamma - 1.0) * (E - 0.5 * (mn * mn + m1 * m1 + m2 * m2) / rd
-                                        - 0.5 * (bn * bn + b1 * b1 + b2 * b2));
-        if (prd < a.p_min) { prd = a.p_min; floored = out_cell; }
+        double prd;
         Bd0 = R(Bdg[DIR]); Bd1 = R(Bdg[T1]); Bd2 = R(Bdg[T2]);
-        rho = R(rd); u = R(mn / rd); v1 = R(m1 / rd); v2 = R(m2 / rd);
+        if constexpr (EX) {
+            prd = (a.gamma - 1.0) * (E - 0.5 * (mn * mn + m1 * m1 + m2 * m2) / rd
+                                     - 0.5 * (bn * bn + b1 * b1 + b2 * b2));
+            rho = R(rd); u = R(mn / rd); v1 = R(m1 / rd); v2 = R(m2 / rd);
+            e = R(E / rd);
+        } else {
+            const double ir = 1.0 / rd;
+            prd = (a.gamma - 1.0) * (E - 0.5 * (mn * mn + m1 * m1 + m2 * m2) * ir
+                                     - 0.5 * (bn * bn + b1 * b1 + b2 * b2));
+            rho = R(rd); u = R(mn * ir); v1 = R(m1 * ir); v2 = R(m2 * ir);
+            e = R(E * ir);
+        }
+        if (prd < a.p_min) { prd = a.p_min; floored = out_cell; }
         Bn = R(bn); B1 = R(b1); B2 = R(b2); pr = R(prd);
-        e = R(E / rd);
         dm = R(rd * dx);
     } else if (act) {
         // mixed path: float geometry, float dipole, integer double->float
@@ -306,7 +368,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     }
     if (act) {
         R Pt = pr + R(0.5) * (Bn * Bn + B1 * B1 + B2 * B2);
-        W = rho * K<R>::sq(fast2<R>(rho, pr, Bn, B1, B2, gam));
+        W = rho * K<R>::sq(fast2<R, EX>(rho, pr, Bn, B1, B2, gam));
         SM(A_RHO, s) = rho; SM(A_U, s) = u; SM(A_V1, s) = v1; SM(A_V2, s) = v2;
         SM(A_B1, s) = B1; SM(A_B2, s) = B2; SM(A_P, s) = pr; SM(A_DM, s) = dm;
         SM(A_PT, s) = Pt; SM(A_BN, s) = Bn;
@@ -325,7 +387,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     R dmv[7];
     R src_m[3] = {0, 0, 0}, src_b[3] = {0, 0, 0}, src_e = 0;
     if (act && p >= 1 && p <= NPe - 2) {
-        SlopeCoef<R> k = slope_coef<R>(SM(A_DM, s - PS), dm, SM(A_DM, s + PS));
+        SlopeCoef<R> k = slope_coef<R, EX>(SM(A_DM, s - PS), dm, SM(A_DM, s + PS));
         const R own[7] = {rho, u, v1, v2, B1, B2, pr};
 #pragma unroll
         for (int v = 0; v < 7; v++) {
@@ -351,11 +413,21 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             R h;
             if constexpr (F64) h = R(0.5) * R(a.w[g + GH - 1]) + R(dx) + R(0.5) * R(a.w[g + GH + 1]);
             else h = R(0.5) * a.wf[g + GH - 1] + a.wf[g + GH] + R(0.5) * a.wf[g + GH + 1];
-            R DB0 = (SM(A_BN, s + PS) - SM(A_BN, s - PS)) / h;
-            R DB1 = (SM(A_B1, s + PS) - SM(A_B1, s - PS)) / h;
-            R DB2 = (SM(A_B2, s + PS) - SM(A_B2, s - PS)) / h;
-            R DA1 = (SM(A_AY, s + PS) - SM(A_AY, s - PS)) / h;
-            R DA2 = (SM(A_AZ, s + PS) - SM(A_AZ, s - PS)) / h;
+            R DB0, DB1, DB2, DA1, DA2;
+            if constexpr (EX) {
+                DB0 = (SM(A_BN, s + PS) - SM(A_BN, s - PS)) / h;
+                DB1 = (SM(A_B1, s + PS) - SM(A_B1, s - PS)) / h;
+                DB2 = (SM(A_B2, s + PS) - SM(A_B2, s - PS)) / h;
+                DA1 = (SM(A_AY, s + PS) - SM(A_AY, s - PS)) / h;
+                DA2 = (SM(A_AZ, s + PS) - SM(A_AZ, s - PS)) / h;
+            } else {
+                const R ih = R(1) / h;
+                DB0 = (SM(A_BN, s + PS) - SM(A_BN, s - PS)) * ih;
+                DB1 = (SM(A_B1, s + PS) - SM(A_B1, s - PS)) * ih;
+                DB2 = (SM(A_B2, s + PS) - SM(A_B2, s - PS)) * ih;
+                DA1 = (SM(A_AY, s + PS) - SM(A_AY, s - PS)) * ih;
+                DA2 = (SM(A_AZ, s + PS) - SM(A_AZ, s - PS)) * ih;
+            }
             R J0 = 0, J1 = -DB2, J2 = DB1;
             R cA0 = 0, cA1 = -DA2, cA2 = DA1;
             src_m[0] = J1 * Bd2 - J2 * Bd1;
@@ -375,7 +447,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     R edg[7];
     R flat = 0;
     if (act && p >= 1 && p <= NPe - 3) {
-        EdgeCoef<R> k = edge_coef<R>(SM(A_DM, s - PS), dm, SM(A_DM, s + PS), SM(A_DM, s + 2 * PS));
+        EdgeCoef<R> k = edge_coef<R, EX>(SM(A_DM, s - PS), dm, SM(A_DM, s + PS), SM(A_DM, s + 2 * PS));
         const R own[7] = {rho, u, v1, v2, B1, B2, pr};
 #pragma unroll
         for (int v = 0; v < 7; v++) {
@@ -395,8 +467,15 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     // right state of interface p-1/2 (this zone, left end): to A[0..8] for p-1.
     R sl[9];
     if (act && p >= 3 && p <= NPe - 4) {
-        R yf = W * dtr / dm;
-        R ya = K<R>::sq(rho) * K<R>::ab(Bn) * dtr / dm;
+        R yf, ya;
+        if constexpr (EX) {
+            yf = W * dtr / dm;
+            ya = K<R>::sq(rho) * K<R>::ab(Bn) * dtr / dm;
+        } else {
+            const R dtm = dtr / dm;
+            yf = W * dtm;
+            ya = K<R>::sq(rho) * K<R>::ab(Bn) * dtm;
+        }
         const R own[7] = {rho, u, v1, v2, B1, B2, pr};
         R srv[9];
 #pragma unroll
@@ -426,14 +505,22 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         R Bnf = R(0.5) * (Bn + SM(A_BN, s + PS));
         R PL = sl[6] + R(0.5) * (sl[4] * sl[4] + sl[5] * sl[5]);
         R PR = Rs[6] + R(0.5) * (Rs[4] * Rs[4] + Rs[5] * Rs[5]);
-        R WL = sl[0] * K<R>::sq(fast2<R>(sl[0], sl[6], Bnf, sl[4], sl[5], gam));
-        R WR = Rs[0] * K<R>::sq(fast2<R>(Rs[0], Rs[6], Bnf, Rs[4], Rs[5], gam));
-        R us = (WL * sl[1] + WR * Rs[1] + PL - PR) / (WL + WR);
-        R Ps = (WR * PL + WL * PR + WL * WR * (sl[1] - Rs[1])) / (WL + WR);
+        R WL = sl[0] * K<R>::sq(fast2<R, EX>(sl[0], sl[6], Bnf, sl[4], sl[5], gam));
+        R WR = Rs[0] * K<R>::sq(fast2<R, EX>(Rs[0], Rs[6], Bnf, Rs[4], Rs[5], gam));
+        R us, Ps;
+        if constexpr (EX) {
+            us = (WL * sl[1] + WR * Rs[1] + PL - PR) / (WL + WR);
+            Ps = (WR * PL + WL * PR + WL * WR * (sl[1] - Rs[1])) / (WL + WR);
+        } else {
+            const R iW = R(1) / (WL + WR);
+            us = (WL * sl[1] + WR * Rs[1] + PL - PR) * iW;
+            Ps = (WR * PL + WL * PR + WL * WR * (sl[1] - Rs[1])) * iW;
+        }
         R Ss = Ps - R(0.5) * Bnf * Bnf;
         R ZL = K<R>::sq(sl[0]) * K<R>::ab(Bnf);
         R ZR = K<R>::sq(Rs[0]) * K<R>::ab(Bnf);
         R vs[2], ss[2];
+        const R iZ = (EX || ZL + ZR == R(0)) ? R(0) : R(1) / (ZL + ZR);
 #pragma unroll
         for (int t = 0; t < 2; t++) {
             R vL = sl[2 + t], vR = Rs[2 + t];
@@ -441,9 +528,12 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             if (ZL + ZR == R(0)) {
                 vs[t] = R(0.5) * (vL + vR);
                 ss[t] = R(0);
-            } else {
+            } else if constexpr (EX) {
                 vs[t] = (ZL * vL + ZR * vR + sR - sL) / (ZL + ZR);
                 ss[t] = (ZR * sL + ZL * sR + ZL * ZR * (vR - vL)) / (ZL + ZR);
+            } else {
+                vs[t] = (ZL * vL + ZR * vR + sR - sL) * iZ;
+                ss[t] = (ZR * sL + ZL * sR + ZL * ZR * (vR - vL)) * iZ;
             }
         }
         rs_u = us; rs_S = Ss; rs_s1 = ss[0]; rs_s2 = ss[1];
@@ -464,17 +554,28 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         else dxr = a.wf[g + GH];
         dxL = dxr + dtr * (rs_u - lu);
         if (!(dxL > R(0))) atomicOr(a.flags, FLAG_CFL);
-        R uL = u - dtr * (rs_S - lS) / dm;
-        R v1L = v1 + dtr * (rs_s1 - ls1) / dm;
-        R v2L = v2 + dtr * (rs_s2 - ls2) / dm;
         R bv1 = dtr * (rs_b1 - lb1);
         R bv2 = dtr * (rs_b2 - lb2);
         R B1dx = B1 * dxr + bv1;
         R B2dx = B2 * dxr + bv2;
-        R eL = e - dtr * (rs_fe - lfe) / dm;
-        R rhoL = dm / dxL;
-        qL[0] = rhoL; qL[1] = rhoL * uL; qL[2] = rhoL * v1L; qL[3] = rhoL * v2L;
-        qL[4] = B1dx / dxL; qL[5] = B2dx / dxL; qL[6] = rhoL * eL;
+        if constexpr (EX) {
+            R uL = u - dtr * (rs_S - lS) / dm;
+            R v1L = v1 + dtr * (rs_s1 - ls1) / dm;
+            R v2L = v2 + dtr * (rs_s2 - ls2) / dm;
+            R eL = e - dtr * (rs_fe - lfe) / dm;
+            R rhoL = dm / dxL;
+            qL[0] = rhoL; qL[1] = rhoL * uL; qL[2] = rhoL * v1L; qL[3] = rhoL * v2L;
+            qL[4] = B1dx / dxL; qL[5] = B2dx / dxL; qL[6] = rhoL * eL;
+        } else {
+            const R dtm = dtr / dm, idxL = R(1) / dxL;
+            R uL = u - (rs_S - lS) * dtm;
+            R v1L = v1 + (rs_s1 - ls1) * dtm;
+            R v2L = v2 + (rs_s2 - ls2) * dtm;
+            R eL = e - (rs_fe - lfe) * dtm;
+            R rhoL = dm * idxL;
+            qL[0] = rhoL; qL[1] = rhoL * uL; qL[2] = rhoL * v1L; qL[3] = rhoL * v2L;
+            qL[4] = B1dx * idxL; qL[5] = B2dx * idxL; qL[6] = rhoL * eL;
+        }
         dC[0] = -dtr * (rs_S - lS);
         dC[1] = dtr * (rs_s1 - ls1);
         dC[2] = dtr * (rs_s2 - ls2);
@@ -492,7 +593,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     // ---------------- P7: remap slopes ----------------
     R rmv[7];
     if (act && p >= 5 && p <= NPe - 6) {
-        SlopeCoef<R> k = slope_coef<R>(SM(SB0 + 7, s - PS), dxL, SM(SB0 + 7, s + PS));
+        SlopeCoef<R> k = slope_coef<R, EX>(SM(SB0 + 7, s - PS), dxL, SM(SB0 + 7, s + PS));
 #pragma unroll
         for (int v = 0; v < 7; v++) {
             rmv[v] = limit_slope<R>(SM(SB0 + v, s - PS), qL[v], SM(SB0 + v, s + PS), k.c1, k.c2, k.c3);
@@ -504,7 +605,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     // ---------------- P8: remap interface values ----------------
     R red[7];
     if (act && p >= 5 && p <= NPe - 7) {
-        EdgeCoef<R> k = edge_coef<R>(SM(SB0 + 7, s - PS), dxL, SM(SB0 + 7, s + PS), SM(SB0 + 7, s + 2 * PS));
+        EdgeCoef<R> k = edge_coef<R, EX>(SM(SB0 + 7, s - PS), dxL, SM(SB0 + 7, s + PS), SM(SB0 + 7, s + 2 * PS));
 #pragma unroll
         for (int v = 0; v < 7; v++) {
             red[v] = edge_value<R>(k, qL[v], SM(SB0 + v, s + PS), rmv[v], SM(v, s + PS));
@@ -551,9 +652,12 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         const int cmap[7] = {0, 1 + DIR, 1 + T1, 1 + T2, 4 + T1, 4 + T2, 7};
         const R dCv[7] = {R(0), dC[0], dC[1], dC[2], dC[3], dC[4], dC[5]};
         if constexpr (F64) {
+            const double idx = EX ? 0.0 : 1.0 / dx;
 #pragma unroll
             for (int v = 0; v < 7; v++) {
-                double dU = (dCv[v] + SM(SB0 + v, s - PS) - SM(SB0 + v, s)) / dx;
+                double dU;
+                if constexpr (EX) dU = (dCv[v] + SM(SB0 + v, s - PS) - SM(SB0 + v, s)) / dx;
+                else dU = (dCv[v] + SM(SB0 + v, s - PS) - SM(SB0 + v, s)) * idx;
                 Un[cmap[v]] = Un[cmap[v]] + dU;
             }
             if (a.do_src) {
@@ -566,10 +670,10 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
                 Un[7] = Un[7] + dt * src_e;
             }
         } else {
-            const R dxr = a.wf[g + GH];
+            const R idx = R(1) / a.wf[g + GH];
             R dU[8];
 #pragma unroll
-            for (int v = 0; v < 7; v++) dU[cmap[v]] = (dCv[v] + SM(SB0 + v, s - PS) - SM(SB0 + v, s)) / dxr;
+            for (int v = 0; v < 7; v++) dU[cmap[v]] = (dCv[v] + SM(SB0 + v, s - PS) - SM(SB0 + v, s)) * idx;
             dU[4 + DIR] = R(0);
             if (a.do_src) {
                 dU[1 + DIR] += dtr * src_m[0]; dU[1 + T1] += dtr * src_m[1]; dU[1 + T2] += dtr * src_m[2];
@@ -619,11 +723,11 @@ template <typename R> struct MaxThreads { static constexpr int value = MAXT; };
 template <> struct MaxThreads<double> { static constexpr int value = MAXT_F64; };
 
 // Single domain: one block per tile.
-template <int DIR, typename R>
+template <int DIR, typename R, bool EX>
 __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_kernel(SweepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    sweep_tile<DIR, R, const SweepArgs>(a, blockIdx.x, smem_raw, 0);
+    sweep_tile<DIR, R, EX, const SweepArgs>(a, blockIdx.x, smem_raw, 0);
 }
 
 // Ensemble: a persistent kernel.  Each block repeatedly takes the next tile
@@ -631,7 +735,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_kernel(SweepArgs a
 // instance that owns it from the per-instance first-tile table and processes
 // the tile with that instance's arguments (read-only device table).
 // Instances of different sizes and boundary data share the launch.
-template <int DIR, typename R>
+template <int DIR, typename R, bool EX>
 __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_kernel(EnsSweepArgs e)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -661,7 +765,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_kernel(En
         // read through a volatile view: each use is a shared-memory load
         // rather than a register held across the tile's phases
         const volatile SweepArgs &va = args;
-        sweep_tile<DIR, R, const volatile SweepArgs>(va, t - __ldg(e.first_tile + lo), smem_raw, e.flip);
+        sweep_tile<DIR, R, EX, const volatile SweepArgs>(va, t - __ldg(e.first_tile + lo), smem_raw, e.flip);
         __syncthreads();
     }
 }
@@ -669,7 +773,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_kernel(En
 // Ensemble, one block per tile: the block scheduler hands out (instance,
 // tile) items in order; the block finds its instance from the first-tile
 // table and copies that instance's arguments to shared memory.
-template <int DIR, typename R>
+template <int DIR, typename R, bool EX>
 __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_grid_kernel(EnsSweepArgs e)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -684,13 +788,13 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_grid_kern
     int *dst = reinterpret_cast<int *>(&args);
     for (int k = threadIdx.x; k < (int)(sizeof(SweepArgs) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
     __syncthreads();
-    sweep_tile<DIR, R, const SweepArgs>(args, t - __ldg(e.first_tile + lo), smem_raw, e.flip);
+    sweep_tile<DIR, R, EX, const SweepArgs>(args, t - __ldg(e.first_tile + lo), smem_raw, e.flip);
 }
 
 // Ensemble, one block per tile, arguments of all instances in the kernel
 // parameter (constant bank): the block finds its instance from the first-tile
 // table and reads that instance's fields straight from the parameter space.
-template <int DIR, typename R>
+template <int DIR, typename R, bool EX>
 __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_param_kernel(const __grid_constant__ EnsSweepParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -700,7 +804,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_param_ker
         const int mid = (lo + hi + 1) >> 1;
         if (p.first_tile[mid] <= t) lo = mid; else hi = mid - 1;
     }
-    sweep_tile<DIR, R, const SweepArgs>(p.args[lo], t - p.first_tile[lo], smem_raw, p.flip);
+    sweep_tile<DIR, R, EX, const SweepArgs>(p.args[lo], t - p.first_tile[lo], smem_raw, p.flip);
 }
 
 }  // namespace ppmlr

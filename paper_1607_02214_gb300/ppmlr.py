@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libppmlr_gb300.so")
 
 PPMLR_OK, PPMLR_E_INVALID, PPMLR_E_CUDA, PPMLR_E_OOM, PPMLR_E_NONFINITE, PPMLR_E_CFL, PPMLR_E_TIMEOUT = range(7)
-PPMLR_FP64, PPMLR_MIXED = 0, 1
+PPMLR_FP64, PPMLR_MIXED, PPMLR_FP64_EXACT = 0, 1, 2
 PPMLR_BC_PERIODIC, PPMLR_BC_OUTFLOW, PPMLR_BC_INFLOW = 0, 1, 2
 STATUS_NAMES = {0: "PPMLR_OK", 1: "PPMLR_E_INVALID", 2: "PPMLR_E_CUDA", 3: "PPMLR_E_OOM",
                 4: "PPMLR_E_NONFINITE", 5: "PPMLR_E_CFL", 6: "PPMLR_E_TIMEOUT"}

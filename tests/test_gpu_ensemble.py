@@ -1,10 +1,12 @@
 """Batched ensemble and autotuners on the GPU.
 
-Every ensemble instance must evolve bit for bit like a single context
-advanced with ppmlr_step_cfl from the same state (the same per-cell
-arithmetic, per-instance device dt); graph replay must equal direct launches;
-tuned tile shapes must not change any result.  FP64 instances also match the
-oracle."""
+Every ensemble instance must evolve like a single context advanced with
+ppmlr_step_cfl from the same state (the same per-cell arithmetic and a
+per-instance device dt): bit for bit on the exact FP64 path; to roundoff on
+the paths compiled with contraction, whose fused multiply-adds may be formed
+differently in differently inlined kernels.  Graph replay must equal direct
+launches; tuned tile shapes must not change results.  FP64 instances also
+match the oracle."""
 import numpy as np
 import pytest
 
@@ -31,7 +33,7 @@ def small_ensemble(seed=7):
     return out
 
 
-@pytest.mark.parametrize("precision", [ppmlr.PPMLR_MIXED, ppmlr.PPMLR_FP64])
+@pytest.mark.parametrize("precision", [ppmlr.PPMLR_MIXED, ppmlr.PPMLR_FP64, ppmlr.PPMLR_FP64_EXACT])
 def test_ensemble_equals_independent_contexts(precision):
     probs = small_ensemble()
     ens = ppmlr.Ensemble(probs, precision=precision)
@@ -45,15 +47,22 @@ def test_ensemble_equals_independent_contexts(precision):
         ctx = ppmlr.Context.from_problem(p, precision)
         ctx.set_state(p.U0)
         ctx.step_cfl(0.4, nsteps)
-        assert np.array_equal(ens.get_state(i), ctx.get_state()), i
-        assert dts[i] == ctx.last_dt()
+        a, b = ens.get_state(i), ctx.get_state()
+        if precision == ppmlr.PPMLR_FP64_EXACT:
+            assert np.array_equal(a, b), i
+            assert dts[i] == ctx.last_dt()
+        else:
+            tol = 1e-12 if precision == ppmlr.PPMLR_FP64 else 1e-6
+            assert np.max(rel_l1(a, b)) <= tol, (i, rel_l1(a, b))
+            assert abs(dts[i] - ctx.last_dt()) <= tol * dts[i]
     assert ens.diagnostics()["step"] == nsteps
 
 
-def test_ensemble_graph_equals_direct_launches_and_autotune_is_neutral():
+@pytest.mark.parametrize("precision", [ppmlr.PPMLR_MIXED, ppmlr.PPMLR_FP64_EXACT])
+def test_ensemble_graph_equals_direct_launches_and_autotune_is_neutral(precision):
     probs = small_ensemble(11)
-    a = ppmlr.Ensemble(probs, precision=ppmlr.PPMLR_MIXED)
-    b = ppmlr.Ensemble(probs, precision=ppmlr.PPMLR_MIXED)
+    a = ppmlr.Ensemble(probs, precision=precision)
+    b = ppmlr.Ensemble(probs, precision=precision)
     for i, p in enumerate(probs):
         a.set_state(i, p.U0)
         b.set_state(i, p.U0)
@@ -62,7 +71,10 @@ def test_ensemble_graph_equals_direct_launches_and_autotune_is_neutral():
     ms = b.time_kernels(0.4, 4)        # direct launches, tuned tiles
     assert all(v > 0 for v in ms.values())
     for i in range(len(probs)):
-        assert np.array_equal(a.get_state(i), b.get_state(i)), i
+        if precision == ppmlr.PPMLR_FP64_EXACT:      # any launch form, bit for bit
+            assert np.array_equal(a.get_state(i), b.get_state(i)), i
+        else:                                        # tuned launch form may contract differently
+            assert np.max(rel_l1(a.get_state(i), b.get_state(i))) <= 1e-6, i
 
 
 def test_ensemble_fp64_instance_matches_oracle():
@@ -79,7 +91,7 @@ def test_ensemble_fp64_instance_matches_oracle():
         assert np.max(err) <= 1e-11, err
 
 
-@pytest.mark.parametrize("precision", [ppmlr.PPMLR_FP64, ppmlr.PPMLR_MIXED])
+@pytest.mark.parametrize("precision", [ppmlr.PPMLR_FP64, ppmlr.PPMLR_MIXED, ppmlr.PPMLR_FP64_EXACT])
 def test_autotune_changes_speed_not_results(precision):
     p = inputs.magnetosphere(n=(56, 44, 40), h0=1.0)
     a = ppmlr.Context.from_problem(p, precision)

@@ -30,10 +30,11 @@ def periodic_random(n, seed, stretched=True):
     return inputs.Problem("rand", edges, 5.0 / 3.0, inputs.BoundarySpec(powell=1), U)
 
 
+@pytest.mark.parametrize("precision", [ppmlr.PPMLR_FP64, ppmlr.PPMLR_FP64_EXACT])
 @pytest.mark.parametrize("axis", [0, 1, 2])
-def test_single_sweep_fp64(axis):
+def test_single_sweep_fp64(axis, precision):
     pr = periodic_random((37, 29, 23), 3)
-    o, g = make_oracle(pr), make_gpu(pr)
+    o, g = make_oracle(pr), make_gpu(pr, precision)
     dt = o.cfl_dt(0.4)
     assert o.sweep(axis, dt) == 0
     g.sweep(axis, dt)
@@ -43,8 +44,24 @@ def test_single_sweep_fp64(axis):
 
 def test_cfl_dt_matches():
     pr = inputs.magnetosphere(n=(40, 34, 30), h0=1.0)
-    o, g = make_oracle(pr), make_gpu(pr)
-    assert g.cfl_dt(0.4) == o.cfl_dt(0.4)
+    o = make_oracle(pr)
+    ref = o.cfl_dt(0.4)
+    assert make_gpu(pr, ppmlr.PPMLR_FP64_EXACT).cfl_dt(0.4) == ref          # bit-identical
+    assert abs(make_gpu(pr, ppmlr.PPMLR_FP64).cfl_dt(0.4) - ref) <= 1e-14 * ref
+    assert abs(make_gpu(pr, ppmlr.PPMLR_MIXED).cfl_dt(0.4) - ref) <= 1e-5 * ref
+
+
+@pytest.mark.parametrize("prob", ["brio_wu", "magnetosphere", "random"])
+def test_exact_path_is_bit_identical(prob):
+    if prob == "brio_wu":
+        pr = inputs.brio_wu_3d((32, 32, 32))
+    elif prob == "magnetosphere":
+        pr = inputs.magnetosphere(n=(48, 40, 36), h0=1.0)
+    else:
+        pr = periodic_random((37, 29, 23), 5)
+    o, g, _ = run_pair(pr, 6, precision=ppmlr.PPMLR_FP64_EXACT)
+    assert np.array_equal(g.get_state(), o.get_state())
+    assert g.diagnostics()["floor_hits"] == o.floor_hits
 
 
 def test_brio_wu_3d_32_cubed_fp64_10_steps():
@@ -89,11 +106,12 @@ def test_step_cfl_matches_host_loop():
     assert np.array_equal(g1.get_state(), g2.get_state())
 
 
-def test_split_symmetry_gpu():
+@pytest.mark.parametrize("precision", [ppmlr.PPMLR_FP64, ppmlr.PPMLR_FP64_EXACT, ppmlr.PPMLR_MIXED])
+def test_split_symmetry_gpu(precision):
     res = []
     for axis in range(3):
         pr = inputs.brio_wu_1d(40, axis=axis)
-        g = make_gpu(pr)
+        g = make_gpu(pr, precision)
         for _ in range(8):
             g.step(g.cfl_dt(0.4))
         U = g.get_state()
@@ -161,8 +179,10 @@ def test_high_mach_translation_fp64_exact_mixed_bounded():
     def pressure(X):
         return (2.0 / 3.0) * (X[7] - 0.5 * (X[1] ** 2 + X[2] ** 2 + X[3] ** 2) / X[0]
                               - 0.5 * (X[4] ** 2 + X[5] ** 2 + X[6] ** 2))
-    o, g, dts = run_pair(pr, 5)
+    o, g, dts = run_pair(pr, 5, precision=ppmlr.PPMLR_FP64_EXACT)
     assert np.array_equal(g.get_state(), o.get_state())
+    _, gf, _ = run_pair(pr, 5, dts=dts)
+    assert np.max(rel_l1(gf.get_state(), o.get_state())) <= FP64_TOL
     _, gm, _ = run_pair(pr, 5, precision=ppmlr.PPMLR_MIXED, dts=dts)
     pa, pb = pressure(gm.get_state()), pressure(o.get_state())
     assert np.all(pb > 0.5)
