@@ -45,20 +45,25 @@ BYTES_PER_CELL_SWEEP = 128      # read 8 FP64 + write 8 FP64
 # DRAM bytes per cell of one launch measured by ncu for each kernel, with the
 # sha256 prefix of the kernel source they were taken on (null once it changes).
 NCU_TRAFFIC = {
-    "fp64:x": {"bytes_per_cell": 123.6, "src": "59978c472013f835"},
-    "fp64:y": {"bytes_per_cell": 124.0, "src": "59978c472013f835"},
-    "fp64:z": {"bytes_per_cell": 124.1, "src": "59978c472013f835"},
-    "fp64:cfl": {"bytes_per_cell": 64.5, "src": "59978c472013f835"},
-    "mixed:x": {"bytes_per_cell": 123.1, "src": "59978c472013f835"},
-    "mixed:y": {"bytes_per_cell": 123.7, "src": "59978c472013f835"},
-    "mixed:z": {"bytes_per_cell": 124.2, "src": "59978c472013f835"},
-    "mixed:cfl": {"bytes_per_cell": 64.4, "src": "59978c472013f835"},
+    "fp64:x": {"bytes_per_cell": 123.3, "src": "a43db4ae1c19108d"},
+    "fp64:y": {"bytes_per_cell": 123.8, "src": "a43db4ae1c19108d"},
+    "fp64:z": {"bytes_per_cell": 124.2, "src": "a43db4ae1c19108d"},
+    "fp64:cfl": {"bytes_per_cell": 64.5, "src": "a43db4ae1c19108d"},
+    "mixed:x": {"bytes_per_cell": 123.0, "src": "a43db4ae1c19108d"},
+    "mixed:y": {"bytes_per_cell": 123.7, "src": "a43db4ae1c19108d"},
+    "mixed:z": {"bytes_per_cell": 124.1, "src": "a43db4ae1c19108d"},
+    "mixed:cfl": {"bytes_per_cell": 64.3, "src": "a43db4ae1c19108d"},
+    "ensemble:x": {"bytes_per_cell": 127.4, "src": "a43db4ae1c19108d"},
 }
+
+
+KERNEL_SOURCES = ("sweep.cuh", "launch.cuh", "mixed_util.cuh", "cfl.cuh", "sweep_fp64.cu", "sweep_fp64_exact.cu",
+                  "sweep_mixed.cu", "cfl.cu", "cfl_fp64.cu", "cfl_mixed.cu")
 
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("sweep.cuh", "sweep_fp64.cu", "sweep_mixed.cu", "cfl.cu"):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1607_02214_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -66,6 +71,38 @@ def kernel_source_hash():
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------- ranks -------------
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """Maximum of a per-rank float over all ranks (the slowest rank sets the time)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, dist=None, device="cpu"):
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def shard(count, rank, world):
+    """Instances of an ensemble owned by `rank`: independent problems are split
+    round-robin, with no data exchanged between ranks."""
+    return list(range(rank, count, world))
+
+
+def throughput(cells_all_ranks, steps, max_ms):
+    """Whole-job cell-updates/s: all ranks' cells x steps over the slowest rank's time."""
+    return cells_all_ranks * steps / (max_ms * 1e-3)
 
 
 # ---------------------------------------------------------------- clocks ------
@@ -214,12 +251,8 @@ def run_ours(args, rank, world, dist):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def max_ranks(x):
+        return max_over_ranks(x, dist, "cuda")
 
     def timed_run(precision, steps, warmup, with_clocks=False):
         ctx = ppmlr.Context.from_problem(prob, precision)
@@ -254,8 +287,8 @@ def run_ours(args, rank, world, dist):
 
     # ---- main measurement
     ctx, ms, kern, launches, clocks = timed_run(prec, args.steps, args.warmup, with_clocks=True)
-    ms = max_over_ranks(ms)
-    value = world * cells * args.steps / (ms * 1e-3)
+    ms = max_ranks(ms)
+    value = throughput(world * cells, args.steps, ms)
     log(f"[bench] {name}: {ms / args.steps:.3f} ms/step, {value:.4e} cell-updates/s, kernels {kern}")
 
     # ---- roofline of the dominant kernel (largest total time)
@@ -290,7 +323,7 @@ def run_ours(args, rank, world, dist):
     if not args.quick:
         other = ppmlr.PPMLR_MIXED if prec == ppmlr.PPMLR_FP64 else ppmlr.PPMLR_FP64
         octx, oms, okern, _, _ = timed_run(other, args.steps, args.warmup)
-        oms = max_over_ranks(oms)
+        oms = max_ranks(oms)
         ovalue = world * cells * args.steps / (oms * 1e-3)
         # accuracy: both precisions from the same state with the FP64 path's dt
         a = ppmlr.Context.from_problem(prob, ppmlr.PPMLR_FP64)
@@ -331,7 +364,7 @@ def run_ours(args, rank, world, dist):
     # ---- the bit-exact FP64 form (same expression trees as the CPU reference)
     if not args.quick and args.precision == "fp64":
         xctx, xms, xkern, _, _ = timed_run(ppmlr.PPMLR_FP64_EXACT, max(3, args.steps // 2), args.warmup)
-        xms = max_over_ranks(xms)
+        xms = max_ranks(xms)
         nx = max(3, args.steps // 2)
         extra["fp64_exact"] = {"value": world * cells * nx / (xms * 1e-3), "ms_per_step": xms / nx,
                                "kernels_avg_ms": {k: v[0] / max(v[1], 1) for k, v in xkern.items()},
@@ -356,15 +389,16 @@ def run_ours(args, rank, world, dist):
             ectx.step_cfl(prob.cfl, 1)
             ectx.get_state(hout)           # device -> host, synchronises
         barrier()
-        t = max_over_ranks(time.perf_counter() - t0)
+        t = max_ranks(time.perf_counter() - t0)
         nbytes = 8 * 8 * cells
         e2e = {"value": world * cells * ksteps / t, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": ksteps}
         del ectx
 
-    # ---- batched ensemble: 48 seeded instances on uneven grids (mixed path)
-    if not args.quick and not args.no_ensemble and world == 1:
-        extra["ensemble"] = run_ensemble(args, value, barrier)
+    # ---- batched ensemble: 48 seeded instances on uneven grids (mixed path);
+    # with N ranks each owns a round-robin share of the instances
+    if not args.quick and not args.no_ensemble:
+        extra["ensemble"] = run_ensemble(args, value, barrier, rank, world, dist)
 
     # ---- large single domain 512x384x384 (finest 0.2 R_E), both precisions
     if not args.quick and not args.no_large and world == 1:
@@ -390,17 +424,22 @@ def run_ours(args, rank, world, dist):
     return out
 
 
-def run_ensemble(args, fp64_value, barrier):
+def run_ensemble(args, fp64_value, barrier, rank=0, world=1, dist=None):
     """48 magnetosphere instances, grids drawn from {96^3, 128x96x96, 160x128x128},
-    seeded solar wind; one persistent launch per sweep, one CUDA graph per step."""
+    seeded solar wind; one launch per sweep over all instances, one CUDA graph
+    per step.  With N ranks, rank r advances instances r, r+N, ... (no data
+    exchanged; the whole job's throughput is reported)."""
     import torch
     from paper_1607_02214_gb300 import inputs, ppmlr
     t0 = time.perf_counter()
-    probs = inputs.ensemble(48)
+    all_probs = inputs.ensemble(48)
+    probs = [all_probs[i] for i in shard(len(all_probs), rank, world)]
     log(f"[bench] ensemble inputs built in {time.perf_counter() - t0:.1f} s")
     cells = sum(p.cells for p in probs)
-    out = {"workload": "ensemble_48_magnetosphere_mixed", "instances": len(probs), "cells": cells,
-           "grids": sorted({"x".join(map(str, p.n)) for p in probs})}
+    cells_all = sum(p.cells for p in all_probs)
+    out = {"workload": "ensemble_48_magnetosphere_mixed", "instances": len(all_probs), "cells": cells_all,
+           "grids": sorted({"x".join(map(str, p.n)) for p in all_probs}),
+           "scaling": "strong" if world > 1 else None, "instances_per_rank": len(probs)}
     ens = ppmlr.Ensemble(probs, precision=ppmlr.PPMLR_MIXED)
     for i, p in enumerate(probs):
         ens.set_state(i, p.U0)
@@ -416,18 +455,22 @@ def run_ensemble(args, fp64_value, barrier):
     ens.step(0.4, args.steps)
     e1.record(stream)
     e1.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     ens.check()
-    out.update({"value": cells * args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.steps,
+    out.update({"value": throughput(cells_all, args.steps, ms), "unit": UNIT, "ms_per_step": ms / args.steps,
                 "gpu_launches": ens.launch_count - n0, "graph_replay": True})
     out["speedup_vs_fp64"] = out["value"] / fp64_value
+    if world > 1:        # the per-kernel and comparison runs below are single-GPU diagnostics
+        ens.close()
+        return out
     kern = ens.time_kernels(0.4, 3)
     out["kernels_avg_ms"] = kern
     dom = max(("x", "y", "z"), key=lambda k: kern[k])
     ach = BYTES_PER_CELL_SWEEP * cells / (kern[dom] * 1e-3) / 1e9
+    etr = NCU_TRAFFIC.get(f"ensemble:{dom}")
     out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": 6787.2, "unit": "GB/s", "frac": ach / 6787.2,
-                       "traffic": None, "kernel": f"sweep_ensemble_{dom}", "avg_launch_ms": kern[dom],
-                       "peak_source": "measured"}
+                       "traffic": etr["bytes_per_cell"] * cells if etr and etr["src"] == kernel_source_hash() else None,
+                       "kernel": f"sweep_ensemble_{dom}", "avg_launch_ms": kern[dom], "peak_source": "measured"}
     # the same instances advanced one context at a time (no batching)
     ctxs = [ppmlr.Context.from_problem(p, ppmlr.PPMLR_MIXED) for p in probs]
     for c, p in zip(ctxs, probs):
@@ -523,6 +566,7 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--ensemble-only", action="store_true", help="only the 48-instance ensemble section")
     args = ap.parse_args()
     if args.warmup < 3:
         log("[bench] warm-up raised to 3 steps")
@@ -542,6 +586,11 @@ def main():
 
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.ensemble_only:
+        import torch
+        from paper_1607_02214_gb300 import build
+        build.build()
+        out = run_ensemble(args, float("nan"), torch.cuda.synchronize)
     else:
         out = run_ours(args, rank, world, dist)
     if rank == 0 and out is not None:
