@@ -86,10 +86,57 @@ __device__ __forceinline__ void dipole(double M, double x, double y, double z, d
     B[2] = M * (3.0 * mr * z + r2) / r5;
 }
 
+// Sign and magnitude tests of doubles on the integer pipe (the GB300's FP64
+// pipe is its scarcest unit).  For finite values they decide exactly as the
+// floating-point comparisons they replace.
+__device__ __forceinline__ bool pos_d(double x) { return __double_as_longlong(x) > 0; }          // x > 0
+__device__ __forceinline__ bool neg_d(double x)                                                   // x < 0
+{
+    const long long b = __double_as_longlong(x);
+    return b < 0 && (b << 1) != 0;
+}
+__device__ __forceinline__ long long mag_d(double x) { return __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL; }
+__device__ __forceinline__ long long ord_d(double x)      // monotone map of finite doubles to integers
+{
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+// x * y > 0 (both non-zero, same sign; ignores underflow of the product)
+__device__ __forceinline__ bool same_sign_d(double x, double y)
+{
+    const long long a = __double_as_longlong(x), b = __double_as_longlong(y);
+    return (a ^ b) >= 0 && (a << 1) != 0 && (b << 1) != 0;
+}
+
+// x > 0 and x < 0 on the integer pipe for the fast double form, plain
+// comparisons otherwise.
+template <typename R, bool EX>
+__device__ __forceinline__ bool gt0(R x)
+{
+    if constexpr (!EX && std::is_same<R, double>::value) return pos_d(x);
+    else return x > R(0);
+}
+template <typename R, bool EX>
+__device__ __forceinline__ bool lt0(R x)
+{
+    if constexpr (!EX && std::is_same<R, double>::value) return neg_d(x);
+    else return x < R(0);
+}
+
 // Limited PPM slope of zone i from its neighbours (Colella & Woodward 1984).
-template <typename R>
+template <typename R, bool EX = true>
 __device__ __forceinline__ R limit_slope(R am, R a0, R ap, R c1, R c2, R c3)
 {
+    if constexpr (!EX && std::is_same<R, double>::value) {
+        const double dp = ap - a0, dm = a0 - am;
+        const double da = c1 * (c2 * dp + c3 * dm);
+        if (!same_sign_d(dp, dm)) return 0.0;
+        double m = fabs(da);
+        const double lim_m = 2.0 * fabs(dm), lim_p = 2.0 * fabs(dp);
+        if (mag_d(lim_m) < mag_d(m)) m = lim_m;
+        if (mag_d(lim_p) < mag_d(m)) m = lim_p;
+        return pos_d(da) ? m : (neg_d(da) ? -m : 0.0);
+    }
     R dp = ap - a0;
     R dm = a0 - am;
     R da = c1 * (c2 * dp + c3 * dm);
@@ -104,9 +151,24 @@ __device__ __forceinline__ R limit_slope(R am, R a0, R ap, R c1, R c2, R c3)
 }
 
 // Monotonicity constraint of the parabola; returns a6 and updates l, r.
-template <typename R>
+// Fast double form: the extremum test as a sign test, and the two overshoot
+// tests da*m6 > da^2 and -da^2 > da*m6 as comparisons of m6 with +-da (the
+// constraint is continuous at both switch points).
+template <typename R, bool EX = true>
 __device__ __forceinline__ R monotone(R ai, R &l, R &r)
 {
+    if constexpr (!EX && std::is_same<R, double>::value) {
+        if (!same_sign_d(r - ai, ai - l)) {
+            l = ai; r = ai;
+        } else {
+            const double da = r - l;
+            const double m6 = 6.0 * (ai - 0.5 * (l + r));
+            const long long om = ord_d(m6), od = ord_d(da), onda = ord_d(-da);
+            if (pos_d(da) ? om > od : om < od) l = 3.0 * ai - 2.0 * r;
+            else if (pos_d(da) ? om < onda : om > onda) r = 3.0 * ai - 2.0 * l;
+        }
+        return 6.0 * (ai - 0.5 * (l + r));
+    }
     if ((r - ai) * (ai - l) <= R(0)) {
         l = ai; r = ai;
     } else {
@@ -391,7 +453,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         const R own[7] = {rho, u, v1, v2, B1, B2, pr};
 #pragma unroll
         for (int v = 0; v < 7; v++) {
-            dmv[v] = limit_slope<R>(SM(A_RHO + v, s - PS), own[v], SM(A_RHO + v, s + PS), k.c1, k.c2, k.c3);
+            dmv[v] = limit_slope<R, EX>(SM(A_RHO + v, s - PS), own[v], SM(A_RHO + v, s + PS), k.c1, k.c2, k.c3);
             SM(SB0 + v, s) = dmv[v];
         }
         R ft = 0;
@@ -482,7 +544,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         for (int v = 0; v < 7; v++) {
             R lft = flat * own[v] + (R(1) - flat) * SM(SC0 + v, s - PS);
             R rgt = flat * own[v] + (R(1) - flat) * edg[v];
-            R a6 = monotone<R>(own[v], lft, rgt);
+            R a6 = monotone<R, EX>(own[v], lft, rgt);
             R y = (v == 2 || v == 3) ? ya : yf;
             sl[v] = avg_right<R>(lft, rgt, a6, y);
             srv[v] = avg_left<R>(lft, rgt, a6, y);
@@ -553,7 +615,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         if constexpr (F64) dxr = R(dx);
         else dxr = a.wf[g + GH];
         dxL = dxr + dtr * (rs_u - lu);
-        if (!(dxL > R(0))) atomicOr(a.flags, FLAG_CFL);
+        if (!gt0<R, EX>(dxL)) atomicOr(a.flags, FLAG_CFL);
         R bv1 = dtr * (rs_b1 - lb1);
         R bv2 = dtr * (rs_b2 - lb2);
         R B1dx = B1 * dxr + bv1;
@@ -596,7 +658,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         SlopeCoef<R> k = slope_coef<R, EX>(SM(SB0 + 7, s - PS), dxL, SM(SB0 + 7, s + PS));
 #pragma unroll
         for (int v = 0; v < 7; v++) {
-            rmv[v] = limit_slope<R>(SM(SB0 + v, s - PS), qL[v], SM(SB0 + v, s + PS), k.c1, k.c2, k.c3);
+            rmv[v] = limit_slope<R, EX>(SM(SB0 + v, s - PS), qL[v], SM(SB0 + v, s + PS), k.c1, k.c2, k.c3);
             SM(v, s) = rmv[v];
         }
     }
@@ -621,22 +683,22 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         for (int v = 0; v < 7; v++) {
             pl[v] = SM(SC0 + v, s - PS);
             pr_[v] = red[v];
-            p6[v] = monotone<R>(qL[v], pl[v], pr_[v]);
+            p6[v] = monotone<R, EX>(qL[v], pl[v], pr_[v]);
         }
         if (p <= NPe - 8) {                       // edge p+1/2: donor is this zone when del >= 0
-            if (del_p > R(0)) {
+            if (gt0<R, EX>(del_p)) {
                 R y = del_p / dxL;
-                if (y >= R(1)) atomicOr(a.flags, FLAG_CFL);
+                if (!gt0<R, EX>(R(1) - y)) atomicOr(a.flags, FLAG_CFL);
 #pragma unroll
                 for (int v = 0; v < 7; v++) SM(SB0 + v, s) = del_p * avg_right<R>(pl[v], pr_[v], p6[v], y);
-            } else if (!(del_p < R(0))) {
+            } else if (!lt0<R, EX>(del_p)) {
 #pragma unroll
                 for (int v = 0; v < 7; v++) SM(SB0 + v, s) = R(0);
             }
         }
-        if (p >= 7 && del_m < R(0)) {             // edge p-1/2: donor is this zone when del < 0
+        if (p >= 7 && lt0<R, EX>(del_m)) {       // edge p-1/2: donor is this zone when del < 0
             R y = -del_m / dxL;
-            if (y >= R(1)) atomicOr(a.flags, FLAG_CFL);
+            if (!gt0<R, EX>(R(1) - y)) atomicOr(a.flags, FLAG_CFL);
 #pragma unroll
             for (int v = 0; v < 7; v++) SM(SB0 + v, s - PS) = del_m * avg_left<R>(pl[v], pr_[v], p6[v], y);
         }
