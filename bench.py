@@ -355,6 +355,7 @@ def run_ours(args, rank, world, dist):
                  "kernel": f"sweep_{odom}" if odom != "cfl" else "cfl", "avg_launch_ms": oavg,
                  "peak_source": "measured"}
         extra[key] = {"value": ovalue, "ms_per_step": oms / args.steps, "roofline": oroof,
+                      "tiles": {"C_L": octx.tiles(), "forms": octx.sweep_forms()},
                       "speedup_vs_fp64": (ovalue / value) if key == "mixed" else (value / ovalue),
                       "kernels_avg_ms": {k: v[0] / max(v[1], 1) for k, v in okern.items()},
                       "error_vs_fp64": {"steps": args.accuracy_steps,
@@ -419,7 +420,8 @@ def run_ours(args, rank, world, dist):
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": config_dict(prob, name, args, world), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-           "clocks": clocks, "gpu_launches": launches, "kernels": per_kernel, "kernel_src": src_hash}
+           "clocks": clocks, "gpu_launches": launches, "kernels": per_kernel, "kernel_src": src_hash,
+           "tiles": {"C_L": ctx.tiles(), "forms": ctx.sweep_forms()}}
     out.update(extra)
     return out
 
@@ -544,7 +546,7 @@ def run_large(args, barrier):
             if name == "fp64":
                 per[k]["fp64_gflops"] = FLOPS_PER_CELL[k] * cells / (avg * 1e-3) / 1e9
         out[name] = {"value": cells * steps / (ms * 1e-3), "ms_per_step": ms / steps, "steps": steps,
-                     "kernels": per, "tiles": ctx.tiles()}
+                     "kernels": per, "tiles": ctx.tiles(), "forms": ctx.sweep_forms()}
         ctx.close()
     out["mixed"]["speedup_vs_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
     del U0

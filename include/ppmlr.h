@@ -40,7 +40,7 @@ typedef enum {
     PPMLR_E_OOM = 3,        /* device allocation failed */
     PPMLR_E_NONFINITE = 4,  /* a sweep produced a non-finite conserved value */
     PPMLR_E_CFL = 5,        /* dt too large: a Lagrangian width <= 0 or a remap sliver >= one zone */
-    PPMLR_E_TIMEOUT = 6     /* a bounded device wait gave up */
+    PPMLR_E_TIMEOUT = 6     /* a bounded device wait (TMA copy completion) gave up */
 } ppmlr_status;
 
 typedef enum {
@@ -184,6 +184,26 @@ ppmlr_status ppmlr_autotune(ppmlr_ctx *ctx, double *best_ms);
 /* Tile shape in use per direction: C (cells per chunk) and L (lanes);
  * C and L point to 3 entries each. */
 ppmlr_status ppmlr_get_tiles(ppmlr_ctx *ctx, int *C, int *L);
+
+/* Force the tile shape of one direction (axis 0, 1, 2): C cells per chunk
+ * (1 <= C <= n[axis]) and L lanes (L >= 1) with (C + 14) * L within the
+ * thread budget (448 for the FP64 forms, 512 for PPMLR_MIXED).  Resets that
+ * direction's launch form to 0.  Results do not depend on the shape.  Returns
+ * PPMLR_E_INVALID (state unchanged) for shapes outside those bounds. */
+ppmlr_status ppmlr_set_tiles(ppmlr_ctx *ctx, int axis, int C, int L);
+
+/* Launch form of each sweep direction (3 entries): 0 = one block per tile
+ * reading its input from global memory; 1 = persistent blocks whose input
+ * boxes (8 arrays x positions x lanes) are staged into shared memory by the
+ * tensor memory accelerator, double-buffered so the next tile's copy overlaps
+ * the current tile's arithmetic; 2 = one block per tile with its input box
+ * staged by the tensor memory accelerator.  Forms 1 and 2 apply to the y and
+ * z sweeps with an even number of lanes, nx even and at most 256 positions
+ * per tile.  The autotuner chooses the form with the tile shape; results do
+ * not depend on it beyond roundoff on the contracted paths. */
+ppmlr_status ppmlr_get_sweep_forms(ppmlr_ctx *ctx, int *form);
+/* Select a launch form for one axis (PPMLR_E_INVALID if not available). */
+ppmlr_status ppmlr_set_sweep_form(ppmlr_ctx *ctx, int axis, int form);
 
 /* ---- Batched ensemble ----------------------------------------------------
  * count independent instances, each with its own grid and boundary

@@ -39,6 +39,12 @@ struct ppmlr_ctx {
     unsigned int *counter;
     int cfl_blocks;
     Tile tile[3];
+    int mode[3];                 // 0: one block per tile; 1: persistent, TMA-staged input (y, z);
+                                 // 2: one block per tile, TMA-staged input (y, z)
+    CUtensorMap tmap[3][2];      // per direction, per state buffer (input = buffer 0 or 1)
+    int tma_blocks[3];
+    size_t tma_smem[3];
+    int sms;
     long long steps;
     long long launches;
     std::string err;
@@ -192,6 +198,80 @@ bool ppmlr::validate_grid_bc(const ppmlr_grid *grid, const ppmlr_bc *bc)
     return ncell <= (1LL << 31) - 1;
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+static size_t stage_pad_bytes(const Tile &t) { return ((size_t)8 * t.NP * t.L * sizeof(double) + 1023) / 1024 * 1024; }
+
+// The TMA form applies to y and z sweeps whose box fits the copy engine's
+// rules: lanes (x extent) even and rows 16-byte aligned (nx even), at most
+// 256 positions along the sweep axis, both staging buffers plus the exchange
+// arrays within shared memory.
+static const char *tma_ineligible(const ppmlr_ctx *c, int d, const Tile &t, int form)
+{
+    if (d == 0) return "the x sweep has no TMA form";
+    if (!encode_fn()) return "cuTensorMapEncodeTiled is not available from the driver";
+    if (t.L < 2 || (t.L & 1)) return "the TMA form needs an even number of lanes";
+    if (t.NP > 256) return "the TMA form needs at most 256 positions per tile (C + 14)";
+    if (c->n[0] & 1) return "the TMA form needs nx even (16-byte aligned rows)";
+    const int persist = form == 1;
+    const size_t smem = (persist ? 2 : 1) * stage_pad_bytes(t) + t.smem;
+    if (smem > 226 * 1024) return "the TMA staging buffers do not fit in shared memory";   // 1 KB static
+    if (sweep_launchers(c->prec).tma_per_sm(d, persist, t.threads, smem) < 1)
+        return "the TMA kernel cannot be resident with this tile shape";
+    return nullptr;
+}
+static bool tma_eligible(const ppmlr_ctx *c, int d, const Tile &t, int form)
+{
+    return tma_ineligible(c, d, t, form) == nullptr;
+}
+
+// Tensor maps of direction d for both state buffers: a 4D view (x, y, z,
+// variable) of the 8 equally spaced arrays; box = L lanes x NP positions.
+// Returns nullptr on success, else the reason.
+static const char *setup_tma_why(ppmlr_ctx *c, int d, int form)
+{
+    const Tile &t = c->tile[d];
+    if (const char *why = tma_ineligible(c, d, t, form)) return why;
+    const cuuint64_t dims[4] = {(cuuint64_t)c->n[0], (cuuint64_t)c->n[1], (cuuint64_t)c->n[2], 8};
+    const cuuint64_t strides[3] = {(cuuint64_t)c->n[0] * 8, (cuuint64_t)c->n[0] * c->n[1] * 8,
+                                   (cuuint64_t)c->stride * 8};
+    cuuint32_t box[4] = {(cuuint32_t)t.L, 1, 1, 8};
+    box[d] = (cuuint32_t)t.NP;
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    for (int b = 0; b < 2; b++) {
+        void *base = c->state + (size_t)b * 8 * c->stride;
+        CUresult r = encode_fn()(&c->tmap[d][b], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, base, dims, strides, box, es,
+                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled rejected the state layout";
+    }
+    const int persist = form == 1;
+    c->tma_smem[d] = (persist ? 2 : 1) * stage_pad_bytes(t) + t.smem;
+    const int per_sm = sweep_launchers(c->prec).tma_per_sm(d, persist, t.threads, c->tma_smem[d]);
+    const long long b = (long long)per_sm * c->sms;
+    c->tma_blocks[d] = persist ? (int)(b < t.ntiles ? b : t.ntiles) : t.ntiles;
+    return nullptr;
+}
+static bool setup_tma(ppmlr_ctx *c, int d, int form) { return setup_tma_why(c, d, form) == nullptr; }
+
 static bool is_sweep_noop(const ppmlr_ctx *c, int d)
 {
     return c->n[d] == 1 && c->bc.face[d][0] == PPMLR_BC_PERIODIC && c->bc.face[d][1] == PPMLR_BC_PERIODIC &&
@@ -269,7 +349,8 @@ ppmlr_status ppmlr_create(const ppmlr_grid *grid, double gamma, const ppmlr_bc *
         if (e != cudaSuccess) { cudaFree(c->geof); cudaFree(c->geo); cudaFree(c->state); delete c; return PPMLR_E_CUDA; }
     }
     size_t rs = prec == PPMLR_MIXED ? sizeof(float) : sizeof(double);
-    for (int d = 0; d < 3; d++) c->tile[d] = choose_tile(d, c->n, rs);
+    for (int d = 0; d < 3; d++) { c->tile[d] = choose_tile(d, c->n, rs); c->mode[d] = 0; }
+    c->sms = dev_sms;
     *out = c;
     return PPMLR_OK;
 }
@@ -318,6 +399,7 @@ static ppmlr_status read_flags(ppmlr_ctx *c)
     CK(c, cudaStreamSynchronize(c->stream), "stream sync");
     if (f) {
         CK(c, cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream), "flags reset");
+        if (f & FLAG_TIMEOUT) return fail(c, PPMLR_E_TIMEOUT, "a bounded device wait gave up");
         if (f & FLAG_NONFINITE) return fail(c, PPMLR_E_NONFINITE, "a sweep produced a non-finite state");
         return fail(c, PPMLR_E_CFL, "time step too large for the CFL condition");
     }
@@ -372,7 +454,14 @@ static ppmlr_status launch_one_sweep(ppmlr_ctx *c, int d, double dt, const doubl
     a.gammaf = (float)a.gamma; a.p_minf = (float)a.p_min; a.Mf = (float)a.M; a.r_innerf = (float)a.r_inner;
     for (int k = 0; k < 8; k++) a.inflowf[k] = (float)a.inflow[k];
     int rec = timing_begin(c, d);
-    cudaError_t e = sweep_launchers(c->prec).single(d, a, t, c->stream);
+    cudaError_t e;
+    if (c->mode[d] != 0) {
+        const int b = c->U[0] == c->state ? 0 : 1;     // buffer holding the input state
+        e = sweep_launchers(c->prec).tma(d, c->mode[d] == 1, a, c->tmap[d][b], c->tma_blocks[d], t.threads,
+                                         c->tma_smem[d], c->stream);
+    } else {
+        e = sweep_launchers(c->prec).single(d, a, t, c->stream);
+    }
     timing_end(c, rec);
     if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
     c->launches++;
@@ -472,7 +561,7 @@ ppmlr_status ppmlr_get_diagnostics(ppmlr_ctx *c, long long *step, long long *flo
 
 // Per-process cache of tuned tile shapes: (dir, nx, ny, nz, prec) -> (C, L).
 static std::mutex g_tune_mutex;
-static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
+static std::map<std::tuple<int, int, int, int, int>, std::tuple<int, int, int>> g_tune_cache;
 
 ppmlr_status ppmlr_autotune(ppmlr_ctx *c, double *best_ms)
 {
@@ -497,7 +586,9 @@ ppmlr_status ppmlr_autotune(ppmlr_ctx *c, double *best_ms)
             std::lock_guard<std::mutex> lk(g_tune_mutex);
             auto it = g_tune_cache.find(key);
             if (it != g_tune_cache.end()) {
-                c->tile[d] = make_tile(d, c->n, rs, it->second.first, it->second.second);
+                c->tile[d] = make_tile(d, c->n, rs, std::get<0>(it->second), std::get<1>(it->second));
+                const int f = std::get<2>(it->second);
+                c->mode[d] = f != 0 && setup_tma(c, d, f) ? f : 0;
                 continue;
             }
         }
@@ -515,15 +606,26 @@ ppmlr_status ppmlr_autotune(ppmlr_ctx *c, double *best_ms)
             }
         }
         float best = 1e30f;
-        std::pair<int, int> pick = {c->tile[d].C, c->tile[d].L};
+        std::tuple<int, int, int> pick = {c->tile[d].C, c->tile[d].L, c->mode[d]};
         const Tile keep = c->tile[d];
+        const int keep_mode = c->mode[d];
+        std::vector<std::tuple<int, int, int>> trials;
         for (auto &cl : cands) {
-            c->tile[d] = make_tile(d, c->n, rs, cl.first, cl.second);
+            trials.push_back({cl.first, cl.second, 0});
+            for (int f = 1; f <= 2; f++)
+                if (tma_eligible(c, d, make_tile(d, c->n, rs, cl.first, cl.second), f))
+                    trials.push_back({cl.first, cl.second, f});
+        }
+        for (auto &tr : trials) {
+            c->tile[d] = make_tile(d, c->n, rs, std::get<0>(tr), std::get<1>(tr));
+            const int f = std::get<2>(tr);
+            c->mode[d] = f != 0 && setup_tma(c, d, f) ? f : 0;
+            if (c->mode[d] != f) continue;
             float tot = 0.0f;
             for (int rep = 0; rep < 3; rep++) {
                 CK(c, cudaEventRecord(t0, c->stream), "event");
                 st = launch_one_sweep(c, d, 0.0, c->dt_dev);
-                if (st != PPMLR_OK) { c->tile[d] = keep; return st; }
+                if (st != PPMLR_OK) { c->tile[d] = keep; c->mode[d] = keep_mode; return st; }
                 CK(c, cudaEventRecord(t1, c->stream), "event");
                 CK(c, cudaEventSynchronize(t1), "event sync");
                 // undo the buffer swap of launch_one_sweep: the state stays in place
@@ -532,9 +634,11 @@ ppmlr_status ppmlr_autotune(ppmlr_ctx *c, double *best_ms)
                 cudaEventElapsedTime(&ms, t0, t1);
                 if (rep > 0) tot += ms;
             }
-            if (tot < best) { best = tot; pick = cl; }
+            if (tot < best) { best = tot; pick = tr; }
         }
-        c->tile[d] = make_tile(d, c->n, rs, pick.first, pick.second);
+        c->tile[d] = make_tile(d, c->n, rs, std::get<0>(pick), std::get<1>(pick));
+        const int fp = std::get<2>(pick);
+        c->mode[d] = fp != 0 && setup_tma(c, d, fp) ? fp : 0;
         if (best_ms) best_ms[d] = best / 2.0f;
         std::lock_guard<std::mutex> lk(g_tune_mutex);
         g_tune_cache[key] = pick;
@@ -553,6 +657,37 @@ ppmlr_status ppmlr_get_tiles(ppmlr_ctx *c, int *C, int *L)
 {
     if (!c || !C || !L) return PPMLR_E_INVALID;
     for (int d = 0; d < 3; d++) { C[d] = c->tile[d].C; L[d] = c->tile[d].L; }
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_set_tiles(ppmlr_ctx *c, int axis, int C, int L)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (axis < 0 || axis > 2) return fail(c, PPMLR_E_INVALID, "set_tiles: bad axis");
+    const int N = c->n[axis];
+    if (C < 1 || C > N || L < 1) return fail(c, PPMLR_E_INVALID, "set_tiles: need 1 <= C <= n[axis] and L >= 1");
+    const size_t rs = c->prec == PPMLR_MIXED ? sizeof(float) : sizeof(double);
+    const int maxt = c->prec == PPMLR_MIXED ? MAXT : MAXT_F64;
+    if ((long long)(C + 2 * GH) * L > maxt) return fail(c, PPMLR_E_INVALID, "set_tiles: (C + 14) * L exceeds the thread budget");
+    c->tile[axis] = make_tile(axis, c->n, rs, C, L);
+    c->mode[axis] = 0;
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_get_sweep_forms(ppmlr_ctx *c, int *form)
+{
+    if (!c || !form) return PPMLR_E_INVALID;
+    for (int d = 0; d < 3; d++) form[d] = c->mode[d];
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_set_sweep_form(ppmlr_ctx *c, int axis, int form)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (axis < 0 || axis > 2 || form < 0 || form > 2) return fail(c, PPMLR_E_INVALID, "set_sweep_form: bad axis or form");
+    if (form == 0) { c->mode[axis] = 0; return PPMLR_OK; }
+    if (const char *why = setup_tma_why(c, axis, form)) return fail(c, PPMLR_E_INVALID, why);
+    c->mode[axis] = form;
     return PPMLR_OK;
 }
 

@@ -58,6 +58,56 @@ struct SweepVariant {
             return 1;
         return n > 0 ? n : 1;
     }
+    // dynamic shared memory up to the 227 KB per block less the kernel's
+    // static part (its mbarriers)
+    template <int DIR, bool P>
+    static cudaError_t allow_tma_smem()
+    {
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, sweep_tma_kernel<DIR, R, EX, P>);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(sweep_tma_kernel<DIR, R, EX, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    227 * 1024 - (int)fa.sharedSizeBytes);
+    }
+    template <int DIR, bool P>
+    static cudaError_t tma_dir(const SweepArgs &a, const CUtensorMap &map, int blocks, int threads, size_t smem,
+                               cudaStream_t s)
+    {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = allow_tma_smem<DIR, P>();
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        sweep_tma_kernel<DIR, R, EX, P><<<blocks, threads, smem, s>>>(a, map);
+        return cudaGetLastError();
+    }
+    template <int DIR, bool P>
+    static int tma_per_sm_dir(int threads, size_t smem)
+    {
+        if (allow_tma_smem<DIR, P>() != cudaSuccess) return 0;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_tma_kernel<DIR, R, EX, P>, threads, smem) !=
+            cudaSuccess)
+            return 0;
+        return n;
+    }
+    // persist: 1 = persistent double-buffered, 0 = one tile per block
+    static cudaError_t tma(int dir, int persist, const SweepArgs &a, const CUtensorMap &map, int blocks,
+                           int threads, size_t smem, cudaStream_t s)
+    {
+        if (persist)
+            return dir == 1 ? tma_dir<1, true>(a, map, blocks, threads, smem, s)
+                            : tma_dir<2, true>(a, map, blocks, threads, smem, s);
+        return dir == 1 ? tma_dir<1, false>(a, map, blocks, threads, smem, s)
+                        : tma_dir<2, false>(a, map, blocks, threads, smem, s);
+    }
+    static int tma_per_sm(int dir, int persist, int threads, size_t smem)
+    {
+        if (persist)
+            return dir == 1 ? tma_per_sm_dir<1, true>(threads, smem) : tma_per_sm_dir<2, true>(threads, smem);
+        return dir == 1 ? tma_per_sm_dir<1, false>(threads, smem) : tma_per_sm_dir<2, false>(threads, smem);
+    }
     static cudaError_t single(int dir, const SweepArgs &a, const Tile &t, cudaStream_t s)
     {
         return dir == 0 ? single_dir<0>(a, t, s) : dir == 1 ? single_dir<1>(a, t, s) : single_dir<2>(a, t, s);
@@ -78,7 +128,7 @@ struct SweepVariant {
         return dir == 0 ? per_sm_dir<0>(threads, smem)
                         : dir == 1 ? per_sm_dir<1>(threads, smem) : per_sm_dir<2>(threads, smem);
     }
-    static constexpr SweepLaunchers table() { return {single, ens, param, per_sm}; }
+    static constexpr SweepLaunchers table() { return {single, ens, param, per_sm, tma, tma_per_sm}; }
 };
 
 }  // namespace ppmlr

@@ -1,5 +1,6 @@
 // Internal declarations of the GB300 split-sweep library (not part of the ABI).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -15,7 +16,7 @@ constexpr int NSM = 28;        // shared-memory exchange arrays per tile (see sw
 constexpr int MAXT = 512;      // threads per tile (one thread per cell position and lane), mixed path
 constexpr int MAXT_F64 = 448;  // FP64 path: fewer threads, up to 146 registers each
 
-enum : int { FLAG_CFL = 1, FLAG_NONFINITE = 2 };
+enum : int { FLAG_CFL = 1, FLAG_NONFINITE = 2, FLAG_TIMEOUT = 4 };
 
 // Arguments of one sweep launch (passed by value).
 struct SweepArgs {
@@ -104,6 +105,10 @@ struct SweepLaunchers {
     cudaError_t (*ens)(int dir, const EnsSweepArgs &e, int blocks, int threads, size_t smem, cudaStream_t s);
     cudaError_t (*param)(int dir, const EnsSweepParams &p, int blocks, int threads, size_t smem, cudaStream_t s);
     int (*per_sm)(int dir, int threads, size_t smem);
+    // persistent y/z sweep with TMA-staged input boxes
+    cudaError_t (*tma)(int dir, int persist, const SweepArgs &a, const CUtensorMap &map, int blocks, int threads,
+                       size_t smem, cudaStream_t s);
+    int (*tma_per_sm)(int dir, int persist, int threads, size_t smem);
 };
 extern const SweepLaunchers k_sweep_fp64, k_sweep_fp64_exact, k_sweep_mixed;
 inline const SweepLaunchers &sweep_launchers(ppmlr_precision p)

@@ -20,6 +20,8 @@
 // compiled without contraction), float for the mixed path (pressure recovery
 // and the state accumulation stay in double).
 #pragma once
+#include <cuda.h>
+
 #include <type_traits>
 
 #include "mixed_util.cuh"
@@ -278,8 +280,12 @@ enum : int {
 // within that domain; `smem_raw` holds NSM * NP * L values of type R.
 // EX (double only): every stage evaluates the reference's expression trees;
 // otherwise quotients sharing a denominator use one reciprocal.
+// `stage` (optional): this tile's input box staged in shared memory by TMA,
+// 8 arrays of NP * L doubles in the tile's slot order (position p of lane l
+// at the slot of (p, l)); cells outside the box come from global memory.
 template <int DIR, typename R, bool EX, typename ARGS>
-__device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned char *smem_raw, const int flip)
+__device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned char *smem_raw, const int flip,
+                                           const double *__restrict__ stage = nullptr)
 {
     // input and output state (flip = 1 exchanges them); array v at base + v * vs
     const double *Uin = flip ? a.Un : a.U;
@@ -288,7 +294,12 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
     constexpr bool F64 = std::is_same<R, double>::value;
     R *sm = reinterpret_cast<R *>(smem_raw);
-    const int L = a.L, NP = a.NP, NT = NP * L;
+    // opaque copies: inside a persistent loop the addresses derived from the
+    // tile shape are then recomputed per tile instead of held in registers
+    int L_, NP_;
+    asm volatile("mov.b32 %0, %1;" : "=r"(L_) : "r"(a.L));
+    asm volatile("mov.b32 %0, %1;" : "=r"(NP_) : "r"(a.NP));
+    const int L = L_, NP = NP_, NT = NP * L;
     const int PS = DIR == 0 ? 1 : L;
     const int s = threadIdx.x;
 #define SM(k, slot) sm[(k) * NT + (slot)]
@@ -360,9 +371,16 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             }
         }
         if (!fixed) {
-            const long long gi = base + (long long)src * stride;
+            const int ps = src - (g0 - GH);                 // position of the source cell in the box
+            if (stage && ps >= 0 && ps < NP) {
+                const int slot = DIR == 0 ? l * NP + ps : ps * L + l;
 #pragma unroll
-            for (int v = 0; v < 8; v++) Uc[v] = __ldg(Uin + v * vs + gi);
+                for (int v = 0; v < 8; v++) Uc[v] = stage[v * NT + slot];
+            } else {
+                const long long gi = base + (long long)src * stride;
+#pragma unroll
+                for (int v = 0; v < 8; v++) Uc[v] = __ldg(Uin + v * vs + gi);
+            }
         }
         double rd = Uc[0];
         double mn = Uc[1 + DIR], m1 = Uc[1 + T1], m2 = Uc[1 + T2];
@@ -412,10 +430,17 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             pr = f[7];
             e = pr / (gm1 * rho) + 0.5f * (u * u + v1 * v1 + v2 * v2) + 0.5f * (Bn * Bn + B1 * B1 + B2 * B2) / rho;
         } else {
-            const long long gi = base + (long long)src * stride;
             df q[8];
+            const int ps = src - (g0 - GH);                 // position of the source cell in the box
+            if (stage && ps >= 0 && ps < NP) {
+                const int slot = DIR == 0 ? l * NP + ps : ps * L + l;
 #pragma unroll
-            for (int v = 0; v < 8; v++) q[v] = split_double(__ldg(Uin + v * vs + gi));
+                for (int v = 0; v < 8; v++) q[v] = split_double(stage[v * NT + slot]);
+            } else {
+                const long long gi = base + (long long)src * stride;
+#pragma unroll
+                for (int v = 0; v < 8; v++) q[v] = split_double(__ldg(Uin + v * vs + gi));
+            }
             float prf = pressure_df(q[0], q[1 + DIR], q[1 + T1], q[1 + T2], q[4 + DIR], q[4 + T1], q[4 + T2],
                                     q[7], gm1);
             rho = q[0].h;
@@ -709,8 +734,13 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     if (out_cell) {
         const long long gi = base + (long long)g * stride;
         double Un[8];
+        if (stage) {
 #pragma unroll
-        for (int v = 0; v < 8; v++) Un[v] = __ldg(Uin + v * vs + gi);
+            for (int v = 0; v < 8; v++) Un[v] = stage[v * NT + s];
+        } else {
+#pragma unroll
+            for (int v = 0; v < 8; v++) Un[v] = __ldg(Uin + v * vs + gi);
+        }
         const int cmap[7] = {0, 1 + DIR, 1 + T1, 1 + T2, 4 + T1, 4 + T2, 7};
         const R dCv[7] = {R(0), dC[0], dC[1], dC[2], dC[3], dC[4], dC[5]};
         if constexpr (F64) {
@@ -781,14 +811,138 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
 #undef SM
 }
 
+// ---- TMA staging (y and z sweeps) -------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// Bounded wait on the mbarrier phase; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    for (int it = 0; it < (1 << 22); it++) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// One 4D box (x, y, z, variable) of the state into shared memory.
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
 template <typename R> struct MaxThreads { static constexpr int value = MAXT; };
 template <> struct MaxThreads<double> { static constexpr int value = MAXT_F64; };
+
+// Box origin (x, y, z) of a tile of the y or z sweep: lanes along x from
+// xg * L, positions along the sweep axis from g0 - GH.
+template <int DIR>
+__device__ __forceinline__ void tile_box_origin(const SweepArgs &a, int tile, int &cx, int &cy, int &cz)
+{
+    const int chunk = tile % a.nchunk, grp = tile / a.nchunk;
+    const int xg = grp % a.ngx, t = grp / a.ngx;
+    cx = xg * a.L;
+    if (DIR == 1) { cy = chunk * a.C - GH; cz = t; }
+    else { cy = t; cz = chunk * a.C - GH; }
+}
+
+// Resident blocks the TMA kernels are compiled for: the persistent loop
+// otherwise roughly doubles the register allocation of the tile body.
+template <typename R, bool PERSIST> struct TmaMinBlocks { static constexpr int value = 1; };
+template <bool PERSIST> struct TmaMinBlocks<float, PERSIST> { static constexpr int value = 2; };
+
+// Single domain, y or z sweep, input staged by TMA.  PERSIST: each block
+// takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...; while it computes one
+// tile, the tensor memory accelerator copies the next tile's input box (all 8
+// state arrays, NP positions x L lanes) into the other of two shared buffers.
+// Otherwise one tile per block: the box is copied at the start and the other
+// resident blocks overlap it.  Waits are bounded: a block that gives up raises
+// FLAG_TIMEOUT and returns.
+template <int DIR, typename R, bool EX, bool PERSIST>
+__global__ void __launch_bounds__(MaxThreads<R>::value, TmaMinBlocks<R, PERSIST>::value)
+    sweep_tma_kernel(SweepArgs a, const __grid_constant__ CUtensorMap map)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long bar[2];
+    const int NT = a.NP * a.L;
+    const size_t stage_bytes = (size_t)8 * NT * sizeof(double);
+    const size_t stage_pad = (stage_bytes + 1023) / 1024 * 1024;
+    double *stage0 = reinterpret_cast<double *>(smem_raw);
+    double *stage1 = reinterpret_cast<double *>(smem_raw + (PERSIST ? stage_pad : 0));
+    unsigned char *work = smem_raw + (PERSIST ? 2 : 1) * stage_pad;
+    const int ntiles = a.nchunk * a.ngx * (DIR == 1 ? a.n[2] : a.n[1]);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int t = blockIdx.x;
+    if (t >= ntiles) return;
+    if (threadIdx.x == 0) {
+        int cx, cy, cz;
+        tile_box_origin<DIR>(a, t, cx, cy, cz);
+        mbar_expect_tx(&bar[0], (unsigned)stage_bytes);
+        tma_load_4d(stage0, &map, cx, cy, cz, 0, &bar[0]);
+    }
+    if constexpr (!PERSIST) {                            // one tile per block, no loop
+        if (!mbar_wait(&bar[0], 0u)) {
+            if (threadIdx.x == 0) atomicOr(a.flags, FLAG_TIMEOUT);
+            return;
+        }
+        sweep_tile<DIR, R, EX, const SweepArgs>(a, t, work, 0, stage0);
+    } else {
+    unsigned phase[2] = {0u, 0u};
+    for (int k = 0; t < ntiles; k++, t += gridDim.x) {
+        const int b = k & 1;
+        const int tn = t + gridDim.x;
+        if (PERSIST && threadIdx.x == 0 && tn < ntiles) {   // prefetch the next tile into the other buffer
+            // the buffer's previous contents were read by every thread before
+            // the barrier that ended the last iteration; order those reads
+            // before the copy engine's writes
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            int cx, cy, cz;
+            tile_box_origin<DIR>(a, tn, cx, cy, cz);
+            mbar_expect_tx(&bar[b ^ 1], (unsigned)stage_bytes);
+            tma_load_4d(b ? stage0 : stage1, &map, cx, cy, cz, 0, &bar[b ^ 1]);
+        }
+        if (!mbar_wait(&bar[b], phase[b])) {
+            if (threadIdx.x == 0) atomicOr(a.flags, FLAG_TIMEOUT);
+            return;
+        }
+        phase[b] ^= 1u;
+        sweep_tile<DIR, R, EX, const SweepArgs>(a, t, work, 0, b ? stage1 : stage0);
+        __syncthreads();
+    }
+    }
+}
 
 // Single domain: one block per tile.
 template <int DIR, typename R, bool EX>
 __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_kernel(SweepArgs a)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     sweep_tile<DIR, R, EX, const SweepArgs>(a, blockIdx.x, smem_raw, 0);
 }
 
@@ -800,7 +954,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_kernel(SweepArgs a
 template <int DIR, typename R, bool EX>
 __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_kernel(EnsSweepArgs e)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ SweepArgs args;
     __shared__ int next, inst_cur;
     if (threadIdx.x == 0) inst_cur = -1;
@@ -838,7 +992,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_kernel(En
 template <int DIR, typename R, bool EX>
 __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_grid_kernel(EnsSweepArgs e)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ SweepArgs args;
     const int t = blockIdx.x;
     int lo = 0, hi = e.count - 1;
@@ -859,7 +1013,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_grid_kern
 template <int DIR, typename R, bool EX>
 __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_param_kernel(const __grid_constant__ EnsSweepParams p)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     const int t = blockIdx.x;
     int lo = 0, hi = p.count - 1;
     while (lo < hi) {

@@ -59,6 +59,9 @@ SIGNATURES = [
     ("ppmlr_read_timing", c_int, [c_void_p, POINTER(c_double), POINTER(c_longlong)]),
     ("ppmlr_autotune", c_int, [c_void_p, POINTER(c_double)]),
     ("ppmlr_get_tiles", c_int, [c_void_p, POINTER(c_int), POINTER(c_int)]),
+    ("ppmlr_get_sweep_forms", c_int, [c_void_p, POINTER(c_int)]),
+    ("ppmlr_set_sweep_form", c_int, [c_void_p, c_int, c_int]),
+    ("ppmlr_set_tiles", c_int, [c_void_p, c_int, c_int, c_int]),
     ("ppmlr_ensemble_create", c_int, [c_int, POINTER(ppmlr_grid), POINTER(ppmlr_bc), c_double, c_int, c_void_p,
                                       POINTER(c_void_p)]),
     ("ppmlr_ensemble_set_stream", c_int, [c_void_p, c_void_p]),
@@ -282,6 +285,18 @@ class Context:
         C, L = (c_int * 3)(), (c_int * 3)()
         self._check(load().ppmlr_get_tiles(self._h, C, L))
         return list(C), list(L)
+
+    def set_tiles(self, axis, C, L):
+        return self._check(load().ppmlr_set_tiles(self._h, int(axis), int(C), int(L)))
+
+    def sweep_forms(self):
+        f = (c_int * 3)()
+        self._check(load().ppmlr_get_sweep_forms(self._h, f))
+        return list(f)
+
+    def set_sweep_form(self, axis, form, raise_on_error=True):
+        st = load().ppmlr_set_sweep_form(self._h, int(axis), int(form))
+        return self._check(st) if raise_on_error else st
 
 
 class Ensemble:
