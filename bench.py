@@ -159,6 +159,13 @@ class ClockSampler:
 
 # ------------------------------------------------------------- workloads ------
 
+def parse_launch_config(text):
+    parts = text.split(":")
+    if len(parts) != 3:
+        raise argparse.ArgumentTypeError("need three C,L,form groups separated by ':'")
+    return [tuple(int(v) for v in q.split(",")) for q in parts]
+
+
 def workload(args):
     from paper_1607_02214_gb300 import inputs
     n = tuple(args.grid)
@@ -257,7 +264,11 @@ def run_ours(args, rank, world, dist):
     def timed_run(precision, steps, warmup, with_clocks=False):
         ctx = ppmlr.Context.from_problem(prob, precision)
         ctx.set_state(U0)
-        if not args.no_autotune:
+        if args.launch_config and precision == prec:
+            for axis, (C, L, form) in enumerate(args.launch_config):
+                ctx.set_tiles(axis, C, L)
+                ctx.set_sweep_form(axis, form)
+        elif not args.no_autotune:
             ctx.autotune()
         ctx.step_cfl(prob.cfl, warmup)
         ctx.check()
@@ -568,6 +579,9 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--launch-config", type=parse_launch_config, default=None,
+                    help="fixed tiles and launch forms of the main precision instead of the autotuner: "
+                         "C,L,form for x:y:z, e.g. 256,1,0:64,4,2:64,4,2")
     ap.add_argument("--ensemble-only", action="store_true", help="only the 48-instance ensemble section")
     args = ap.parse_args()
     if args.warmup < 3:

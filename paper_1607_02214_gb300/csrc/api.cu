@@ -151,7 +151,7 @@ Tile ppmlr::make_tile(int dir, const int n[3], size_t real_size, int C, int L)
         t.ntiles = t.ngx * other * t.nchunk;
     }
     t.threads = ((t.NP * t.L + 31) / 32) * 32;
-    t.smem = (size_t)NSM * t.NP * t.L * real_size;
+    t.smem = (size_t)NSMP * t.NP * t.L * real_size;
     return t;
 }
 

@@ -12,7 +12,8 @@
 namespace ppmlr {
 
 constexpr int GH = 7;          // ghost cells per pencil end: the stencil radius of one sweep
-constexpr int NSM = 28;        // shared-memory exchange arrays per tile (see sweep.cuh)
+constexpr int NSM = 28;        // shared-memory exchange values per slot (see sweep.cuh)
+constexpr int NSMP = 29;       // slot pitch in values: odd, so consecutive slots hit distinct banks
 constexpr int MAXT = 512;      // threads per tile (one thread per cell position and lane), mixed path
 constexpr int MAXT_F64 = 448;  // FP64 path: fewer threads, up to 146 registers each
 

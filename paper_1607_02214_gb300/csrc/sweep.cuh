@@ -8,8 +8,10 @@
 // Thread layout: a tile is L pencils ("lanes") x NP = C + 2*GH positions along
 // the sweep axis; one thread owns one (position, lane) for the whole kernel
 // and keeps its own cell's values in registers between phases.  Only what a
-// neighbour needs crosses threads, through NSM shared-memory arrays of NP*L
-// entries that are reused from phase to phase (barrier-separated).  The thread
+// neighbour needs crosses threads, through NSM shared-memory values per slot
+// (slot-major with an odd pitch NSMP, so a warp's accesses to one value hit 32
+// distinct banks and every value of a slot sits at a constant offset from the
+// slot's address) that are reused from phase to phase (barrier-separated).  The thread
 // index is the shared-memory slot: x sweeps run positions fastest (contiguous
 // global rows), y and z sweeps run lanes fastest (consecutive x cells, so every
 // global access of a warp is a set of contiguous row segments: coalesced, no
@@ -139,6 +141,12 @@ __device__ __forceinline__ R limit_slope(R am, R a0, R ap, R c1, R c2, R c3)
         if (mag_d(lim_p) < mag_d(m)) m = lim_p;
         return pos_d(da) ? m : (neg_d(da) ? -m : 0.0);
     }
+    if constexpr (!EX && std::is_same<R, float>::value) {   // branch-free: min/max and selects
+        const float dp = ap - a0, dm = a0 - am;
+        const float da = c1 * (c2 * dp + c3 * dm);
+        const float m = fminf(fabsf(da), 2.0f * fminf(fabsf(dm), fabsf(dp)));
+        return dp * dm > 0.0f ? copysignf(m, da) : 0.0f;
+    }
     R dp = ap - a0;
     R dm = a0 - am;
     R da = c1 * (c2 * dp + c3 * dm);
@@ -170,6 +178,18 @@ __device__ __forceinline__ R monotone(R ai, R &l, R &r)
             else if (pos_d(da) ? om < onda : om > onda) r = 3.0 * ai - 2.0 * l;
         }
         return 6.0 * (ai - 0.5 * (l + r));
+    }
+    if constexpr (!EX && std::is_same<R, float>::value) {   // branch-free: selects only
+        const float da = r - l;
+        const float m6 = 6.0f * (ai - 0.5f * (l + r));
+        const float dm6 = da * m6, dd = da * da;
+        const bool ext = (r - ai) * (ai - l) <= 0.0f;
+        const bool lo = dm6 > dd, hi = !lo && -dd > dm6;
+        const float nl = lo ? 3.0f * ai - 2.0f * r : l;
+        const float nr = hi ? 3.0f * ai - 2.0f * l : r;
+        l = ext ? ai : nl;
+        r = ext ? ai : nr;
+        return 6.0f * (ai - 0.5f * (l + r));
     }
     if ((r - ai) * (ai - l) <= R(0)) {
         l = ai; r = ai;
@@ -277,7 +297,7 @@ enum : int {
 // One tile of one sweep, processed by the calling block.  `a` describes the
 // domain (the single-domain kernel passes its launch argument, the ensemble
 // kernel a per-instance copy in shared memory); `tile` is the tile index
-// within that domain; `smem_raw` holds NSM * NP * L values of type R.
+// within that domain; `smem_raw` holds NSMP * NP * L values of type R.
 // EX (double only): every stage evaluates the reference's expression trees;
 // otherwise quotients sharing a denominator use one reciprocal.
 // `stage` (optional): this tile's input box staged in shared memory by TMA,
@@ -302,7 +322,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     const int L = L_, NP = NP_, NT = NP * L;
     const int PS = DIR == 0 ? 1 : L;
     const int s = threadIdx.x;
-#define SM(k, slot) sm[(k) * NT + (slot)]
+#define SM(k, slot) sm[(slot) * NSMP + (k)]
 
     // ---- tile decode ----
     const int chunk = tile % a.nchunk;
