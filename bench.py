@@ -407,6 +407,10 @@ def run_ours(args, rank, world, dist):
                "d2h_bytes_per_step": nbytes, "steps": ksteps}
         del ectx
 
+    # ---- long run: graph-replayed steps, real-time factor, checkpoint I/O
+    if not args.quick and not args.no_steady and world == 1:
+        extra["steady"] = run_steady(args, prob, U0, barrier)
+
     # ---- batched ensemble: 48 seeded instances on uneven grids (mixed path);
     # with N ranks each owns a round-robin share of the instances
     if not args.quick and not args.no_ensemble:
@@ -434,6 +438,53 @@ def run_ours(args, rank, world, dist):
            "clocks": clocks, "gpu_launches": launches, "kernels": per_kernel, "kernel_src": src_hash,
            "tiles": {"C_L": ctx.tiles(), "forms": ctx.sweep_forms()}}
     out.update(extra)
+    return out
+
+
+def run_steady(args, prob, U0, barrier):
+    """The magnetosphere run as it is used in production: many steps with the
+    device CFL time step, replayed from CUDA graphs of 16 steps.  Reports the
+    real-time factor (simulated seconds per wall-clock second; the code time
+    unit is R_E / 100 km/s) per precision, and the time to write and read a
+    checksummed checkpoint of the state."""
+    import tempfile
+    import torch
+    from paper_1607_02214_gb300 import inputs, ppmlr
+    t_unit = inputs.R_E_KM * 1e3 / inputs.V0
+    out = {"graph_steps": 16, "time_unit_s": t_unit}
+    for key, precision, nsteps in (("mixed", ppmlr.PPMLR_MIXED, 640), ("fp64", ppmlr.PPMLR_FP64, 48)):
+        ctx = ppmlr.Context.from_problem(prob, precision)
+        ctx.set_state(U0)
+        ctx.autotune()
+        ctx.run(prob.cfl, 16, graph_steps=16)      # captures both parities' graphs
+        ctx.run(prob.cfl, 16, graph_steps=16)
+        ctx.check()
+        t_start = ctx.time
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        ctx.run(prob.cfl, nsteps, graph_steps=16)
+        e1.record(stream)
+        e1.synchronize()
+        wall = e0.elapsed_time(e1) * 1e-3
+        ctx.check()
+        sim = (ctx.time - t_start) * t_unit
+        out[key] = {"steps": nsteps, "ms_per_step": wall * 1e3 / nsteps, "sim_seconds": sim, "wall_seconds": wall,
+                    "real_time_factor": sim / wall, "mean_dt_s": sim / nsteps}
+        if key == "mixed":
+            with tempfile.TemporaryDirectory() as d:
+                path = os.path.join(d, "state.ck")
+                t0 = time.perf_counter()
+                ctx.checkpoint_save(path)
+                t1 = time.perf_counter()
+                ctx.checkpoint_load(path)
+                t2 = time.perf_counter()
+                size = os.path.getsize(path)
+            out["checkpoint"] = {"bytes": size, "save_s": t1 - t0, "load_s": t2 - t1}
+        ctx.close()
+    log(f"[bench] steady: real-time factor mixed {out['mixed']['real_time_factor']:.1f}, "
+        f"fp64 {out['fp64']['real_time_factor']:.2f}")
     return out
 
 
@@ -578,6 +629,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-steady", action="store_true", help="skip the long graph-replayed run")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--launch-config", type=parse_launch_config, default=None,
                     help="fixed tiles and launch forms of the main precision instead of the autotuner: "

@@ -205,6 +205,52 @@ ppmlr_status ppmlr_get_sweep_forms(ppmlr_ctx *ctx, int *form);
 /* Select a launch form for one axis (PPMLR_E_INVALID if not available). */
 ppmlr_status ppmlr_set_sweep_form(ppmlr_ctx *ctx, int axis, int form);
 
+/* ---- Long runs: graph replay, simulated time, checkpoints -----------------
+ * The paper's production use is a magnetosphere driven to a steady state
+ * over many steps, run faster than real time (Secs. I and IV-A); none of the
+ * calls below changes the arithmetic of a step. */
+
+/* nsteps steps exactly as ppmlr_step_cfl (same dt, same results bit for
+ * bit), replayed from CUDA graphs of graph_steps steps each (a CFL pass and
+ * three sweeps per step; graph_steps even, 2..4096), with any remainder
+ * launched directly; graph_steps = 0 launches every kernel directly.  Graphs
+ * are captured on first use for the current step parity, input buffer,
+ * length and cfl, kept by the context and dropped when the tile shapes or
+ * launch forms change.  Asynchronous.  PPMLR_E_INVALID for cfl <= 0,
+ * nsteps < 0 or an odd or out-of-range graph_steps. */
+ppmlr_status ppmlr_run(ppmlr_ctx *ctx, double cfl, long long nsteps, int graph_steps);
+
+/* Simulated time in code units (R_E / v0 with v0 = 100 km/s: 63.712 s): the
+ * FP64 sum of the dt of every step since creation or the last
+ * ppmlr_set_time / ppmlr_checkpoint_load.  Device-dt steps (ppmlr_step_cfl,
+ * ppmlr_run) add on the device; ppmlr_step adds its dt on the host.
+ * Synchronises. */
+ppmlr_status ppmlr_get_time(ppmlr_ctx *ctx, double *t_out);
+ppmlr_status ppmlr_set_time(ppmlr_ctx *ctx, double t);
+
+/* Checkpoint of the state, step counter and simulated time.  File layout
+ * (little-endian): a 56-byte header -- magic "PPMLRCK1", u32 version (1),
+ * u32 precision, i32 n[3], i32 0, i64 step, f64 time, f64 gamma -- then the
+ * grid edges of x, y, z (n[d] + 1 doubles each), the 8 conserved arrays
+ * (n0*n1*n2 doubles each, x fastest; rho, m_x, m_y, m_z, B'_x, B'_y, B'_z,
+ * E) and a u64 checksum: FNV-1a (offset 0xcbf29ce484222325, prime
+ * 0x100000001b3) over all preceding bytes taken as 64-bit words.
+ * ppmlr_checkpoint_save synchronises, writes `path`.part and renames it to
+ * `path` (PPMLR_E_INVALID if the file cannot be written); it then reports
+ * pending device flags.  ppmlr_checkpoint_load verifies the whole file
+ * (magic, version, checksum, grid size and edges bit for bit against the
+ * context's) before it replaces the state, step counter and simulated time;
+ * otherwise PPMLR_E_INVALID with the state unchanged.  A checkpoint of any
+ * precision loads into a context of any precision (the state is FP64).
+ * Loading a checkpoint of step k and continuing reproduces an uninterrupted
+ * run bit for bit (state and time). */
+ppmlr_status ppmlr_checkpoint_save(ppmlr_ctx *ctx, const char *path);
+ppmlr_status ppmlr_checkpoint_load(ppmlr_ctx *ctx, const char *path);
+/* Host only (no device, no context): verify a checkpoint file and read its
+ * header fields (any output pointer may be NULL).  PPMLR_E_INVALID if the
+ * file is missing, truncated or corrupt. */
+ppmlr_status ppmlr_checkpoint_info(const char *path, int n[3], long long *step, double *time, int *precision);
+
 /* ---- Batched ensemble ----------------------------------------------------
  * count independent instances, each with its own grid and boundary
  * specification (e.g. different solar-wind and IMF inputs, uneven grid

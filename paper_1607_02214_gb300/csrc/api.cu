@@ -3,6 +3,7 @@
 // device status word.  Built with -ffp-contract=off so that the geometry is
 // computed with the same IEEE double operations as the CPU reference.
 #include <math.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -48,6 +49,16 @@ struct ppmlr_ctx {
     long long steps;
     long long launches;
     std::string err;
+    // simulated time: device accumulator (dt_dev[1], steps with a device dt)
+    // plus the explicit dt of ppmlr_step, summed on the host
+    double t_host;
+    std::vector<double> edges[3];   // host copies of the grid edges (checkpoint validation)
+    // graph replay of ppmlr_run: one executable graph per starting step
+    // parity, input buffer, length and CFL number; dropped when the tiles or
+    // launch forms change
+    cudaStream_t cap;
+    struct Graph { int parity, buf, ksteps; double cfl; cudaGraphExec_t exec; long long launches; };
+    std::vector<Graph> graphs;
     // per-kernel timing records (kind, start, stop) and a pool of spare events
     bool timing;
     struct Rec { int kind; cudaEvent_t a, b; };
@@ -301,6 +312,9 @@ ppmlr_status ppmlr_create(const ppmlr_grid *grid, double gamma, const ppmlr_bc *
     c->steps = 0;
     c->launches = 0;
     c->timing = false;
+    c->t_host = 0.0;
+    c->cap = nullptr;
+    for (int d = 0; d < 3; d++) c->edges[d].assign(grid->edges[d], grid->edges[d] + grid->n[d] + 1);
     if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return PPMLR_E_CUDA; }
 
     // state: 16 arrays, each padded to 256-byte multiples
@@ -355,10 +369,18 @@ ppmlr_status ppmlr_create(const ppmlr_grid *grid, double gamma, const ppmlr_bc *
     return PPMLR_OK;
 }
 
+static void drop_graphs(ppmlr_ctx *c)
+{
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+}
+
 void ppmlr_destroy(ppmlr_ctx *c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    if (c->cap) cudaStreamDestroy(c->cap);
     for (auto &r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->pool) cudaEventDestroy(e);
     cudaFree(c->geof);
@@ -493,10 +515,13 @@ ppmlr_status ppmlr_step(ppmlr_ctx *c, double dt)
 {
     if (!c) return PPMLR_E_INVALID;
     if (!(dt > 0.0) || !isfinite(dt)) return fail(c, PPMLR_E_INVALID, "step: dt must be finite and > 0");
-    return do_step(c, dt, nullptr);
+    ppmlr_status s = do_step(c, dt, nullptr);
+    if (s == PPMLR_OK) c->t_host += dt;
+    return s;
 }
 
-static ppmlr_status launch_cfl_kernel(ppmlr_ctx *c, double cfl)
+// advance_time: the kernel also adds the new dt to the device time accumulator
+static ppmlr_status launch_cfl_kernel(ppmlr_ctx *c, double cfl, bool advance_time = false)
 {
     CflArgs a;
     memset(&a, 0, sizeof(a));
@@ -505,6 +530,7 @@ static ppmlr_status launch_cfl_kernel(ppmlr_ctx *c, double cfl)
     a.gamma = c->gamma; a.p_min = c->bc.p_min; a.M = c->bc.dipole_moment; a.r_inner = c->bc.r_inner;
     a.cfl = cfl;
     a.partial = c->partial; a.counter = c->counter; a.dt_out = c->dt_dev;
+    a.t_acc = advance_time ? c->dt_dev + 1 : nullptr;
     for (int d = 0; d < 3; d++) { a.wf[d] = c->wf[d]; a.cf[d] = c->cf[d]; }
     a.gammaf = (float)a.gamma; a.p_minf = (float)a.p_min; a.Mf = (float)a.M; a.r_innerf = (float)a.r_inner;
     int rec = timing_begin(c, 3);
@@ -525,17 +551,22 @@ ppmlr_status ppmlr_cfl_dt(ppmlr_ctx *c, double cfl, double *dt_out)
     return read_flags(c);
 }
 
-ppmlr_status ppmlr_step_cfl(ppmlr_ctx *c, double cfl, int nsteps)
+static ppmlr_status step_cfl_direct(ppmlr_ctx *c, double cfl, long long nsteps)
 {
-    if (!c) return PPMLR_E_INVALID;
-    if (!(cfl > 0.0) || nsteps < 0) return fail(c, PPMLR_E_INVALID, "step_cfl: need cfl > 0, nsteps >= 0");
-    for (int k = 0; k < nsteps; k++) {
-        ppmlr_status s = launch_cfl_kernel(c, cfl);
+    for (long long k = 0; k < nsteps; k++) {
+        ppmlr_status s = launch_cfl_kernel(c, cfl, true);
         if (s != PPMLR_OK) return s;
         s = do_step(c, 0.0, c->dt_dev);
         if (s != PPMLR_OK) return s;
     }
     return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_step_cfl(ppmlr_ctx *c, double cfl, int nsteps)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (!(cfl > 0.0) || nsteps < 0) return fail(c, PPMLR_E_INVALID, "step_cfl: need cfl > 0, nsteps >= 0");
+    return step_cfl_direct(c, cfl, nsteps);
 }
 
 ppmlr_status ppmlr_get_dt(ppmlr_ctx *c, double *dt_out)
@@ -578,6 +609,7 @@ ppmlr_status ppmlr_autotune(ppmlr_ctx *c, double *best_ms)
     CK(c, cudaEventCreate(&t1), "event");
     const bool was_timing = c->timing;
     c->timing = false;
+    drop_graphs(c);
     for (int d = 0; d < 3; d++) {
         if (best_ms) best_ms[d] = 0.0;
         if (is_sweep_noop(c, d)) continue;
@@ -671,6 +703,7 @@ ppmlr_status ppmlr_set_tiles(ppmlr_ctx *c, int axis, int C, int L)
     if ((long long)(C + 2 * GH) * L > maxt) return fail(c, PPMLR_E_INVALID, "set_tiles: (C + 14) * L exceeds the thread budget");
     c->tile[axis] = make_tile(axis, c->n, rs, C, L);
     c->mode[axis] = 0;
+    drop_graphs(c);
     return PPMLR_OK;
 }
 
@@ -685,6 +718,7 @@ ppmlr_status ppmlr_set_sweep_form(ppmlr_ctx *c, int axis, int form)
 {
     if (!c) return PPMLR_E_INVALID;
     if (axis < 0 || axis > 2 || form < 0 || form > 2) return fail(c, PPMLR_E_INVALID, "set_sweep_form: bad axis or form");
+    drop_graphs(c);
     if (form == 0) { c->mode[axis] = 0; return PPMLR_OK; }
     if (const char *why = setup_tma_why(c, axis, form)) return fail(c, PPMLR_E_INVALID, why);
     c->mode[axis] = form;
@@ -722,6 +756,269 @@ ppmlr_status ppmlr_set_step_count(ppmlr_ctx *c, long long step)
     if (!c) return PPMLR_E_INVALID;
     if (step < 0) return fail(c, PPMLR_E_INVALID, "set_step_count: negative");
     c->steps = step;
+    return PPMLR_OK;
+}
+
+// ---- long runs: simulated time, graph replay, checkpoints ----
+
+ppmlr_status ppmlr_get_time(ppmlr_ctx *c, double *t_out)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (!t_out) return fail(c, PPMLR_E_INVALID, "get_time: null output");
+    double td = 0.0;
+    CK(c, cudaMemcpyAsync(&td, c->dt_dev + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "time copy");
+    CK(c, cudaStreamSynchronize(c->stream), "stream sync");
+    *t_out = c->t_host + td;
+    return PPMLR_OK;
+}
+
+static ppmlr_status put_device_time(ppmlr_ctx *c, double t)
+{
+    CK(c, cudaMemcpyAsync(c->dt_dev + 1, &t, sizeof(double), cudaMemcpyHostToDevice, c->stream), "time copy");
+    CK(c, cudaStreamSynchronize(c->stream), "stream sync");
+    c->t_host = 0.0;
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_set_time(ppmlr_ctx *c, double t)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (!isfinite(t)) return fail(c, PPMLR_E_INVALID, "set_time: t must be finite");
+    return put_device_time(c, t);
+}
+
+// Captures ksteps steps (CFL pass + three sweeps each) from the current step
+// parity and input buffer into an executable graph.  The host-side view
+// (step count, launch count, buffer roles) is left as it was: the graph has
+// not run yet.
+static ppmlr_status capture_run_graph(ppmlr_ctx *c, double cfl, int ksteps, ppmlr_ctx::Graph &g)
+{
+    if (!c->cap) CK(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "capture stream");
+    const cudaStream_t user = c->stream;
+    const bool was_timing = c->timing;
+    const long long steps0 = c->steps, launches0 = c->launches;
+    double *U0[8], *Un0[8];
+    memcpy(U0, c->U, sizeof(U0));
+    memcpy(Un0, c->Un, sizeof(Un0));
+    g.parity = (int)(c->steps & 1);
+    g.buf = c->U[0] == c->state ? 0 : 1;
+    g.ksteps = ksteps;
+    g.cfl = cfl;
+    g.exec = nullptr;
+    c->timing = false;
+    c->stream = c->cap;
+    cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+    ppmlr_status st = e == cudaSuccess ? PPMLR_OK : cuda_fail(c, e, "begin capture");
+    for (int k = 0; st == PPMLR_OK && k < ksteps; k++) {
+        st = launch_cfl_kernel(c, cfl, true);
+        if (st == PPMLR_OK) st = do_step(c, 0.0, c->dt_dev);
+    }
+    cudaGraph_t graph = nullptr;
+    if (e == cudaSuccess) {
+        cudaError_t e2 = cudaStreamEndCapture(c->cap, &graph);
+        if (st == PPMLR_OK && e2 != cudaSuccess) st = cuda_fail(c, e2, "end capture");
+    }
+    g.launches = c->launches - launches0;
+    c->stream = user;
+    c->timing = was_timing;
+    c->steps = steps0;
+    c->launches = launches0;
+    memcpy(c->U, U0, sizeof(U0));
+    memcpy(c->Un, Un0, sizeof(Un0));
+    if (st == PPMLR_OK) {
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        if (e != cudaSuccess) st = cuda_fail(c, e, "graph instantiate");
+    }
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+}
+
+ppmlr_status ppmlr_run(ppmlr_ctx *c, double cfl, long long nsteps, int graph_steps)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (!(cfl > 0.0) || !isfinite(cfl) || nsteps < 0 || graph_steps < 0 || (graph_steps & 1) || graph_steps > 4096)
+        return fail(c, PPMLR_E_INVALID, "run: need cfl > 0, nsteps >= 0 and an even graph_steps in [0, 4096]");
+    long long left = nsteps;
+    while (graph_steps > 0 && left >= graph_steps) {
+        const int parity = (int)(c->steps & 1), buf = c->U[0] == c->state ? 0 : 1;
+        ppmlr_ctx::Graph *g = nullptr;
+        for (auto &x : c->graphs)
+            if (x.parity == parity && x.buf == buf && x.ksteps == graph_steps && x.cfl == cfl) { g = &x; break; }
+        if (!g) {
+            ppmlr_ctx::Graph ng;
+            ppmlr_status st = capture_run_graph(c, cfl, graph_steps, ng);
+            if (st != PPMLR_OK) return st;
+            c->graphs.push_back(ng);
+            g = &c->graphs.back();
+        }
+        CK(c, cudaGraphLaunch(g->exec, c->stream), "graph launch");
+        // an even number of steps swaps the buffers an even number of times
+        c->steps += graph_steps;
+        c->launches += g->launches;
+        left -= graph_steps;
+    }
+    return step_cfl_direct(c, cfl, left);
+}
+
+}  // extern "C"
+
+// Checkpoint file (little-endian): a 56-byte header (magic "PPMLRCK1",
+// u32 version 1, u32 precision, i32 n[3], i32 0, i64 step, f64 simulated
+// time, f64 gamma), the grid edges of x, y, z (n[d] + 1 doubles each), the
+// 8 state arrays (n0*n1*n2 doubles each, x fastest), then a u64 checksum:
+// FNV-1a over the preceding bytes taken as 64-bit words.
+namespace {
+struct CkHeader {
+    char magic[8];
+    uint32_t version, precision;
+    int32_t n[3], reserved;
+    int64_t step;
+    double time, gamma;
+};
+static_assert(sizeof(CkHeader) == 56, "checkpoint header layout");
+const char k_magic[8] = {'P', 'P', 'M', 'L', 'R', 'C', 'K', '1'};
+
+struct Fnv64 {
+    uint64_t h = 0xcbf29ce484222325ull;
+    void add(const void *p, size_t bytes)      // bytes: a multiple of 8
+    {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        for (size_t k = 0; k + 8 <= bytes; k += 8) {
+            uint64_t w;
+            memcpy(&w, b + k, 8);
+            h ^= w;
+            h *= 0x100000001b3ull;
+        }
+    }
+};
+
+struct File {
+    FILE *f = nullptr;
+    ~File() { if (f) fclose(f); }
+};
+
+// Reads and verifies a checkpoint; `sink(v, data)` receives state array v.
+// Returns nullptr or the reason it is not a valid checkpoint.
+template <typename Sink>
+const char *read_checkpoint(const char *path, CkHeader &h, std::vector<double> edges[3], Sink sink)
+{
+    File in;
+    in.f = fopen(path, "rb");
+    if (!in.f) return "checkpoint: cannot open the file";
+    Fnv64 hash;
+    if (fread(&h, sizeof(h), 1, in.f) != 1) return "checkpoint: truncated header";
+    if (memcmp(h.magic, k_magic, 8) != 0 || h.version != 1) return "checkpoint: not a version-1 checkpoint";
+    if (h.n[0] < 1 || h.n[1] < 1 || h.n[2] < 1 || (long long)h.n[0] * h.n[1] * h.n[2] > (1LL << 31) - 1)
+        return "checkpoint: bad grid size";
+    hash.add(&h, sizeof(h));
+    for (int d = 0; d < 3; d++) {
+        edges[d].resize((size_t)h.n[d] + 1);
+        if (fread(edges[d].data(), sizeof(double), edges[d].size(), in.f) != edges[d].size())
+            return "checkpoint: truncated edges";
+        hash.add(edges[d].data(), sizeof(double) * edges[d].size());
+    }
+    const size_t ncell = (size_t)h.n[0] * h.n[1] * h.n[2];
+    std::vector<double> buf(ncell);
+    for (int v = 0; v < 8; v++) {
+        if (fread(buf.data(), sizeof(double), ncell, in.f) != ncell) return "checkpoint: truncated state";
+        hash.add(buf.data(), sizeof(double) * ncell);
+        if (const char *why = sink(v, buf.data())) return why;
+    }
+    uint64_t sum = 0;
+    if (fread(&sum, sizeof(sum), 1, in.f) != 1) return "checkpoint: missing checksum";
+    if (fgetc(in.f) != EOF) return "checkpoint: trailing bytes";
+    if (sum != hash.h) return "checkpoint: checksum mismatch";
+    return nullptr;
+}
+}  // namespace
+
+extern "C" {
+
+ppmlr_status ppmlr_checkpoint_save(ppmlr_ctx *c, const char *path)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (!path || !*path) return fail(c, PPMLR_E_INVALID, "checkpoint_save: empty path");
+    double t = 0.0;
+    ppmlr_status st = ppmlr_get_time(c, &t);
+    if (st != PPMLR_OK) return st;
+    CkHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, k_magic, 8);
+    h.version = 1;
+    h.precision = (uint32_t)c->prec;
+    for (int d = 0; d < 3; d++) h.n[d] = c->n[d];
+    h.step = c->steps;
+    h.time = t;
+    h.gamma = c->gamma;
+    const std::string tmp = std::string(path) + ".part";
+    File out;
+    out.f = fopen(tmp.c_str(), "wb");
+    if (!out.f) return fail(c, PPMLR_E_INVALID, "checkpoint_save: cannot create " + tmp);
+    Fnv64 hash;
+    bool ok = fwrite(&h, sizeof(h), 1, out.f) == 1;
+    hash.add(&h, sizeof(h));
+    for (int d = 0; d < 3 && ok; d++) {
+        ok = fwrite(c->edges[d].data(), sizeof(double), c->edges[d].size(), out.f) == c->edges[d].size();
+        hash.add(c->edges[d].data(), sizeof(double) * c->edges[d].size());
+    }
+    std::vector<double> buf((size_t)c->ncell);
+    for (int v = 0; v < 8 && ok; v++) {
+        CK(c, cudaMemcpyAsync(buf.data(), c->U[v], sizeof(double) * buf.size(), cudaMemcpyDeviceToHost, c->stream),
+           "checkpoint copy");
+        CK(c, cudaStreamSynchronize(c->stream), "stream sync");
+        ok = fwrite(buf.data(), sizeof(double), buf.size(), out.f) == buf.size();
+        hash.add(buf.data(), sizeof(double) * buf.size());
+    }
+    if (ok) ok = fwrite(&hash.h, sizeof(hash.h), 1, out.f) == 1;
+    if (fclose(out.f) != 0) ok = false;
+    out.f = nullptr;
+    if (!ok || rename(tmp.c_str(), path) != 0) {
+        remove(tmp.c_str());
+        return fail(c, PPMLR_E_INVALID, std::string("checkpoint_save: write failed for ") + path);
+    }
+    return read_flags(c);
+}
+
+ppmlr_status ppmlr_checkpoint_load(ppmlr_ctx *c, const char *path)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (!path) return fail(c, PPMLR_E_INVALID, "checkpoint_load: null path");
+    CK(c, cudaStreamSynchronize(c->stream), "stream sync");
+    CkHeader h;
+    std::vector<double> edges[3];
+    cudaError_t ce = cudaSuccess;
+    // the arrays go to the output buffers first: the state changes only once
+    // the whole file has been verified
+    const char *why = read_checkpoint(path, h, edges, [&](int v, const double *data) -> const char * {
+        if (v == 0) {
+            for (int d = 0; d < 3; d++)
+                if (h.n[d] != c->n[d]) return "checkpoint: grid size differs from the context's";
+            for (int d = 0; d < 3; d++)
+                if (memcmp(edges[d].data(), c->edges[d].data(), sizeof(double) * edges[d].size()) != 0)
+                    return "checkpoint: grid edges differ from the context's";
+        }
+        ce = cudaMemcpy(c->Un[v], data, sizeof(double) * (size_t)c->ncell, cudaMemcpyHostToDevice);
+        return ce == cudaSuccess ? nullptr : "checkpoint: device copy failed";
+    });
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "checkpoint copy");
+    if (why) return fail(c, PPMLR_E_INVALID, why);
+    for (int v = 0; v < 8; v++) { double *tmp = c->U[v]; c->U[v] = c->Un[v]; c->Un[v] = tmp; }
+    c->steps = h.step;
+    CK(c, cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream), "flags reset");
+    return put_device_time(c, h.time);
+}
+
+ppmlr_status ppmlr_checkpoint_info(const char *path, int n[3], long long *step, double *time, int *precision)
+{
+    if (!path) return PPMLR_E_INVALID;
+    CkHeader h;
+    std::vector<double> edges[3];
+    if (read_checkpoint(path, h, edges, [](int, const double *) -> const char * { return nullptr; }))
+        return PPMLR_E_INVALID;
+    if (n) for (int d = 0; d < 3; d++) n[d] = h.n[d];
+    if (step) *step = h.step;
+    if (time) *time = h.time;
+    if (precision) *precision = (int)h.precision;
     return PPMLR_OK;
 }
 

@@ -133,7 +133,9 @@ __device__ __forceinline__ void cfl_body(const CflArgs &a, const int bid, const 
         }
         m = block_min(m);
         if (threadIdx.x == 0) {
-            *a.dt_out = a.cfl * m;
+            const double dt = a.cfl * m;
+            *a.dt_out = dt;
+            if (a.t_acc) *a.t_acc += dt;
             *a.counter = 0u;
         }
     }

@@ -80,7 +80,9 @@ __device__ __forceinline__ void cfl_mixed_body(const CflArgs &a, const int bid, 
         }
         float mf = block_min_f((float)m);   // exact: every partial is a widened float
         if (threadIdx.x == 0) {
-            *a.dt_out = a.cfl * widen(mf);
+            const double dt = a.cfl * widen(mf);
+            *a.dt_out = dt;
+            if (a.t_acc) *a.t_acc += dt;
             *a.counter = 0u;
         }
     }

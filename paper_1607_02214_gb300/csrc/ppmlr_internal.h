@@ -85,6 +85,7 @@ struct CflArgs {
     double *partial;           // one entry per block
     unsigned int *counter;     // zero between launches; the last block resets it
     double *dt_out;            // device scalar
+    double *t_acc;             // device scalar or null: the last block adds dt (simulated time)
 };
 
 // Tile shape of one sweep direction.

@@ -62,6 +62,13 @@ SIGNATURES = [
     ("ppmlr_get_sweep_forms", c_int, [c_void_p, POINTER(c_int)]),
     ("ppmlr_set_sweep_form", c_int, [c_void_p, c_int, c_int]),
     ("ppmlr_set_tiles", c_int, [c_void_p, c_int, c_int, c_int]),
+    ("ppmlr_run", c_int, [c_void_p, c_double, c_longlong, c_int]),
+    ("ppmlr_get_time", c_int, [c_void_p, POINTER(c_double)]),
+    ("ppmlr_set_time", c_int, [c_void_p, c_double]),
+    ("ppmlr_checkpoint_save", c_int, [c_void_p, ctypes.c_char_p]),
+    ("ppmlr_checkpoint_load", c_int, [c_void_p, ctypes.c_char_p]),
+    ("ppmlr_checkpoint_info", c_int, [ctypes.c_char_p, POINTER(c_int), POINTER(c_longlong), POINTER(c_double),
+                                      POINTER(c_int)]),
     ("ppmlr_ensemble_create", c_int, [c_int, POINTER(ppmlr_grid), POINTER(ppmlr_bc), c_double, c_int, c_void_p,
                                       POINTER(c_void_p)]),
     ("ppmlr_ensemble_set_stream", c_int, [c_void_p, c_void_p]),
@@ -259,6 +266,28 @@ class Context:
         self._check(load().ppmlr_get_dt(self._h, ctypes.byref(dt)))
         return dt.value
 
+    def run(self, cfl, nsteps, graph_steps=16):
+        """nsteps device-dt steps (as step_cfl), replayed from CUDA graphs of
+        graph_steps steps (0: direct launches)."""
+        return self._check(load().ppmlr_run(self._h, float(cfl), int(nsteps), int(graph_steps)))
+
+    @property
+    def time(self):
+        """Simulated time in code units (R_E / 100 km/s)."""
+        t = c_double()
+        self._check(load().ppmlr_get_time(self._h, ctypes.byref(t)))
+        return t.value
+
+    @time.setter
+    def time(self, t):
+        self._check(load().ppmlr_set_time(self._h, float(t)))
+
+    def checkpoint_save(self, path):
+        return self._check(load().ppmlr_checkpoint_save(self._h, os.fsencode(path)))
+
+    def checkpoint_load(self, path):
+        return self._check(load().ppmlr_checkpoint_load(self._h, os.fsencode(path)))
+
     @property
     def launch_count(self):
         return load().ppmlr_launch_count(self._h)
@@ -297,6 +326,16 @@ class Context:
     def set_sweep_form(self, axis, form, raise_on_error=True):
         st = load().ppmlr_set_sweep_form(self._h, int(axis), int(form))
         return self._check(st) if raise_on_error else st
+
+
+def checkpoint_info(path):
+    """Verify a checkpoint file on the host and return its header fields
+    (raises PPMLRError for a missing, truncated or corrupt file)."""
+    n, step, t, prec = (c_int * 3)(), c_longlong(), c_double(), c_int()
+    st = load().ppmlr_checkpoint_info(os.fsencode(path), n, ctypes.byref(step), ctypes.byref(t), ctypes.byref(prec))
+    if st != PPMLR_OK:
+        raise PPMLRError(st, f"invalid checkpoint {path}")
+    return {"n": list(n), "step": step.value, "time": t.value, "precision": prec.value}
 
 
 class Ensemble:
