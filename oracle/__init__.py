@@ -63,6 +63,8 @@ def lib():
         L.orc_avg_left.restype = ctypes.c_double
         L.orc_avg_left.argtypes = [ctypes.c_double] * 4
         L.orc_riemann.argtypes = [_dp, _dp, ctypes.c_double, ctypes.c_double, _dp]
+        L.orc_riemann_nl.argtypes = [_dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp]
+        L.orc_set_riemann.argtypes = [ctypes.c_void_p, ctypes.c_int]
         _lib = L
     return _lib
 
@@ -146,6 +148,11 @@ class Oracle:
     def step_count(self, s):
         lib().orc_set_step_count(self._h, int(s))
 
+    def set_riemann(self, iters):
+        """0: two-wave Riemann solver; k > 0: k two-shock Newton steps on the
+        fast mode (nonlinear variant)."""
+        lib().orc_set_riemann(self._h, int(iters))
+
     def run(self, cfl, nsteps=None, t_end=None, max_steps=10**7):
         """Advance with the CFL time step for nsteps steps or up to t_end."""
         t, k, flags = 0.0, 0, 0
@@ -199,9 +206,10 @@ def avg_left(aL, aR, a6, y):
     return lib().orc_avg_left(float(aL), float(aR), float(a6), float(y))
 
 
-def riemann(L, R, Bn, gamma):
+def riemann(L, R, Bn, gamma, iters=0):
     """L, R = (rho, u, v1, v2, B1, B2, p[, B1a, B2a]); when the Alfven-traced
-    B1a, B2a are omitted they equal B1, B2.  Returns
+    B1a, B2a are omitted they equal B1, B2.  iters = 0: two-wave solver;
+    iters > 0: that many two-shock Newton steps on the fast mode.  Returns
     (u*, P*, S*, v1*, v2*, sigma1*, sigma2*, F_E)."""
     def full(s):
         s = list(map(float, s))
@@ -210,5 +218,5 @@ def riemann(L, R, Bn, gamma):
         return np.ascontiguousarray(s, dtype=np.float64)
     Lv, Rv = full(L), full(R)
     out = np.zeros(8)
-    lib().orc_riemann(_ptr(Lv), _ptr(Rv), float(Bn), float(gamma), _ptr(out))
+    lib().orc_riemann_nl(_ptr(Lv), _ptr(Rv), float(Bn), float(gamma), int(iters), _ptr(out))
     return out

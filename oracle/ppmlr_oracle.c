@@ -65,6 +65,7 @@ typedef struct {
     double inner[8];         /* rho, vx, vy, vz, (B ignored: B' = 0 inside), p */
     double p_min;
     int powell;
+    int riemann_iters;       /* 0: two-wave Riemann solver; k > 0: k two-shock Newton steps */
     double *U;               /* [8][nz][ny][nx], x fastest */
     double *Unew;
     long long floors;
@@ -206,12 +207,47 @@ double orc_avg_left(double aL, double aR, double a6, double y)
 /* Z = sqrt(rho) |Bn|.  Both take the two-wave acoustic solution, i.e. the     */
 /* intersection of the two incoming Riemann invariants.                        */
 /* out = (u*, P*, S* = P* - Bn^2/2, v1*, v2*, sigma1*, sigma2*, F_E).           */
-void orc_riemann(const double *L, const double *R, double Bn, double gamma, double *out)
+/*                                                                            */
+/* iters > 0 selects the nonlinear variant of the normal subsystem [R: the    */
+/* two-shock Riemann solver of Colella & Woodward (1984), which the paper     */
+/* cites for its scheme, carried over to MHD by taking the fast Lagrangian    */
+/* speed C = rho c_f for the gas's rho c and the total pressure P for p].     */
+/* Each side's wave is treated as a shock whose Lagrangian speed depends on   */
+/* the middle pressure, W(P) = C sqrt(1 + (gamma+1)/(2 gamma) (P/P_s - 1)),   */
+/* so that u*_L(P) = u_L - (P - P_L)/W_L(P) and u*_R(P) = u_R + (P - P_R)/     */
+/* W_R(P).  Starting from the two-wave P*, `iters` Newton steps on            */
+/* u*_R(P) - u*_L(P) = 0, with the slope of each curve dP/du = Z =            */
+/* 2 W^3 / (W^2 + C^2) (the derivative of the curve above), move P* towards   */
+/* their intersection (P clipped at 0 where W is evaluated).  u* and P* then  */
+/* follow from the two-wave formulas with W_L, W_R at the final P*; at        */
+/* convergence they lie on both curves.  With B = 0 this is the gas-dynamic   */
+/* two-shock solver, exact when both waves are shocks.  The transverse        */
+/* (Alfven) subsystem is linear in this model and stays as above.  Without    */
+/* positive total pressures on both sides the two-wave solution is kept.      */
+void orc_riemann_nl(const double *L, const double *R, double Bn, double gamma, int iters, double *out)
 {
     double PL = L[6] + 0.5 * (L[4] * L[4] + L[5] * L[5]);
     double PR = R[6] + 0.5 * (R[4] * R[4] + R[5] * R[5]);
     double WL = L[0] * sqrt(orc_fast_speed2(L[0], L[6], Bn, L[4], L[5], gamma));
     double WR = R[0] * sqrt(orc_fast_speed2(R[0], R[6], Bn, R[4], R[5], gamma));
+    if (iters > 0 && PL > 0.0 && PR > 0.0) {
+        double CL = WL, CR = WR;
+        double a = (gamma + 1.0) / (2.0 * gamma);
+        double P = (WR * PL + WL * PR + WL * WR * (L[1] - R[1])) / (WL + WR);
+        for (int k = 0; k < iters; k++) {
+            double Pc = P > 0.0 ? P : 0.0;
+            double WLk = CL * sqrt(1.0 + a * (Pc / PL - 1.0));
+            double WRk = CR * sqrt(1.0 + a * (Pc / PR - 1.0));
+            double uLk = L[1] - (Pc - PL) / WLk;
+            double uRk = R[1] + (Pc - PR) / WRk;
+            double ZL = 2.0 * WLk * WLk * WLk / (WLk * WLk + CL * CL);
+            double ZR = 2.0 * WRk * WRk * WRk / (WRk * WRk + CR * CR);
+            P = Pc - ZL * ZR * (uRk - uLk) / (ZL + ZR);
+        }
+        double Pc = P > 0.0 ? P : 0.0;
+        WL = CL * sqrt(1.0 + a * (Pc / PL - 1.0));
+        WR = CR * sqrt(1.0 + a * (Pc / PR - 1.0));
+    }
     double us = (WL * L[1] + WR * R[1] + PL - PR) / (WL + WR);
     double Ps = (WR * PL + WL * PR + WL * WR * (L[1] - R[1])) / (WL + WR);
     double Ss = Ps - 0.5 * Bn * Bn;
@@ -232,6 +268,11 @@ void orc_riemann(const double *L, const double *R, double Bn, double gamma, doub
     out[0] = us; out[1] = Ps; out[2] = Ss;
     out[3] = vs[0]; out[4] = vs[1]; out[5] = ss[0]; out[6] = ss[1];
     out[7] = Ss * us - ss[0] * vs[0] - ss[1] * vs[1];
+}
+
+void orc_riemann(const double *L, const double *R, double Bn, double gamma, double *out)
+{
+    orc_riemann_nl(L, R, Bn, gamma, 0, out);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -297,6 +338,7 @@ void orc_get_state(const orc_ctx *c, double *U) { memcpy(U, c->U, sizeof(double)
 long long orc_floor_hits(const orc_ctx *c) { return c->floors; }
 long long orc_step_count(const orc_ctx *c) { return c->steps; }
 void orc_set_step_count(orc_ctx *c, long long s) { c->steps = s; }
+void orc_set_riemann(orc_ctx *c, int iters) { c->riemann_iters = iters > 0 ? iters : 0; }
 
 int orc_set_threads(int t)
 {
@@ -501,7 +543,7 @@ static void sweep_pencil(orc_ctx *c, int d, int j, int k, double dt, pencil_buf 
         double Ls[NTR], Rs[NTR], o[8];
         for (int v = 0; v < NTR; v++) { Ls[v] = b->sl[v][p]; Rs[v] = b->sr[v][p + 1]; }
         double Bnf = 0.5 * (b->Bn[p] + b->Bn[p + 1]);
-        orc_riemann(Ls, Rs, Bnf, gam, o);
+        orc_riemann_nl(Ls, Rs, Bnf, gam, c->riemann_iters, o);
         for (int v = 0; v < 8; v++) b->rs[v][p] = o[v];
         b->Bnf[p] = Bnf;
     }

@@ -43,9 +43,14 @@ MUTANTS = {
     "source_centre_field": ("double Bd0 = b->Bd[0][p], Bd1 = b->Bd[1][p], Bd2 = b->Bd[2][p];",
                             "double Bd0 = b->Bd[0][p], Bd1 = b->Bd[2][p], Bd2 = b->Bd[1][p];"),
     "inflow_field_sign": ("double Bp[3] = {c->inflow[4] - Bdg[0]", "double Bp[3] = {c->inflow[4] + Bdg[0]"),
+    "two_shock_constant": ("double a = (gamma + 1.0) / (2.0 * gamma);", "double a = (gamma - 1.0) / (2.0 * gamma);"),
+    "two_shock_slope": ("double ZL = 2.0 * WLk * WLk * WLk / (WLk * WLk + CL * CL);", "double ZL = WLk;"),
+    "two_shock_curve_sign": ("double uRk = R[1] + (Pc - PR) / WRk;", "double uRk = R[1] - (Pc - PR) / WRk;"),
+    "two_shock_final_speed": ("WR = CR * sqrt(1.0 + a * (Pc / PR - 1.0));\n    }", "WR = CR;\n    }"),
 }
 
-PINS = ["tests/test_oracle_ppm.py", "tests/test_oracle_riemann.py", "tests/test_oracle_sources.py",
+PINS = ["tests/test_oracle_ppm.py", "tests/test_oracle_riemann.py", "tests/test_oracle_riemann_nl.py",
+        "tests/test_oracle_sources.py",
         "tests/test_oracle_scheme.py", "tests/test_golden.py"]
 
 
