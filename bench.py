@@ -261,9 +261,10 @@ def run_ours(args, rank, world, dist):
     def max_ranks(x):
         return max_over_ranks(x, dist, "cuda")
 
-    def timed_run(precision, steps, warmup, with_clocks=False):
+    def timed_run(precision, steps, warmup, with_clocks=False, riemann_iters=0):
         ctx = ppmlr.Context.from_problem(prob, precision)
         ctx.set_state(U0)
+        ctx.set_riemann_solver(riemann_iters)
         if args.launch_config and precision == prec:
             for axis, (C, L, form) in enumerate(args.launch_config):
                 ctx.set_tiles(axis, C, L)
@@ -382,6 +383,17 @@ def run_ours(args, rank, world, dist):
                                "kernels_avg_ms": {k: v[0] / max(v[1], 1) for k, v in xkern.items()},
                                "note": "bit-identical to the CPU reference"}
         xctx.close()
+
+    # ---- the nonlinear (two-shock, fast-mode) Riemann solver variant: its cost
+    if not args.quick:
+        nl = {"iters": 4}
+        for key, p in (("fp64", ppmlr.PPMLR_FP64), ("mixed", ppmlr.PPMLR_MIXED)):
+            nsteps = max(3, args.steps // 4) if key == "fp64" else args.steps
+            nctx, nms, _, _, _ = timed_run(p, nsteps, args.warmup, riemann_iters=4)
+            nms = max_ranks(nms)
+            nl[key] = {"value": world * cells * nsteps / (nms * 1e-3), "ms_per_step": nms / nsteps}
+            nctx.close()
+        extra["riemann_two_shock"] = nl
 
     # ---- end to end through the C ABI with host buffers
     e2e = None

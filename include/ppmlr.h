@@ -192,6 +192,19 @@ ppmlr_status ppmlr_get_tiles(ppmlr_ctx *ctx, int *C, int *L);
  * PPMLR_E_INVALID (state unchanged) for shapes outside those bounds. */
 ppmlr_status ppmlr_set_tiles(ppmlr_ctx *ctx, int axis, int C, int L);
 
+/* Riemann solver of the sweeps.  iters = 0 (default): the linearised
+ * two-wave solver (total pressure, fast impedance rho c_f; Alfven subsystem
+ * with impedance sqrt(rho) |B_n|).  iters = 1..16: the nonlinear variant --
+ * the two-shock solver of Colella & Woodward (1984), which the paper cites
+ * for its scheme (Sec. II), on the fast mode: each side's wave is a shock
+ * with Lagrangian speed W(P) = rho c_f sqrt(1 + (gamma+1)/(2 gamma)
+ * (P/P_s - 1)) in the total pressure P; `iters` Newton steps from the
+ * two-wave P* (4 reach the exact two-shock solution to roundoff for strong
+ * shocks).  The Alfven subsystem stays linear.  Same arithmetic forms as the
+ * rest of the sweep (PPMLR_FP64_EXACT: the reference's expressions).
+ * PPMLR_E_INVALID outside [0, 16]. */
+ppmlr_status ppmlr_set_riemann_solver(ppmlr_ctx *ctx, int iters);
+
 /* Launch form of each sweep direction (3 entries): 0 = one block per tile
  * reading its input from global memory; 1 = persistent blocks whose input
  * boxes (8 arrays x positions x lanes) are staged into shared memory by the

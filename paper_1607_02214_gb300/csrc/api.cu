@@ -52,6 +52,7 @@ struct ppmlr_ctx {
     // simulated time: device accumulator (dt_dev[1], steps with a device dt)
     // plus the explicit dt of ppmlr_step, summed on the host
     double t_host;
+    int riemann_iters;              // 0: two-wave Riemann solver; k > 0: k two-shock Newton steps
     std::vector<double> edges[3];   // host copies of the grid edges (checkpoint validation)
     // graph replay of ppmlr_run: one executable graph per starting step
     // parity, input buffer, length and CFL number; dropped when the tiles or
@@ -313,6 +314,7 @@ ppmlr_status ppmlr_create(const ppmlr_grid *grid, double gamma, const ppmlr_bc *
     c->launches = 0;
     c->timing = false;
     c->t_host = 0.0;
+    c->riemann_iters = 0;
     c->cap = nullptr;
     for (int d = 0; d < 3; d++) c->edges[d].assign(grid->edges[d], grid->edges[d] + grid->n[d] + 1);
     if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return PPMLR_E_CUDA; }
@@ -469,6 +471,7 @@ static ppmlr_status launch_one_sweep(ppmlr_ctx *c, int d, double dt, const doubl
     a.gamma = c->gamma; a.p_min = c->bc.p_min; a.M = c->bc.dipole_moment; a.r_inner = c->bc.r_inner;
     a.powell = c->bc.powell ? 1 : 0;
     a.do_src = (a.M != 0.0 || a.powell) ? 1 : 0;
+    a.riemann_iters = c->riemann_iters;
     a.dt = dt; a.dt_dev = dt_dev;
     a.flags = c->flags; a.floors = c->floors;
     a.wf = c->wf[d];
@@ -703,6 +706,15 @@ ppmlr_status ppmlr_set_tiles(ppmlr_ctx *c, int axis, int C, int L)
     if ((long long)(C + 2 * GH) * L > maxt) return fail(c, PPMLR_E_INVALID, "set_tiles: (C + 14) * L exceeds the thread budget");
     c->tile[axis] = make_tile(axis, c->n, rs, C, L);
     c->mode[axis] = 0;
+    drop_graphs(c);
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_set_riemann_solver(ppmlr_ctx *c, int iters)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (iters < 0 || iters > 16) return fail(c, PPMLR_E_INVALID, "set_riemann_solver: iters must be in [0, 16]");
+    c->riemann_iters = iters;
     drop_graphs(c);
     return PPMLR_OK;
 }

@@ -39,6 +39,7 @@ struct SweepArgs {
     double gamma, p_min, M, r_inner;
     double inner[8];           // rho, vx, vy, vz, -, -, -, p
     int powell, do_src;
+    int riemann_iters;         // 0: two-wave Riemann solver; k > 0: k two-shock Newton steps
     double dt;                 // used when dt_dev == nullptr
     const double *dt_dev;
     int *flags;

@@ -35,10 +35,12 @@ template <typename R> struct K;
 template <> struct K<double> {
     static __device__ __forceinline__ double sq(double x) { return sqrt(x); }
     static __device__ __forceinline__ double ab(double x) { return fabs(x); }
+    static __device__ __forceinline__ double rs(double x) { return rsqrt(x); }
 };
 template <> struct K<float> {
     static __device__ __forceinline__ float sq(float x) { return sqrtf(x); }
     static __device__ __forceinline__ float ab(float x) { return fabsf(x); }
+    static __device__ __forceinline__ float rs(float x) { return rsqrtf(x); }
 };
 
 // Fast magnetosonic speed squared along the normal (mu0 = 1).  EX: the
@@ -64,6 +66,56 @@ __device__ __forceinline__ R fast2(R rho, R p, R Bn, R B1, R B2, R gam)
     R disc = s * s - R(4) * a2 * bn2;
     if (disc < R(0)) disc = R(0);
     return R(0.5) * (s + K<R>::sq(disc));
+}
+
+// Nonlinear (two-shock) normal subsystem of the Lagrangian Riemann problem:
+// each side's fast wave is a shock whose Lagrangian speed depends on the
+// middle total pressure, W(P) = C sqrt(1 + (gamma+1)/(2 gamma) (P/P_s - 1)),
+// C = rho c_f (Colella & Woodward 1984 two-shock solver, fast speed and total
+// pressure for the gas's).  Starting from the two-wave P*, `iters` Newton steps
+// on u*_R(P) - u*_L(P) = 0 (slope of each shock curve dP/du =
+// 2 W^3 / (W^2 + C^2)); on return WL, WR hold W at the final P (clipped at 0),
+// and the caller's two-wave formulas give u*, P*.  EX: the reference's
+// expression trees; otherwise one reciprocal square root per side and one
+// division per step (W = C / rsqrt(q), 1/Z = (1 + 1/q) / (2 W)).
+template <typename R, bool EX>
+__device__ __forceinline__ void two_shock(const int iters, const R uL, const R uR, const R PL, const R PR,
+                                          const R gam, R &WL, R &WR)
+{
+    const R CL = WL, CR = WR;
+    if constexpr (EX) {
+        const R a = (gam + R(1)) / (R(2) * gam);
+        R P = (WR * PL + WL * PR + WL * WR * (uL - uR)) / (WL + WR);
+        for (int k = 0; k < iters; k++) {
+            const R Pc = P > R(0) ? P : R(0);
+            const R WLk = CL * K<R>::sq(R(1) + a * (Pc / PL - R(1)));
+            const R WRk = CR * K<R>::sq(R(1) + a * (Pc / PR - R(1)));
+            const R uLk = uL - (Pc - PL) / WLk;
+            const R uRk = uR + (Pc - PR) / WRk;
+            const R ZL = R(2) * WLk * WLk * WLk / (WLk * WLk + CL * CL);
+            const R ZR = R(2) * WRk * WRk * WRk / (WRk * WRk + CR * CR);
+            P = Pc - ZL * ZR * (uRk - uLk) / (ZL + ZR);
+        }
+        const R Pc = P > R(0) ? P : R(0);
+        WL = CL * K<R>::sq(R(1) + a * (Pc / PL - R(1)));
+        WR = CR * K<R>::sq(R(1) + a * (Pc / PR - R(1)));
+    } else {
+        const R a = (gam + R(1)) / (R(2) * gam);
+        const R aL = a / PL, aR = a / PR, b = R(1) - a;       // q = 1 + a (P/P_s - 1) = b + (a/P_s) P
+        const R iCL = R(1) / CL, iCR = R(1) / CR;
+        R P = (WR * PL + WL * PR + WL * WR * (uL - uR)) / (WL + WR);
+        for (int k = 0; k < iters; k++) {
+            const R Pc = P > R(0) ? P : R(0);
+            const R rqL = K<R>::rs(b + aL * Pc), rqR = K<R>::rs(b + aR * Pc);
+            const R rWL = rqL * iCL, rWR = rqR * iCR;         // 1 / W
+            const R f = (uR - uL) + (Pc - PR) * rWR + (Pc - PL) * rWL;
+            const R izL = R(0.5) * (R(1) + rqL * rqL) * rWL, izR = R(0.5) * (R(1) + rqR * rqR) * rWR;   // 1 / Z
+            P = Pc - f / (izL + izR);
+        }
+        const R Pc = P > R(0) ? P : R(0);
+        WL = CL * K<R>::sq(b + aL * Pc);
+        WR = CR * K<R>::sq(b + aR * Pc);
+    }
 }
 
 // Earth dipole along -z: B_d = M [3 (m.r) r - m r^2] / r^5, m = -z.
@@ -614,6 +666,8 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         R PR = Rs[6] + R(0.5) * (Rs[4] * Rs[4] + Rs[5] * Rs[5]);
         R WL = sl[0] * K<R>::sq(fast2<R, EX>(sl[0], sl[6], Bnf, sl[4], sl[5], gam));
         R WR = Rs[0] * K<R>::sq(fast2<R, EX>(Rs[0], Rs[6], Bnf, Rs[4], Rs[5], gam));
+        if (a.riemann_iters > 0 && PL > R(0) && PR > R(0))
+            two_shock<R, EX>(a.riemann_iters, sl[1], Rs[1], PL, PR, gam, WL, WR);
         R us, Ps;
         if constexpr (EX) {
             us = (WL * sl[1] + WR * Rs[1] + PL - PR) / (WL + WR);

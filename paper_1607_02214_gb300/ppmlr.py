@@ -63,6 +63,7 @@ SIGNATURES = [
     ("ppmlr_set_sweep_form", c_int, [c_void_p, c_int, c_int]),
     ("ppmlr_set_tiles", c_int, [c_void_p, c_int, c_int, c_int]),
     ("ppmlr_run", c_int, [c_void_p, c_double, c_longlong, c_int]),
+    ("ppmlr_set_riemann_solver", c_int, [c_void_p, c_int]),
     ("ppmlr_get_time", c_int, [c_void_p, POINTER(c_double)]),
     ("ppmlr_set_time", c_int, [c_void_p, c_double]),
     ("ppmlr_checkpoint_save", c_int, [c_void_p, ctypes.c_char_p]),
@@ -265,6 +266,11 @@ class Context:
         dt = c_double()
         self._check(load().ppmlr_get_dt(self._h, ctypes.byref(dt)))
         return dt.value
+
+    def set_riemann_solver(self, iters):
+        """0: two-wave Riemann solver; k > 0: k two-shock Newton steps on the
+        fast mode (nonlinear variant)."""
+        return self._check(load().ppmlr_set_riemann_solver(self._h, int(iters)))
 
     def run(self, cfl, nsteps, graph_steps=16):
         """nsteps device-dt steps (as step_cfl), replayed from CUDA graphs of
