@@ -45,15 +45,14 @@ BYTES_PER_CELL_SWEEP = 128      # read 8 FP64 + write 8 FP64
 # DRAM bytes per cell of one launch measured by ncu for each kernel, with the
 # sha256 prefix of the kernel source they were taken on (null once it changes).
 NCU_TRAFFIC = {
-    "fp64:x": {"bytes_per_cell": 123.3, "src": "a43db4ae1c19108d"},
-    "fp64:y": {"bytes_per_cell": 123.8, "src": "a43db4ae1c19108d"},
-    "fp64:z": {"bytes_per_cell": 124.2, "src": "a43db4ae1c19108d"},
-    "fp64:cfl": {"bytes_per_cell": 64.5, "src": "a43db4ae1c19108d"},
-    "mixed:x": {"bytes_per_cell": 123.0, "src": "a43db4ae1c19108d"},
-    "mixed:y": {"bytes_per_cell": 123.7, "src": "a43db4ae1c19108d"},
-    "mixed:z": {"bytes_per_cell": 124.1, "src": "a43db4ae1c19108d"},
-    "mixed:cfl": {"bytes_per_cell": 64.3, "src": "a43db4ae1c19108d"},
-    "ensemble:x": {"bytes_per_cell": 127.4, "src": "a43db4ae1c19108d"},
+    "fp64:x": {"bytes_per_cell": 123.3, "src": "6ba194d5459153d0"},
+    "fp64:y": {"bytes_per_cell": 123.8, "src": "6ba194d5459153d0"},
+    "fp64:z": {"bytes_per_cell": 124.2, "src": "6ba194d5459153d0"},
+    "fp64:cfl": {"bytes_per_cell": 64.6, "src": "6ba194d5459153d0"},
+    "mixed:x": {"bytes_per_cell": 123.0, "src": "6ba194d5459153d0"},
+    "mixed:y": {"bytes_per_cell": 123.8, "src": "6ba194d5459153d0"},
+    "mixed:z": {"bytes_per_cell": 124.2, "src": "6ba194d5459153d0"},
+    "mixed:cfl": {"bytes_per_cell": 64.3, "src": "6ba194d5459153d0"},
 }
 
 

@@ -24,43 +24,62 @@ __device__ __forceinline__ float block_min_f(float v)
     return v;
 }
 
+// Bound dx_d / (|v_d| + c_f,d) of one cell (INFINITY inside the inner sphere)
+// from its 8 conserved values.
+__device__ __forceinline__ float cell_bound(const CflArgs &a, const long long i, const double *u)
+{
+    const long long nx = a.n[0], ny = a.n[1];
+    const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / (nx * ny));
+    const float x = a.cf[0][ix + GH], y = a.cf[1][iy + GH], z = a.cf[2][iz + GH];
+    if (a.r_innerf > 0.0f) {
+        const float r2 = x * x + y * y + z * z, ri2 = a.r_innerf * a.r_innerf;
+        if (r2 < ri2 * (1.0f - 1e-5f)) return INFINITY;
+        if (r2 < ri2 * (1.0f + 1e-5f)) {
+            const double xd = a.c[0][ix + GH], yd = a.c[1][iy + GH], zd = a.c[2][iz + GH];
+            if (xd * xd + yd * yd + zd * zd < a.r_inner * a.r_inner) return INFINITY;
+        }
+    }
+    const float gm1 = a.gammaf - 1.0f;
+    df q[8];
+#pragma unroll
+    for (int v = 0; v < 8; v++) q[v] = split_double(u[v]);
+    float pr = pressure_df(q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], gm1);
+    if (pr < a.p_minf) pr = a.p_minf;
+    float Bd[3];
+    dipole_f(a.Mf, x, y, z, Bd);
+    const float rho = q[0].h, ir = 1.0f / rho;
+    const int idx[3] = {ix, iy, iz};
+    float best = INFINITY;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+        const float Bn = q[4 + d].h, B1 = q[4 + t1].h, B2 = q[4 + t2].h;
+        const float c1 = fast2<float>(rho, pr, Bn, B1, B2, a.gammaf);
+        const float c2 = fast2<float>(rho, pr, Bn + Bd[d], B1 + Bd[t1], B2 + Bd[t2], a.gammaf);
+        const float cf = sqrtf(fmaxf(c1, c2));
+        const float sv = a.wf[d][idx[d] + GH] / (fabsf(q[1 + d].h * ir) + cf);
+        best = fminf(best, sv);
+    }
+    return best;
+}
+
+// Grid-stride pass over the cells, two cells per iteration: both cells' 16
+// loads are issued before either is used, doubling the loads in flight.
 __device__ __forceinline__ void cfl_mixed_body(const CflArgs &a, const int bid, const int nb)
 {
-    const long long nx = a.n[0], ny = a.n[1], nz = a.n[2];
-    const long long ncell = nx * ny * nz;
-    const float gm1 = a.gammaf - 1.0f;
+    const long long ncell = (long long)a.n[0] * a.n[1] * a.n[2];
+    const long long step = (long long)nb * blockDim.x;
     float best = INFINITY;
-    for (long long i = (long long)bid * blockDim.x + threadIdx.x; i < ncell;
-         i += (long long)nb * blockDim.x) {
-        const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / (nx * ny));
-        const float x = a.cf[0][ix + GH], y = a.cf[1][iy + GH], z = a.cf[2][iz + GH];
-        if (a.r_innerf > 0.0f) {
-            const float r2 = x * x + y * y + z * z, ri2 = a.r_innerf * a.r_innerf;
-            if (r2 < ri2 * (1.0f - 1e-5f)) continue;
-            if (r2 < ri2 * (1.0f + 1e-5f)) {
-                const double xd = a.c[0][ix + GH], yd = a.c[1][iy + GH], zd = a.c[2][iz + GH];
-                if (xd * xd + yd * yd + zd * zd < a.r_inner * a.r_inner) continue;
-            }
-        }
-        df q[8];
+    for (long long i0 = (long long)bid * blockDim.x + threadIdx.x; i0 < ncell; i0 += 2 * step) {
+        const long long i1 = i0 + step;
+        const bool two = i1 < ncell;
+        double u0[8], u1[8];
 #pragma unroll
-        for (int v = 0; v < 8; v++) q[v] = split_double(__ldg(a.U[v] + i));
-        float pr = pressure_df(q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], gm1);
-        if (pr < a.p_minf) pr = a.p_minf;
-        float Bd[3];
-        dipole_f(a.Mf, x, y, z, Bd);
-        const float rho = q[0].h, ir = 1.0f / rho;
-        const int idx[3] = {ix, iy, iz};
+        for (int v = 0; v < 8; v++) u0[v] = __ldg(a.U[v] + i0);
 #pragma unroll
-        for (int d = 0; d < 3; d++) {
-            const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-            const float Bn = q[4 + d].h, B1 = q[4 + t1].h, B2 = q[4 + t2].h;
-            const float c1 = fast2<float>(rho, pr, Bn, B1, B2, a.gammaf);
-            const float c2 = fast2<float>(rho, pr, Bn + Bd[d], B1 + Bd[t1], B2 + Bd[t2], a.gammaf);
-            const float cf = sqrtf(fmaxf(c1, c2));
-            const float sv = a.wf[d][idx[d] + GH] / (fabsf(q[1 + d].h * ir) + cf);
-            best = fminf(best, sv);
-        }
+        for (int v = 0; v < 8; v++) u1[v] = two ? __ldg(a.U[v] + i1) : u0[v];
+        best = fminf(best, cell_bound(a, i0, u0));
+        if (two) best = fminf(best, cell_bound(a, i1, u1));
     }
     best = block_min_f(best);
     __shared__ bool last;
@@ -88,7 +107,7 @@ __device__ __forceinline__ void cfl_mixed_body(const CflArgs &a, const int bid, 
     }
 }
 
-__global__ void __launch_bounds__(CFLM_THREADS) cfl_mixed_kernel(CflArgs a) { cfl_mixed_body(a, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(CFLM_THREADS, 4) cfl_mixed_kernel(CflArgs a) { cfl_mixed_body(a, blockIdx.x, gridDim.x); }
 
 __global__ void __launch_bounds__(CFLM_THREADS) cfl_mixed_ensemble_kernel(EnsCflArgs e)
 {
