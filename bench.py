@@ -45,27 +45,51 @@ BYTES_PER_CELL_SWEEP = 128      # read 8 FP64 + write 8 FP64
 # DRAM bytes per cell of one launch measured by ncu for each kernel, with the
 # sha256 prefix of the kernel source they were taken on (null once it changes).
 NCU_TRAFFIC = {
-    "fp64:x": {"bytes_per_cell": 123.3, "src": "6ba194d5459153d0"},
-    "fp64:y": {"bytes_per_cell": 123.8, "src": "6ba194d5459153d0"},
-    "fp64:z": {"bytes_per_cell": 124.2, "src": "6ba194d5459153d0"},
-    "fp64:cfl": {"bytes_per_cell": 64.6, "src": "6ba194d5459153d0"},
-    "mixed:x": {"bytes_per_cell": 123.0, "src": "6ba194d5459153d0"},
-    "mixed:y": {"bytes_per_cell": 123.8, "src": "6ba194d5459153d0"},
-    "mixed:z": {"bytes_per_cell": 124.2, "src": "6ba194d5459153d0"},
-    "mixed:cfl": {"bytes_per_cell": 64.3, "src": "6ba194d5459153d0"},
+    "fp64:x": {"bytes_per_cell": 123.3, "src": "1edff4ad4285916d"},
+    "fp64:y": {"bytes_per_cell": 123.8, "src": "1edff4ad4285916d"},
+    "fp64:z": {"bytes_per_cell": 124.2, "src": "1edff4ad4285916d"},
+    "fp64:cfl": {"bytes_per_cell": 64.6, "src": "20d17fefda611b6f"},
+    "mixed:x": {"bytes_per_cell": 123.0, "src": "5bc57b712850d0dc"},
+    "mixed:y": {"bytes_per_cell": 123.8, "src": "5bc57b712850d0dc"},
+    "mixed:z": {"bytes_per_cell": 124.2, "src": "5bc57b712850d0dc"},
+    "mixed:cfl": {"bytes_per_cell": 64.3, "src": "8025c11eef4f426b"},
 }
 
 
-KERNEL_SOURCES = ("sweep.cuh", "launch.cuh", "mixed_util.cuh", "cfl.cuh", "sweep_fp64.cu", "sweep_fp64_exact.cu",
-                  "sweep_mixed.cu", "cfl.cu", "cfl_fp64.cu", "cfl_mixed.cu")
+# Sources of each (precision, kernel) entry of NCU_TRAFFIC; the hash of the
+# files at capture time is stored with the entry.
+_SWEEP = ("sweep.cuh", "launch.cuh", "mixed_util.cuh", "ppmlr_internal.h")
+KERNEL_SOURCES = {
+    "fp64:sweep": _SWEEP + ("sweep_fp64.cu",),
+    "mixed:sweep": _SWEEP + ("sweep_mixed.cu",),
+    "ensemble:sweep": _SWEEP + ("sweep_mixed.cu", "ensemble.cu"),
+    "fp64:cfl": ("cfl.cuh", "cfl_fp64.cu", "ppmlr_internal.h"),
+    "mixed:cfl": ("cfl_mixed.cu", "sweep.cuh", "mixed_util.cuh", "ppmlr_internal.h"),
+}
 
 
-def kernel_source_hash():
+def kernel_source_hash(key=None):
+    """sha256 prefix of the sources behind one NCU_TRAFFIC key ("fp64:x",
+    "mixed:cfl", ...), or of all kernel sources when key is None."""
+    if key is None:
+        files = sorted({f for v in KERNEL_SOURCES.values() for f in v})
+    else:
+        prec, kern = key.split(":")
+        files = KERNEL_SOURCES[f"{prec}:{'cfl' if kern == 'cfl' else 'sweep'}"]
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in files:
         with open(os.path.join(ROOT, "paper_1607_02214_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def ncu_traffic(key, cells):
+    """DRAM bytes of one launch from the ncu table, or None if the kernel's
+    sources changed since the capture."""
+    tr = NCU_TRAFFIC.get(key)
+    if tr and tr["src"] == kernel_source_hash(key):
+        return tr["bytes_per_cell"] * cells
+    return None
 
 
 def log(*a):
@@ -305,11 +329,8 @@ def run_ours(args, rank, world, dist):
     # ---- roofline of the dominant kernel (largest total time)
     dom = max(kern, key=lambda k: kern[k][0])
     avg_ms = kern[dom][0] / max(kern[dom][1], 1)
-    traffic = None
     src_hash = kernel_source_hash()
-    tr = NCU_TRAFFIC.get(f"{args.precision}:{dom}")
-    if tr and tr["src"] == src_hash:
-        traffic = tr["bytes_per_cell"] * cells
+    traffic = ncu_traffic(f"{args.precision}:{dom}", cells)
     if args.precision == "fp64":
         ach = FLOPS_PER_CELL[dom] * cells / (avg_ms * 1e-3) / 1e9
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PIPE_GOPS, "unit": "GFLOP/s",
@@ -358,11 +379,10 @@ def run_ours(args, rank, world, dist):
         key = "mixed" if other == ppmlr.PPMLR_MIXED else "fp64"
         odom = max(okern, key=lambda k: okern[k][0])
         oavg = okern[odom][0] / max(okern[odom][1], 1)
-        otr = NCU_TRAFFIC.get(f"{key}:{odom}")
         obytes = (128 if odom != "cfl" else 64) * cells
         oach = obytes / (oavg * 1e-3) / 1e9
         oroof = {"bound": "hbm", "achieved": oach, "peak": 6787.2, "unit": "GB/s", "frac": oach / 6787.2,
-                 "traffic": otr["bytes_per_cell"] * cells if otr and otr["src"] == src_hash else None,
+                 "traffic": ncu_traffic(f"{key}:{odom}", cells),
                  "kernel": f"sweep_{odom}" if odom != "cfl" else "cfl", "avg_launch_ms": oavg,
                  "peak_source": "measured"}
         extra[key] = {"value": ovalue, "ms_per_step": oms / args.steps, "roofline": oroof,
@@ -542,9 +562,8 @@ def run_ensemble(args, fp64_value, barrier, rank=0, world=1, dist=None):
     out["kernels_avg_ms"] = kern
     dom = max(("x", "y", "z"), key=lambda k: kern[k])
     ach = BYTES_PER_CELL_SWEEP * cells / (kern[dom] * 1e-3) / 1e9
-    etr = NCU_TRAFFIC.get(f"ensemble:{dom}")
     out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": 6787.2, "unit": "GB/s", "frac": ach / 6787.2,
-                       "traffic": etr["bytes_per_cell"] * cells if etr and etr["src"] == kernel_source_hash() else None,
+                       "traffic": ncu_traffic(f"ensemble:{dom}", cells),
                        "kernel": f"sweep_ensemble_{dom}", "avg_launch_ms": kern[dom], "peak_source": "measured"}
     # the same instances advanced one context at a time (no batching)
     ctxs = [ppmlr.Context.from_problem(p, ppmlr.PPMLR_MIXED) for p in probs]

@@ -294,6 +294,10 @@ ppmlr_status ppmlr_ensemble_time_kernels(ppmlr_ens *ens, double cfl, int nsteps,
  * parameter, up to 64 instances), timed out of place; best_ms: 3 entries or
  * NULL. */
 ppmlr_status ppmlr_ensemble_autotune(ppmlr_ens *ens, double *best_ms);
+/* Riemann solver of every instance's sweeps, as ppmlr_set_riemann_solver
+ * (0: two-wave; 1..16: two-shock Newton steps on the fast mode).  Drops the
+ * captured step graphs.  PPMLR_E_INVALID outside [0, 16]. */
+ppmlr_status ppmlr_ensemble_set_riemann_solver(ppmlr_ens *ens, int iters);
 /* Launch form and thread budget per direction in use: 1000 * form + budget
  * (3 entries). */
 ppmlr_status ppmlr_ensemble_get_tiles(ppmlr_ens *ens, int *maxt);

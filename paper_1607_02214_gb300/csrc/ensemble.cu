@@ -29,6 +29,7 @@ struct ppmlr_ens {
     std::vector<int> n;          // 3 per instance
     std::vector<long long> ncell;
     std::vector<ppmlr_bc> bc;
+    int riemann_iters;           // 0: two-wave Riemann solver; k > 0: k two-shock Newton steps
     double *state;               // all instances, A and B sets
     std::vector<double *> A, B;  // 8 per instance
     double *geo;                 // per instance: w[3], c[3] (double)
@@ -148,6 +149,7 @@ static ppmlr_status upload_direction(ppmlr_ens *e, int d)
         a.gamma = e->gamma; a.p_min = b.p_min; a.M = b.dipole_moment; a.r_inner = b.r_inner;
         a.powell = b.powell ? 1 : 0;
         a.do_src = (a.M != 0.0 || a.powell) ? 1 : 0;
+        a.riemann_iters = e->riemann_iters;
         a.dt = 0.0; a.dt_dev = e->dt + i;
         a.flags = e->flags; a.floors = e->floors;
         a.gammaf = (float)a.gamma; a.p_minf = (float)a.p_min; a.Mf = (float)a.M; a.r_innerf = (float)a.r_inner;
@@ -593,6 +595,20 @@ ppmlr_status ppmlr_ensemble_time_kernels(ppmlr_ens *e, double cfl, int nsteps, d
         }
     for (auto &x : ev) cudaEventDestroy(x);
     for (int j = 0; j < 4; j++) avg_ms[j] = cnt[j] ? tot[j] / cnt[j] : 0.0;
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_ensemble_set_riemann_solver(ppmlr_ens *e, int iters)
+{
+    if (!e) return PPMLR_E_INVALID;
+    if (iters < 0 || iters > 16) return efail(e, PPMLR_E_INVALID, "set_riemann_solver: iters must be in [0, 16]");
+    e->riemann_iters = iters;
+    for (int d = 0; d < 3; d++) {
+        ppmlr_status st = upload_direction(e, d);
+        if (st != PPMLR_OK) return st;
+    }
+    ECK(e, cudaStreamSynchronize(e->stream), "sync");
+    drop_graphs(e);
     return PPMLR_OK;
 }
 

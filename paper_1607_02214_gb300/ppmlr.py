@@ -79,6 +79,7 @@ SIGNATURES = [
     ("ppmlr_ensemble_time_kernels", c_int, [c_void_p, c_double, c_int, POINTER(c_double)]),
     ("ppmlr_ensemble_autotune", c_int, [c_void_p, POINTER(c_double)]),
     ("ppmlr_ensemble_get_tiles", c_int, [c_void_p, POINTER(c_int)]),
+    ("ppmlr_ensemble_set_riemann_solver", c_int, [c_void_p, c_int]),
     ("ppmlr_ensemble_get_dt", c_int, [c_void_p, POINTER(c_double)]),
     ("ppmlr_ensemble_check", c_int, [c_void_p]),
     ("ppmlr_ensemble_get_diagnostics", c_int, [c_void_p, POINTER(c_longlong), POINTER(c_longlong)]),
@@ -425,6 +426,10 @@ class Ensemble:
         t = (c_int * 3)()
         self._check(load().ppmlr_ensemble_get_tiles(self._h, t))
         return list(t)
+
+    def set_riemann_solver(self, iters):
+        """0: two-wave Riemann solver; k > 0: k two-shock Newton steps."""
+        return self._check(load().ppmlr_ensemble_set_riemann_solver(self._h, int(iters)))
 
     def dt(self):
         out = (c_double * self.count)()

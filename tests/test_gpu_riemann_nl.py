@@ -90,3 +90,21 @@ def test_graph_run_uses_the_nonlinear_solver():
     a.run(pr.cfl, 4, graph_steps=2)
     b.step_cfl(pr.cfl, 4)
     assert np.array_equal(a.get_state(), b.get_state())
+
+
+def test_ensemble_instances_use_the_nonlinear_solver():
+    from test_gpu_ensemble import small_ensemble
+    probs = small_ensemble(3)[:3]
+    ens = ppmlr.Ensemble(probs, precision=ppmlr.PPMLR_FP64_EXACT)
+    ens.set_riemann_solver(ITERS)
+    for i, p in enumerate(probs):
+        ens.set_state(i, p.U0)
+    ens.step(0.4, 3)                                 # graph replay, per-instance device dt
+    for i, p in enumerate(probs):
+        o = make_oracle(p)
+        o.set_riemann(ITERS)
+        for _ in range(3):
+            assert o.step(o.cfl_dt(0.4)) == 0
+        assert np.array_equal(ens.get_state(i), o.get_state()), i
+    with pytest.raises(ppmlr.PPMLRError):
+        ens.set_riemann_solver(17)
