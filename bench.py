@@ -32,11 +32,13 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s per full xyz step"
 UNIT = "cell-updates/s"
 HBM_FALLBACK_GBS = 6800.0
-# FP64 pipe throughput of a GB300 measured with a dependent-free DFMA/DADD/DMUL
-# loop over all 152 SMs: 502 G instructions/s (each a +, -, x or FMA).  The FP64
-# sweeps compile without contraction, so one algorithmic flop is one pipe op;
-# a division or square root occupies the pipe for ~6 and ~9 ops.
-FP64_PIPE_GOPS = 502.4
+# FP64 peak of a GB300 in flop/s: bench_fp64_rate.cu measures 503 G FP64
+# fused multiply-adds per second over all 152 SMs (1.60 per SM per clock at
+# 2070 MHz; DADD and DMUL run at the same instruction rate, DDIV at 88.6 G/s,
+# DSQRT at 58.4 G/s), i.e. 1006 GFLOP/s with an FMA counted as two flops.
+# The nominal dense FP64 rate of the part is 1.25 TFLOP/s.
+FP64_PEAK_GFLOPS = 1006.0
+FP64_NOMINAL_GFLOPS = 1250.0
 # Algorithmic FP64 flops (+, -, x, /, sqrt) per interior cell of one sweep on
 # the magnetosphere workload (PPM coefficients counted once per zone), counted
 # by an instrumented build of the reference; and per cell of the CFL pass.
@@ -333,10 +335,11 @@ def run_ours(args, rank, world, dist):
     traffic = ncu_traffic(f"{args.precision}:{dom}", cells)
     if args.precision == "fp64":
         ach = FLOPS_PER_CELL[dom] * cells / (avg_ms * 1e-3) / 1e9
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PIPE_GOPS, "unit": "GFLOP/s",
-                "frac": ach / FP64_PIPE_GOPS, "traffic": traffic, "kernel": f"sweep_{dom}" if dom != "cfl" else "cfl",
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": ach / FP64_PEAK_GFLOPS, "traffic": traffic, "kernel": f"sweep_{dom}" if dom != "cfl" else "cfl",
                 "avg_launch_ms": avg_ms,
-                "peak_source": "measured FP64 pipe rate (DFMA/DADD/DMUL loop, 152 SMs)"}
+                "peak_source": "measured FP64 FMA rate x 2 flops (bench_fp64_rate.cu, 152 SMs)",
+                "peak_nominal": FP64_NOMINAL_GFLOPS, "frac_of_nominal": ach / FP64_NOMINAL_GFLOPS}
     else:
         try:
             with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -637,6 +640,7 @@ def run_large(args, barrier):
             per[k] = {"avg_ms": avg, "hbm_frac_of_measured": byts / (avg * 1e-3) / 1e9 / 6787.2}
             if name == "fp64":
                 per[k]["fp64_gflops"] = FLOPS_PER_CELL[k] * cells / (avg * 1e-3) / 1e9
+                per[k]["fp64_frac_of_measured"] = per[k]["fp64_gflops"] / FP64_PEAK_GFLOPS
         out[name] = {"value": cells * steps / (ms * 1e-3), "ms_per_step": ms / steps, "steps": steps,
                      "kernels": per, "tiles": ctx.tiles(), "forms": ctx.sweep_forms()}
         ctx.close()
