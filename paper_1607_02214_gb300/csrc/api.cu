@@ -36,6 +36,7 @@ struct ppmlr_ctx {
     int *flags;
     unsigned long long *floors;
     double *dt_dev;
+    double *bd;                  // FP64 forms with a dipole: B_d at every cell (3 arrays, stride `stride`)
     double *partial;
     unsigned int *counter;
     int cfl_blocks;
@@ -367,6 +368,19 @@ ppmlr_status ppmlr_create(const ppmlr_grid *grid, double gamma, const ppmlr_bc *
     size_t rs = prec == PPMLR_MIXED ? sizeof(float) : sizeof(double);
     for (int d = 0; d < 3; d++) { c->tile[d] = choose_tile(d, c->n, rs); c->mode[d] = 0; }
     c->sms = dev_sms;
+    c->bd = nullptr;
+    if (prec != PPMLR_MIXED && bc->dipole_moment != 0.0) {
+        // the dipole at every cell centre, evaluated once by the sweeps' own formula
+        e = cudaMalloc(&c->bd, sizeof(double) * c->stride * 3);
+        if (e == cudaSuccess)
+            e = sweep_launchers(prec).dipole_table(bc->dipole_moment, c->n, c->c[0], c->c[1], c->c[2], c->bd,
+                                                   (long long)c->stride, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            cudaFree(c->bd); cudaFree(c->geof); cudaFree(c->geo); cudaFree(c->state); delete c;
+            return e == cudaErrorMemoryAllocation ? PPMLR_E_OOM : PPMLR_E_CUDA;
+        }
+    }
     *out = c;
     return PPMLR_OK;
 }
@@ -385,6 +399,7 @@ void ppmlr_destroy(ppmlr_ctx *c)
     if (c->cap) cudaStreamDestroy(c->cap);
     for (auto &r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->pool) cudaEventDestroy(e);
+    cudaFree(c->bd);
     cudaFree(c->geof);
     cudaFree(c->geo);
     cudaFree(c->state);
@@ -473,6 +488,7 @@ static ppmlr_status launch_one_sweep(ppmlr_ctx *c, int d, double dt, const doubl
     a.do_src = (a.M != 0.0 || a.powell) ? 1 : 0;
     a.riemann_iters = c->riemann_iters;
     a.dt = dt; a.dt_dev = dt_dev;
+    a.bd = c->bd;
     a.flags = c->flags; a.floors = c->floors;
     a.wf = c->wf[d];
     a.cxf = c->cf[0]; a.cyf = c->cf[1]; a.czf = c->cf[2];
@@ -534,6 +550,8 @@ static ppmlr_status launch_cfl_kernel(ppmlr_ctx *c, double cfl, bool advance_tim
     a.cfl = cfl;
     a.partial = c->partial; a.counter = c->counter; a.dt_out = c->dt_dev;
     a.t_acc = advance_time ? c->dt_dev + 1 : nullptr;
+    a.bd = c->bd;
+    a.bd_vs = (long long)c->stride;
     for (int d = 0; d < 3; d++) { a.wf[d] = c->wf[d]; a.cf[d] = c->cf[d]; }
     a.gammaf = (float)a.gamma; a.p_minf = (float)a.p_min; a.Mf = (float)a.M; a.r_innerf = (float)a.r_inner;
     int rec = timing_begin(c, 3);

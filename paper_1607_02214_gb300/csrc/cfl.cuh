@@ -64,7 +64,11 @@ __device__ __forceinline__ void cfl_body(const CflArgs &a, const int bid, const 
 #pragma unroll
         for (int v = 0; v < 8; v++) U[v] = __ldg(a.U[v] + i);
         double Bd[3] = {0.0, 0.0, 0.0};
-        {
+        if (a.bd) {            // the sweeps' dipole table (same formula as below in the exact form)
+            Bd[0] = __ldg(a.bd + i);
+            Bd[1] = __ldg(a.bd + a.bd_vs + i);
+            Bd[2] = __ldg(a.bd + 2 * a.bd_vs + i);
+        } else {
             double r2 = x * x + y * y + z * z;
             if (a.M != 0.0 && r2 != 0.0) {
                 double r = sqrt(r2);

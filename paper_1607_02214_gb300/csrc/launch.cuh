@@ -102,6 +102,19 @@ struct SweepVariant {
         return dir == 1 ? tma_dir<1, false>(a, map, blocks, threads, smem, s)
                         : tma_dir<2, false>(a, map, blocks, threads, smem, s);
     }
+    static cudaError_t dipole_table(double M, const int n[3], const double *cx, const double *cy, const double *cz,
+                                    double *bd, long long vs, cudaStream_t s)
+    {
+        if constexpr (std::is_same<R, double>::value) {
+            const long long ncell = (long long)n[0] * n[1] * n[2];
+            long long blocks = (ncell + 255) / 256;
+            if (blocks > 152 * 16) blocks = 152 * 16;
+            dipole_table_kernel<EX><<<(int)blocks, 256, 0, s>>>(M, n[0], n[1], n[2], cx, cy, cz, bd, vs);
+            return cudaGetLastError();
+        } else {
+            return cudaErrorNotSupported;
+        }
+    }
     static int tma_per_sm(int dir, int persist, int threads, size_t smem)
     {
         if (persist)
@@ -128,7 +141,11 @@ struct SweepVariant {
         return dir == 0 ? per_sm_dir<0>(threads, smem)
                         : dir == 1 ? per_sm_dir<1>(threads, smem) : per_sm_dir<2>(threads, smem);
     }
-    static constexpr SweepLaunchers table() { return {single, ens, param, per_sm, tma, tma_per_sm}; }
+    static constexpr SweepLaunchers table()
+    {
+        return {single, ens, param, per_sm, tma, tma_per_sm,
+                std::is_same<R, double>::value ? &dipole_table : nullptr};
+    }
 };
 
 }  // namespace ppmlr

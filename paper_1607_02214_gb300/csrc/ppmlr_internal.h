@@ -42,6 +42,7 @@ struct SweepArgs {
     int riemann_iters;         // 0: two-wave Riemann solver; k > 0: k two-shock Newton steps
     double dt;                 // used when dt_dev == nullptr
     const double *dt_dev;
+    const double *bd;          // FP64 forms: dipole table (component k at bd + k * vs + cell) or null
     int *flags;
     unsigned long long *floors;
     // float copies for the mixed path (geometry and parameters)
@@ -87,6 +88,8 @@ struct CflArgs {
     unsigned int *counter;     // zero between launches; the last block resets it
     double *dt_out;            // device scalar
     double *t_acc;             // device scalar or null: the last block adds dt (simulated time)
+    const double *bd;          // FP64 forms: dipole table of the domain (component k at bd + k * bd_vs) or null
+    long long bd_vs;
 };
 
 // Tile shape of one sweep direction.
@@ -112,6 +115,9 @@ struct SweepLaunchers {
     cudaError_t (*tma)(int dir, int persist, const SweepArgs &a, const CUtensorMap &map, int blocks, int threads,
                        size_t smem, cudaStream_t s);
     int (*tma_per_sm)(int dir, int persist, int threads, size_t smem);
+    // dipole table of a single domain (null for the mixed path, which evaluates it in float)
+    cudaError_t (*dipole_table)(double M, const int n[3], const double *cx, const double *cy, const double *cz,
+                                double *bd, long long vs, cudaStream_t s);
 };
 extern const SweepLaunchers k_sweep_fp64, k_sweep_fp64_exact, k_sweep_mixed;
 inline const SweepLaunchers &sweep_launchers(ppmlr_precision p)

@@ -422,7 +422,14 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         pos[0] = a.cx[(DIR == 0 ? g : ix) + GH];
         pos[1] = a.cy[(DIR == 1 ? g : iy) + GH];
         pos[2] = a.cz[(DIR == 2 ? g : iz) + GH];
-        dipole<EX>(a.M, pos[0], pos[1], pos[2], Bdg);
+        if (a.bd && g >= 0 && g < a.N) {      // interior cell: the dipole table
+            const long long gi = base + (long long)g * stride;
+            Bdg[0] = __ldg(a.bd + gi);
+            Bdg[1] = __ldg(a.bd + a.vs + gi);
+            Bdg[2] = __ldg(a.bd + 2 * a.vs + gi);
+        } else {
+            dipole<EX>(a.M, pos[0], pos[1], pos[2], Bdg);
+        }
         double Uc[8];
         int src = g;
         bool fixed = false;
@@ -621,6 +628,10 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     }
     __syncthreads();
 
+    // reciprocals kept from one phase to a later one (contracted forms only):
+    // dt / dm (P4 -> P6) and 1 / dxL (P6 -> P9)
+    R dtm_k = 0, idxL_k = 0;
+
     // ---------------- P4: parabolas and characteristic tracing ----------------
     // left state of interface p+1/2 (this zone, right end): kept in registers;
     // right state of interface p-1/2 (this zone, left end): to A[0..8] for p-1.
@@ -632,6 +643,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             ya = K<R>::sq(rho) * K<R>::ab(Bn) * dtr / dm;
         } else {
             const R dtm = dtr / dm;
+            dtm_k = dtm;
             yf = W * dtm;
             ya = K<R>::sq(rho) * K<R>::ab(Bn) * dtm;
         }
@@ -728,7 +740,8 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             qL[0] = rhoL; qL[1] = rhoL * uL; qL[2] = rhoL * v1L; qL[3] = rhoL * v2L;
             qL[4] = B1dx / dxL; qL[5] = B2dx / dxL; qL[6] = rhoL * eL;
         } else {
-            const R dtm = dtr / dm, idxL = R(1) / dxL;
+            const R dtm = dtm_k, idxL = R(1) / dxL;     // dt / dm from P4 (same cells and value)
+            idxL_k = idxL;
             R uL = u - (rs_S - lS) * dtm;
             R v1L = v1 + (rs_s1 - ls1) * dtm;
             R v2L = v2 + (rs_s2 - ls2) * dtm;
@@ -786,7 +799,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         }
         if (p <= NPe - 8) {                       // edge p+1/2: donor is this zone when del >= 0
             if (gt0<R, EX>(del_p)) {
-                R y = del_p / dxL;
+                R y = EX ? del_p / dxL : del_p * idxL_k;
                 if (!gt0<R, EX>(R(1) - y)) atomicOr(a.flags, FLAG_CFL);
 #pragma unroll
                 for (int v = 0; v < 7; v++) SM(SB0 + v, s) = del_p * avg_right<R>(pl[v], pr_[v], p6[v], y);
@@ -796,7 +809,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             }
         }
         if (p >= 7 && lt0<R, EX>(del_m)) {       // edge p-1/2: donor is this zone when del < 0
-            R y = -del_m / dxL;
+            R y = EX ? -del_m / dxL : -del_m * idxL_k;
             if (!gt0<R, EX>(R(1) - y)) atomicOr(a.flags, FLAG_CFL);
 #pragma unroll
             for (int v = 0; v < 7; v++) SM(SB0 + v, s - PS) = del_m * avg_left<R>(pl[v], pr_[v], p6[v], y);
@@ -1095,6 +1108,25 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_param_ker
         if (p.first_tile[mid] <= t) lo = mid; else hi = mid - 1;
     }
     sweep_tile<DIR, R, EX, const SweepArgs>(p.args[lo], t - p.first_tile[lo], smem_raw, p.flip);
+}
+
+// Dipole table of a single domain (FP64 forms): B_d at every cell centre,
+// component k at bd + k * vs + cell, evaluated by the same dipole<EX> as the
+// sweeps evaluate on the fly (ghost cells still do).
+template <bool EX>
+__global__ void dipole_table_kernel(double M, int nx, int ny, int nz, const double *cx, const double *cy,
+                                    const double *cz, double *bd, long long vs)
+{
+    const long long ncell = (long long)nx * ny * nz;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ncell;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / ((long long)nx * ny));
+        double B[3];
+        dipole<EX>(M, cx[ix + GH], cy[iy + GH], cz[iz + GH], B);
+        bd[i] = B[0];
+        bd[vs + i] = B[1];
+        bd[2 * vs + i] = B[2];
+    }
 }
 
 }  // namespace ppmlr
