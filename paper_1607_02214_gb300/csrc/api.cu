@@ -29,8 +29,9 @@ struct ppmlr_ctx {
     double *state;               // 16 arrays: U (8) then Unew (8), each padded
     size_t stride;               // elements between arrays
     double *U[8], *Un[8];
-    double *geo;                 // w[3], c[3]
-    double *w[3], *c[3];
+    double *geo;                 // w[3], c[3], 1/w[3], 1/h[3]
+    double *w[3], *c[3], *iw[3], *ih[3];
+    unsigned char *inner_mask;   // per cell: centre inside the inner sphere (r_inner > 0), else null
     float *geof;                 // float copies of w[3], c[3] (mixed path)
     float *wf[3], *cf[3];
     int *flags;
@@ -328,12 +329,23 @@ ppmlr_status ppmlr_create(const ppmlr_grid *grid, double gamma, const ppmlr_bc *
 
     // geometry
     std::vector<double> host;
-    size_t off[6];
+    size_t off[12];
     for (int d = 0; d < 3; d++) {
         std::vector<double> w, ce;
         build_axis(grid->n[d], grid->edges[d], bc->face[d][0], bc->face[d][1], w, ce);
         off[d] = host.size(); host.insert(host.end(), w.begin(), w.end());
         off[3 + d] = host.size(); host.insert(host.end(), ce.begin(), ce.end());
+    }
+    // reciprocal geometry for the contracted FP64 form: 1 / w and 1 / h with
+    // h = w_-/2 + w + w_+/2 (the span of the centred source differences)
+    for (int d = 0; d < 3; d++) {
+        const size_t len = (size_t)grid->n[d] + 2 * GH;
+        const double *w = host.data() + off[d];
+        std::vector<double> iw(len), ih(len, 0.0);
+        for (size_t k = 0; k < len; k++) iw[k] = 1.0 / w[k];
+        for (size_t k = 1; k + 1 < len; k++) ih[k] = 1.0 / (0.5 * w[k - 1] + w[k] + 0.5 * w[k + 1]);
+        off[6 + d] = host.size(); host.insert(host.end(), iw.begin(), iw.end());
+        off[9 + d] = host.size(); host.insert(host.end(), ih.begin(), ih.end());
     }
     int dev_sms = 152;
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -343,7 +355,10 @@ ppmlr_status ppmlr_create(const ppmlr_grid *grid, double gamma, const ppmlr_bc *
     size_t scratch_bytes = sizeof(double) * (host.size() + 2 + c->cfl_blocks) + 64;
     e = cudaMalloc(&c->geo, scratch_bytes);
     if (e != cudaSuccess) { cudaFree(c->state); delete c; return PPMLR_E_OOM; }
-    for (int d = 0; d < 3; d++) { c->w[d] = c->geo + off[d]; c->c[d] = c->geo + off[3 + d]; }
+    for (int d = 0; d < 3; d++) {
+        c->w[d] = c->geo + off[d]; c->c[d] = c->geo + off[3 + d];
+        c->iw[d] = c->geo + off[6 + d]; c->ih[d] = c->geo + off[9 + d];
+    }
     c->dt_dev = c->geo + host.size();
     c->partial = c->dt_dev + 2;
     unsigned char *tail = reinterpret_cast<unsigned char *>(c->partial + c->cfl_blocks);
@@ -369,6 +384,24 @@ ppmlr_status ppmlr_create(const ppmlr_grid *grid, double gamma, const ppmlr_bc *
     for (int d = 0; d < 3; d++) { c->tile[d] = choose_tile(d, c->n, rs); c->mode[d] = 0; }
     c->sms = dev_sms;
     c->bd = nullptr;
+    c->inner_mask = nullptr;
+    if (bc->r_inner > 0.0) {
+        // the inner-sphere test of every cell, once, with the CPU reference's expression
+        std::vector<unsigned char> mask((size_t)ncell);
+        const double *cx = host.data() + off[3] + GH, *cy = host.data() + off[4] + GH, *cz = host.data() + off[5] + GH;
+        const double r2 = bc->r_inner * bc->r_inner;
+        size_t i = 0;
+        for (int iz = 0; iz < c->n[2]; iz++)
+            for (int iy = 0; iy < c->n[1]; iy++)
+                for (int ix = 0; ix < c->n[0]; ix++, i++)
+                    mask[i] = cx[ix] * cx[ix] + cy[iy] * cy[iy] + cz[iz] * cz[iz] < r2 ? 1 : 0;
+        e = cudaMalloc(&c->inner_mask, mask.size());
+        if (e == cudaSuccess) e = cudaMemcpy(c->inner_mask, mask.data(), mask.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(c->inner_mask); cudaFree(c->geof); cudaFree(c->geo); cudaFree(c->state); delete c;
+            return e == cudaErrorMemoryAllocation ? PPMLR_E_OOM : PPMLR_E_CUDA;
+        }
+    }
     if (prec != PPMLR_MIXED && bc->dipole_moment != 0.0) {
         // the dipole at every cell centre, evaluated once by the sweeps' own formula
         e = cudaMalloc(&c->bd, sizeof(double) * c->stride * 3);
@@ -377,7 +410,8 @@ ppmlr_status ppmlr_create(const ppmlr_grid *grid, double gamma, const ppmlr_bc *
                                                    (long long)c->stride, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) {
-            cudaFree(c->bd); cudaFree(c->geof); cudaFree(c->geo); cudaFree(c->state); delete c;
+            cudaFree(c->bd); cudaFree(c->inner_mask); cudaFree(c->geof); cudaFree(c->geo); cudaFree(c->state);
+            delete c;
             return e == cudaErrorMemoryAllocation ? PPMLR_E_OOM : PPMLR_E_CUDA;
         }
     }
@@ -400,6 +434,7 @@ void ppmlr_destroy(ppmlr_ctx *c)
     for (auto &r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->pool) cudaEventDestroy(e);
     cudaFree(c->bd);
+    cudaFree(c->inner_mask);
     cudaFree(c->geof);
     cudaFree(c->geo);
     cudaFree(c->state);
@@ -489,6 +524,8 @@ static ppmlr_status launch_one_sweep(ppmlr_ctx *c, int d, double dt, const doubl
     a.riemann_iters = c->riemann_iters;
     a.dt = dt; a.dt_dev = dt_dev;
     a.bd = c->bd;
+    if (c->prec != PPMLR_MIXED) { a.iw = c->iw[d]; a.ih = c->ih[d]; }
+    a.inner_mask = c->inner_mask;
     a.flags = c->flags; a.floors = c->floors;
     a.wf = c->wf[d];
     a.cxf = c->cf[0]; a.cyf = c->cf[1]; a.czf = c->cf[2];

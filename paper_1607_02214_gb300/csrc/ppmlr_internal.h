@@ -43,6 +43,8 @@ struct SweepArgs {
     double dt;                 // used when dt_dev == nullptr
     const double *dt_dev;
     const double *bd;          // FP64 forms: dipole table (component k at bd + k * vs + cell) or null
+    const double *iw, *ih;     // FP64 forms: 1 / width and 1 / (w_-/2 + w + w_+/2) along the axis, or null
+    const unsigned char *inner_mask;   // per cell: 1 inside the inner sphere, or null
     int *flags;
     unsigned long long *floors;
     // float copies for the mixed path (geometry and parameters)

@@ -576,9 +576,15 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         }
         SM(SB0 + 7, s) = ft;
         if (a.do_src && out_cell) {
-            R h;
-            if constexpr (F64) h = R(0.5) * R(a.w[g + GH - 1]) + R(dx) + R(0.5) * R(a.w[g + GH + 1]);
-            else h = R(0.5) * a.wf[g + GH - 1] + a.wf[g + GH] + R(0.5) * a.wf[g + GH + 1];
+            // centred-difference span h; the contracted FP64 form reads 1 / h from
+            // the geometry table when the context has one
+            const bool h_table = F64 && !EX && a.ih;
+            R h = R(1);
+            if constexpr (F64) {
+                if (!h_table) h = R(0.5) * R(a.w[g + GH - 1]) + R(dx) + R(0.5) * R(a.w[g + GH + 1]);
+            } else {
+                h = R(0.5) * a.wf[g + GH - 1] + a.wf[g + GH] + R(0.5) * a.wf[g + GH + 1];
+            }
             R DB0, DB1, DB2, DA1, DA2;
             if constexpr (EX) {
                 DB0 = (SM(A_BN, s + PS) - SM(A_BN, s - PS)) / h;
@@ -587,7 +593,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
                 DA1 = (SM(A_AY, s + PS) - SM(A_AY, s - PS)) / h;
                 DA2 = (SM(A_AZ, s + PS) - SM(A_AZ, s - PS)) / h;
             } else {
-                const R ih = R(1) / h;
+                const R ih = h_table ? R(a.ih[g + GH]) : R(1) / h;
                 DB0 = (SM(A_BN, s + PS) - SM(A_BN, s - PS)) * ih;
                 DB1 = (SM(A_B1, s + PS) - SM(A_B1, s - PS)) * ih;
                 DB2 = (SM(A_B2, s + PS) - SM(A_B2, s - PS)) * ih;
@@ -831,7 +837,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         const int cmap[7] = {0, 1 + DIR, 1 + T1, 1 + T2, 4 + T1, 4 + T2, 7};
         const R dCv[7] = {R(0), dC[0], dC[1], dC[2], dC[3], dC[4], dC[5]};
         if constexpr (F64) {
-            const double idx = EX ? 0.0 : 1.0 / dx;
+            const double idx = EX ? 0.0 : (a.iw ? a.iw[g + GH] : 1.0 / dx);
 #pragma unroll
             for (int v = 0; v < 7; v++) {
                 double dU;
@@ -863,7 +869,9 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             for (int v = 0; v < 8; v++) Un[v] = Un[v] + widen(dU[v]);
         }
         bool inner = false;
-        if constexpr (F64) {
+        if (a.inner_mask) {
+            inner = a.inner_mask[gi] != 0;
+        } else if constexpr (F64) {
             inner = a.r_inner > 0.0 &&
                     pos[0] * pos[0] + pos[1] * pos[1] + pos[2] * pos[2] < a.r_inner * a.r_inner;
         } else if (a.r_innerf > 0.0f) {
