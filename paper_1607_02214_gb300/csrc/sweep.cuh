@@ -118,6 +118,19 @@ __device__ __forceinline__ void two_shock(const int iters, const R uL, const R u
     }
 }
 
+// Lagrangian fast impedance W = rho c_f without a reciprocal of rho:
+// W^2 = rho (rho c_f^2) = rho (S + sqrt(S^2 - 4 gamma p Bn^2)) / 2 with
+// S = gamma p + |B|^2 (the fast-speed formula multiplied through by rho).
+template <typename R>
+__device__ __forceinline__ R fast_impedance(R rho, R p, R Bn, R B1, R B2, R gam)
+{
+    const R gp = gam * p;
+    const R S = gp + (Bn * Bn + B1 * B1 + B2 * B2);
+    R D = S * S - R(4) * gp * (Bn * Bn);
+    if (D < R(0)) D = R(0);
+    return K<R>::sq(rho * (R(0.5) * (S + K<R>::sq(D))));
+}
+
 // Earth dipole along -z: B_d = M [3 (m.r) r - m r^2] / r^5, m = -z.
 template <bool EX = true>
 __device__ __forceinline__ void dipole(double M, double x, double y, double z, double *B)
@@ -682,8 +695,14 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         R Bnf = R(0.5) * (Bn + SM(A_BN, s + PS));
         R PL = sl[6] + R(0.5) * (sl[4] * sl[4] + sl[5] * sl[5]);
         R PR = Rs[6] + R(0.5) * (Rs[4] * Rs[4] + Rs[5] * Rs[5]);
-        R WL = sl[0] * K<R>::sq(fast2<R, EX>(sl[0], sl[6], Bnf, sl[4], sl[5], gam));
-        R WR = Rs[0] * K<R>::sq(fast2<R, EX>(Rs[0], Rs[6], Bnf, Rs[4], Rs[5], gam));
+        R WL, WR;
+        if constexpr (EX || !F64) {
+            WL = sl[0] * K<R>::sq(fast2<R, EX>(sl[0], sl[6], Bnf, sl[4], sl[5], gam));
+            WR = Rs[0] * K<R>::sq(fast2<R, EX>(Rs[0], Rs[6], Bnf, Rs[4], Rs[5], gam));
+        } else {            // contracted FP64 form: no reciprocal of the traced densities
+            WL = fast_impedance<R>(sl[0], sl[6], Bnf, sl[4], sl[5], gam);
+            WR = fast_impedance<R>(Rs[0], Rs[6], Bnf, Rs[4], Rs[5], gam);
+        }
         if (a.riemann_iters > 0 && PL > R(0) && PR > R(0))
             two_shock<R, EX>(a.riemann_iters, sl[1], Rs[1], PL, PR, gam, WL, WR);
         R us, Ps;
