@@ -212,27 +212,22 @@ bool ppmlr::validate_grid_bc(const ppmlr_grid *grid, const ppmlr_bc *bc)
     return ncell <= (1LL << 31) - 1;
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_fn() { return tensor_map_encoder(); }
 
-static EncodeTiledFn encode_fn()
+EncodeTiledFn ppmlr::tensor_map_encoder()
 {
-    static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {     // looked up once (thread-safe)
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)p;
-    }
+            return (EncodeTiledFn)p;
+        return nullptr;
+    }();
     return fn;
 }
 
-static size_t stage_pad_bytes(const Tile &t) { return ((size_t)8 * t.NP * t.L * sizeof(double) + 1023) / 1024 * 1024; }
 
 // The TMA form applies to y and z sweeps whose box fits the copy engine's
 // rules: lanes (x extent) even and rows 16-byte aligned (nx even), at most

@@ -12,6 +12,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -47,7 +48,9 @@ struct ppmlr_ens {
     size_t smem[3];
     int maxt[3];                 // tile thread budget chosen per direction
     int mode[3];                 // 0: persistent work queue, 1: one block per tile (table),
-                                 // 2: one block per tile (arguments in the kernel parameter)
+                                 // 2: one block per tile (arguments in the kernel parameter),
+                                 // 3: one block per tile, input box staged by TMA (y, z)
+    CUtensorMap *d_maps[3];      // mode 3: per instance the maps of its two state sets
     std::vector<SweepArgs> host_args[3];
     std::vector<Tile> tiles[3];
     // CFL tables for states in A and in B
@@ -79,9 +82,28 @@ static ppmlr_status efail(ppmlr_ens *e, ppmlr_status s, const std::string &m)
 
 static size_t real_size(const ppmlr_ens *e) { return e->prec == PPMLR_MIXED ? sizeof(float) : sizeof(double); }
 
-// Tile shapes of every instance for one direction under a thread budget.
-static void plan_direction(ppmlr_ens *e, int d, int maxt, int mode)
+// Tile shapes of every instance for one direction under a thread budget;
+// false (nothing changed) when `mode` cannot serve every instance.
+static bool plan_direction(ppmlr_ens *e, int d, int maxt, int mode)
 {
+    if (mode == 3) {     // TMA staging: y/z only, every instance's box within the copy engine's rules
+        if (d == 0 || !tensor_map_encoder()) return false;
+        size_t sm = 0;
+        int thr = 32;
+        for (int i = 0; i < e->count; i++) {
+            const int *n = &e->n[3 * i];
+            int nchunk = 1, C = n[d];
+            while (C + 2 * GH > maxt) { nchunk++; C = (n[d] + nchunk - 1) / nchunk; }
+            int L = maxt / (C + 2 * GH), p2 = 1;
+            while (p2 * 2 <= L && p2 * 2 <= 16) p2 *= 2;
+            while (p2 > 1 && p2 / 2 >= n[0]) p2 /= 2;
+            const Tile t = make_tile(d, n, real_size(e), C, p2);
+            if (t.L < 2 || (t.L & 1) || t.NP > 256 || (n[0] & 1)) return false;
+            sm = std::max(sm, stage_pad_bytes(t) + t.smem);
+            thr = std::max(thr, t.threads);
+        }
+        if (sm > 224 * 1024 || sweep_launchers(e->prec).ens_tma_per_sm(d, thr, sm) < 1) return false;
+    }
     e->maxt[d] = maxt;
     e->mode[d] = mode;
     e->tiles[d].clear();
@@ -104,7 +126,8 @@ static void plan_direction(ppmlr_ens *e, int d, int maxt, int mode)
         Tile t = make_tile(d, n, real_size(e), C, L);
         e->tiles[d].push_back(t);
         if (t.threads > thr) thr = t.threads;
-        if (t.smem > sm) sm = t.smem;
+        const size_t need = mode == 3 ? stage_pad_bytes(t) + t.smem : t.smem;
+        if (need > sm) sm = need;
         total += t.ntiles;
     }
     e->threads[d] = thr;
@@ -114,6 +137,35 @@ static void plan_direction(ppmlr_ens *e, int d, int maxt, int mode)
     int b = per_sm * e->sms;
     e->blocks[d] = (mode != 0 || b > total) ? total : b;
     if (mode == 0 && e->blocks[d] == total && total > 1) e->blocks[d] = total - 1;   // keep it persistent
+    return true;
+}
+
+// Tensor maps of every instance's two state sets for the TMA form along d:
+// a 4D view (x, y, z, variable) with box L lanes x NP positions x 8 arrays.
+static ppmlr_status upload_maps(ppmlr_ens *e, int d)
+{
+    std::vector<CUtensorMap> maps(2 * (size_t)e->count);
+    for (int i = 0; i < e->count; i++) {
+        const int *n = &e->n[3 * i];
+        const Tile &t = e->tiles[d][i];
+        const long long vs = (long long)(e->A[8 * i + 1] - e->A[8 * i]);
+        const cuuint64_t dims[4] = {(cuuint64_t)n[0], (cuuint64_t)n[1], (cuuint64_t)n[2], 8};
+        const cuuint64_t strides[3] = {(cuuint64_t)n[0] * 8, (cuuint64_t)n[0] * n[1] * 8, (cuuint64_t)vs * 8};
+        cuuint32_t box[4] = {(cuuint32_t)t.L, 1, 1, 8};
+        box[d] = (cuuint32_t)t.NP;
+        const cuuint32_t es[4] = {1, 1, 1, 1};
+        for (int b = 0; b < 2; b++) {
+            void *base = b == 0 ? e->A[8 * i] : e->B[8 * i];
+            CUresult r = tensor_map_encoder()(&maps[2 * i + b], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, base, dims, strides,
+                                              box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return efail(e, PPMLR_E_INVALID, "ensemble: tensor map rejected");
+        }
+    }
+    if (!e->d_maps[d]) ECK(e, cudaMalloc(&e->d_maps[d], sizeof(CUtensorMap) * maps.size()), "tensor map table");
+    ECK(e, cudaMemcpyAsync(e->d_maps[d], maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
+                           e->stream), "tensor map upload");
+    return PPMLR_OK;
 }
 
 // Upload the per-instance sweep arguments and first-tile table of a direction.
@@ -159,6 +211,10 @@ static ppmlr_status upload_direction(ppmlr_ens *e, int d)
         acc += t.ntiles;
     }
     e->host_args[d] = args;
+    if (e->mode[d] == 3) {
+        ppmlr_status st = upload_maps(e, d);
+        if (st != PPMLR_OK) return st;
+    }
     ECK(e, cudaMemcpyAsync(e->d_args[d], args.data(), sizeof(SweepArgs) * e->count, cudaMemcpyHostToDevice,
                            e->stream), "ensemble args upload");
     ECK(e, cudaMemcpyAsync(e->d_first_tile[d], first.data(), sizeof(int) * e->count, cudaMemcpyHostToDevice,
@@ -182,6 +238,7 @@ static cudaError_t launch_dir(ppmlr_ens *e, int d, int flip, unsigned int *queue
         return L.param(d, p, e->blocks[d], e->threads[d], e->smem[d], s);
     }
     EnsSweepArgs ea{e->d_args[d], e->d_first_tile[d], e->count, e->total_tiles[d], flip, queue};
+    if (e->mode[d] == 3) return L.ens_tma(d, ea, e->d_maps[d], e->blocks[d], e->threads[d], e->smem[d], s);
     return L.ens(d, ea, e->blocks[d], e->threads[d], e->smem[d], s);
 }
 
@@ -387,6 +444,7 @@ void ppmlr_ensemble_destroy(ppmlr_ens *e)
     drop_graphs(e);
     if (e->cap) cudaStreamDestroy(e->cap);
     cudaFree(e->dev_alloc);
+    for (int d = 0; d < 3; d++) cudaFree(e->d_maps[d]);
     cudaFree(e->geof);
     cudaFree(e->geo);
     cudaFree(e->state);
@@ -515,10 +573,10 @@ ppmlr_status ppmlr_ensemble_autotune(ppmlr_ens *e, double *best_ms)
     for (int d = 0; d < 3; d++) {
         float best = 1e30f;
         int best_t = e->maxt[d], best_m = e->mode[d];
-        const int nmodes = e->count <= ENS_PARAM_MAX ? 3 : 2;
-        for (int k = 0; k < nmodes * nc; k++) {
+        for (int k = 0; k < 4 * nc; k++) {
             const int mode = k / nc;
-            plan_direction(e, d, cands[k % nc], mode);
+            if (mode == 2 && e->count > ENS_PARAM_MAX) continue;
+            if (!plan_direction(e, d, cands[k % nc], mode)) continue;
             ppmlr_status st = upload_direction(e, d);
             if (st != PPMLR_OK) return st;
             float tot = 0.0f;
@@ -595,6 +653,21 @@ ppmlr_status ppmlr_ensemble_time_kernels(ppmlr_ens *e, double cfl, int nsteps, d
         }
     for (auto &x : ev) cudaEventDestroy(x);
     for (int j = 0; j < 4; j++) avg_ms[j] = cnt[j] ? tot[j] / cnt[j] : 0.0;
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_ensemble_set_launch(ppmlr_ens *e, int axis, int form, int budget)
+{
+    if (!e) return PPMLR_E_INVALID;
+    const int maxb = e->prec == PPMLR_MIXED ? MAXT : MAXT_F64;
+    if (axis < 0 || axis > 2 || form < 0 || form > 3 || budget < 2 * GH + 1 || budget > maxb)
+        return efail(e, PPMLR_E_INVALID, "set_launch: bad axis, form or budget");
+    if (form == 2 && e->count > ENS_PARAM_MAX) return efail(e, PPMLR_E_INVALID, "set_launch: form 2 takes at most 64 instances");
+    if (!plan_direction(e, axis, budget, form))
+        return efail(e, PPMLR_E_INVALID, "set_launch: the TMA form does not fit every instance along this axis");
+    ppmlr_status st = upload_direction(e, axis);
+    if (st != PPMLR_OK) return st;
+    drop_graphs(e);
     return PPMLR_OK;
 }
 

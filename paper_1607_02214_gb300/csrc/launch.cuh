@@ -102,6 +102,40 @@ struct SweepVariant {
         return dir == 1 ? tma_dir<1, false>(a, map, blocks, threads, smem, s)
                         : tma_dir<2, false>(a, map, blocks, threads, smem, s);
     }
+    // ensemble y/z sweep with TMA-staged input boxes (one block per tile)
+    template <int DIR>
+    static cudaError_t allow_ens_tma_smem()
+    {
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, sweep_ensemble_tma_kernel<DIR, R, EX>);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(sweep_ensemble_tma_kernel<DIR, R, EX>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - (int)fa.sharedSizeBytes);
+    }
+    static cudaError_t ens_tma(int dir, const EnsSweepArgs &e, const CUtensorMap *maps, int blocks, int threads,
+                               size_t smem, cudaStream_t s)
+    {
+        static bool attr[3] = {false, false, false};
+        if (dir < 1 || dir > 2) return cudaErrorInvalidValue;
+        if (!attr[dir]) {
+            cudaError_t r = dir == 1 ? allow_ens_tma_smem<1>() : allow_ens_tma_smem<2>();
+            if (r != cudaSuccess) return r;
+            attr[dir] = true;
+        }
+        if (dir == 1) sweep_ensemble_tma_kernel<1, R, EX><<<blocks, threads, smem, s>>>(e, maps);
+        else sweep_ensemble_tma_kernel<2, R, EX><<<blocks, threads, smem, s>>>(e, maps);
+        return cudaGetLastError();
+    }
+    static int ens_tma_per_sm(int dir, int threads, size_t smem)
+    {
+        if (dir < 1 || dir > 2) return 0;
+        if ((dir == 1 ? allow_ens_tma_smem<1>() : allow_ens_tma_smem<2>()) != cudaSuccess) return 0;
+        int n = 0;
+        cudaError_t r = dir == 1
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_ensemble_tma_kernel<1, R, EX>, threads, smem)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_ensemble_tma_kernel<2, R, EX>, threads, smem);
+        return r == cudaSuccess ? n : 0;
+    }
     static cudaError_t dipole_table(double M, const int n[3], const double *cx, const double *cy, const double *cz,
                                     double *bd, long long vs, cudaStream_t s)
     {
@@ -144,7 +178,7 @@ struct SweepVariant {
     static constexpr SweepLaunchers table()
     {
         return {single, ens, param, per_sm, tma, tma_per_sm,
-                std::is_same<R, double>::value ? &dipole_table : nullptr};
+                std::is_same<R, double>::value ? &dipole_table : nullptr, ens_tma, ens_tma_per_sm};
     }
 };
 

@@ -120,7 +120,19 @@ struct SweepLaunchers {
     // dipole table of a single domain (null for the mixed path, which evaluates it in float)
     cudaError_t (*dipole_table)(double M, const int n[3], const double *cx, const double *cy, const double *cz,
                                 double *bd, long long vs, cudaStream_t s);
+    // ensemble y/z sweep, input boxes staged by TMA through per-instance tensor maps
+    cudaError_t (*ens_tma)(int dir, const EnsSweepArgs &e, const CUtensorMap *maps, int blocks, int threads,
+                           size_t smem, cudaStream_t s);
+    int (*ens_tma_per_sm)(int dir, int threads, size_t smem);
 };
+
+// cuTensorMapEncodeTiled from the driver (null if unavailable)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn tensor_map_encoder();
+// bytes of a tile's staged input box, padded to 1 KB (the exchange arrays follow it)
+inline size_t stage_pad_bytes(const Tile &t) { return ((size_t)8 * t.NP * t.L * sizeof(double) + 1023) / 1024 * 1024; }
 extern const SweepLaunchers k_sweep_fp64, k_sweep_fp64_exact, k_sweep_mixed;
 inline const SweepLaunchers &sweep_launchers(ppmlr_precision p)
 {

@@ -1121,6 +1121,50 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_grid_kern
     sweep_tile<DIR, R, EX, const SweepArgs>(args, t - __ldg(e.first_tile + lo), smem_raw, e.flip);
 }
 
+// Ensemble, one block per tile of a y or z sweep with the tile's input box
+// staged by TMA: the block finds its instance, copies its arguments to shared
+// memory and loads the box through that instance's tensor map (maps[2 * i +
+// b], b = the buffer holding the input: 0 = the instance's first state set,
+// 1 = its second; the array lives in global memory, written before the
+// launch).  The wait is bounded; a block that gives up raises FLAG_TIMEOUT.
+template <int DIR, typename R, bool EX>
+__global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_tma_kernel(EnsSweepArgs e,
+                                                                                  const CUtensorMap *maps)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ SweepArgs args;
+    __shared__ __align__(8) unsigned long long bar;
+    const int t = blockIdx.x;
+    int lo = 0, hi = e.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(e.first_tile + mid) <= t) lo = mid; else hi = mid - 1;
+    }
+    const int *src = reinterpret_cast<const int *>(e.args + lo);
+    int *dst = reinterpret_cast<int *>(&args);
+    for (int k = threadIdx.x; k < (int)(sizeof(SweepArgs) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int tile = t - __ldg(e.first_tile + lo);
+    const size_t stage_bytes = (size_t)8 * args.NP * args.L * sizeof(double);
+    const size_t stage_pad = (stage_bytes + 1023) / 1024 * 1024;
+    double *stage = reinterpret_cast<double *>(smem_raw);
+    if (threadIdx.x == 0) {
+        int cx, cy, cz;
+        tile_box_origin<DIR>(args, tile, cx, cy, cz);
+        mbar_expect_tx(&bar, (unsigned)stage_bytes);
+        tma_load_4d(stage, maps + 2 * lo + e.flip, cx, cy, cz, 0, &bar);
+    }
+    if (!mbar_wait(&bar, 0u)) {
+        if (threadIdx.x == 0) atomicOr(args.flags, FLAG_TIMEOUT);
+        return;
+    }
+    sweep_tile<DIR, R, EX, const SweepArgs>(args, tile, smem_raw + stage_pad, e.flip, stage);
+}
+
 // Ensemble, one block per tile, arguments of all instances in the kernel
 // parameter (constant bank): the block finds its instance from the first-tile
 // table and reads that instance's fields straight from the parameter space.

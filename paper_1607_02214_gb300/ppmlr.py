@@ -80,6 +80,7 @@ SIGNATURES = [
     ("ppmlr_ensemble_autotune", c_int, [c_void_p, POINTER(c_double)]),
     ("ppmlr_ensemble_get_tiles", c_int, [c_void_p, POINTER(c_int)]),
     ("ppmlr_ensemble_set_riemann_solver", c_int, [c_void_p, c_int]),
+    ("ppmlr_ensemble_set_launch", c_int, [c_void_p, c_int, c_int, c_int]),
     ("ppmlr_ensemble_get_dt", c_int, [c_void_p, POINTER(c_double)]),
     ("ppmlr_ensemble_check", c_int, [c_void_p]),
     ("ppmlr_ensemble_get_diagnostics", c_int, [c_void_p, POINTER(c_longlong), POINTER(c_longlong)]),
@@ -430,6 +431,11 @@ class Ensemble:
     def set_riemann_solver(self, iters):
         """0: two-wave Riemann solver; k > 0: k two-shock Newton steps."""
         return self._check(load().ppmlr_ensemble_set_riemann_solver(self._h, int(iters)))
+
+    def set_launch(self, axis, form, budget, raise_on_error=True):
+        """Fix one direction's launch form (0..3) and tile budget."""
+        st = load().ppmlr_ensemble_set_launch(self._h, int(axis), int(form), int(budget))
+        return self._check(st) if raise_on_error else st
 
     def dt(self):
         out = (c_double * self.count)()

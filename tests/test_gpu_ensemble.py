@@ -104,3 +104,28 @@ def test_autotune_changes_speed_not_results(precision):
     b.step_cfl(0.4, 3)
     assert np.array_equal(a.get_state(), b.get_state())
     assert a.diagnostics()["floor_hits"] == b.diagnostics()["floor_hits"]
+
+
+@pytest.mark.parametrize("precision", [ppmlr.PPMLR_FP64_EXACT, ppmlr.PPMLR_FP64, ppmlr.PPMLR_MIXED])
+def test_ensemble_tma_form_matches_the_other_forms(precision):
+    probs = small_ensemble(5)
+    a = ppmlr.Ensemble(probs, precision=precision)
+    b = ppmlr.Ensemble(probs, precision=precision)
+    for axis in (1, 2):
+        b.set_launch(axis, 3, 256)                   # TMA-staged y/z boxes, per-instance tensor maps
+    assert b.tiles()[1] // 1000 == 3 and b.tiles()[2] // 1000 == 3
+    for i, p in enumerate(probs):
+        a.set_state(i, p.U0)
+        b.set_state(i, p.U0)
+    a.step(0.4, 4)
+    b.step(0.4, 4)
+    b.check()
+    for i in range(len(probs)):
+        if precision == ppmlr.PPMLR_FP64_EXACT:
+            assert np.array_equal(a.get_state(i), b.get_state(i)), i
+        else:
+            tol = 1e-12 if precision == ppmlr.PPMLR_FP64 else 1e-6
+            assert np.max(rel_l1(b.get_state(i), a.get_state(i))) <= tol, i
+    assert b.set_launch(0, 3, 256, raise_on_error=False) == ppmlr.PPMLR_E_INVALID   # no TMA form along x
+    odd = ppmlr.Ensemble([inputs.magnetosphere(n=(41, 30, 30), h0=1.0)], precision=precision)
+    assert odd.set_launch(1, 3, 256, raise_on_error=False) == ppmlr.PPMLR_E_INVALID  # nx odd
