@@ -229,19 +229,27 @@ EncodeTiledFn ppmlr::tensor_map_encoder()
 }
 
 
-// The TMA form applies to y and z sweeps whose box fits the copy engine's
-// rules: lanes (x extent) even and rows 16-byte aligned (nx even), at most
-// 256 positions along the sweep axis, both staging buffers plus the exchange
-// arrays within shared memory.
+// The TMA forms apply where the tile's box fits the copy engine's rules: rows
+// 16-byte aligned (nx even) and every box dimension at most 256.  y/z sweeps:
+// lanes (the x extent of the box) even.  x sweep (one tile per block only):
+// C even so that the box's x origin g0 - 8 is even, and L pencils that lie in
+// one z plane (ny a multiple of L).  The staging buffer(s) plus the exchange
+// arrays must fit in shared memory.
 static const char *tma_ineligible(const ppmlr_ctx *c, int d, const Tile &t, int form)
 {
-    if (d == 0) return "the x sweep has no TMA form";
     if (!encode_fn()) return "cuTensorMapEncodeTiled is not available from the driver";
-    if (t.L < 2 || (t.L & 1)) return "the TMA form needs an even number of lanes";
-    if (t.NP > 256) return "the TMA form needs at most 256 positions per tile (C + 14)";
     if (c->n[0] & 1) return "the TMA form needs nx even (16-byte aligned rows)";
+    if (d == 0) {
+        if (form != 2) return "the x sweep has only the one-tile TMA form (2)";
+        if (t.C & 1) return "the x-sweep TMA form needs an even chunk length C";
+        if (t.NP + 2 > 256) return "the x-sweep TMA form needs at most 254 positions per tile (C + 14)";
+        if (c->n[1] % t.L) return "the x-sweep TMA form needs ny to be a multiple of the lanes L";
+    } else {
+        if (t.L < 2 || (t.L & 1)) return "the TMA form needs an even number of lanes";
+        if (t.NP > 256) return "the TMA form needs at most 256 positions per tile (C + 14)";
+    }
     const int persist = form == 1;
-    const size_t smem = (persist ? 2 : 1) * stage_pad_bytes(t) + t.smem;
+    const size_t smem = (persist ? 2 : 1) * stage_pad_bytes(t, d) + t.smem;
     if (smem > 226 * 1024) return "the TMA staging buffers do not fit in shared memory";   // 1 KB static
     if (sweep_launchers(c->prec).tma_per_sm(d, persist, t.threads, smem) < 1)
         return "the TMA kernel cannot be resident with this tile shape";
@@ -253,7 +261,8 @@ static bool tma_eligible(const ppmlr_ctx *c, int d, const Tile &t, int form)
 }
 
 // Tensor maps of direction d for both state buffers: a 4D view (x, y, z,
-// variable) of the 8 equally spaced arrays; box = L lanes x NP positions.
+// variable) of the 8 equally spaced arrays; box = L lanes x NP positions
+// (x sweep: NP + 2 cells x L pencils).
 // Returns nullptr on success, else the reason.
 static const char *setup_tma_why(ppmlr_ctx *c, int d, int form)
 {
@@ -264,6 +273,7 @@ static const char *setup_tma_why(ppmlr_ctx *c, int d, int form)
                                    (cuuint64_t)c->stride * 8};
     cuuint32_t box[4] = {(cuuint32_t)t.L, 1, 1, 8};
     box[d] = (cuuint32_t)t.NP;
+    if (d == 0) { box[0] = (cuuint32_t)(t.NP + 2); box[1] = (cuuint32_t)t.L; }   // L pencils of one z plane
     const cuuint32_t es[4] = {1, 1, 1, 1};
     for (int b = 0; b < 2; b++) {
         void *base = c->state + (size_t)b * 8 * c->stride;
@@ -273,7 +283,7 @@ static const char *setup_tma_why(ppmlr_ctx *c, int d, int form)
         if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled rejected the state layout";
     }
     const int persist = form == 1;
-    c->tma_smem[d] = (persist ? 2 : 1) * stage_pad_bytes(t) + t.smem;
+    c->tma_smem[d] = (persist ? 2 : 1) * stage_pad_bytes(t, d) + t.smem;
     const int per_sm = sweep_launchers(c->prec).tma_per_sm(d, persist, t.threads, c->tma_smem[d]);
     const long long b = (long long)per_sm * c->sms;
     c->tma_blocks[d] = persist ? (int)(b < t.ntiles ? b : t.ntiles) : t.ntiles;

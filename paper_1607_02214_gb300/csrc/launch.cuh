@@ -98,9 +98,11 @@ struct SweepVariant {
     {
         if (persist)
             return dir == 1 ? tma_dir<1, true>(a, map, blocks, threads, smem, s)
-                            : tma_dir<2, true>(a, map, blocks, threads, smem, s);
-        return dir == 1 ? tma_dir<1, false>(a, map, blocks, threads, smem, s)
-                        : tma_dir<2, false>(a, map, blocks, threads, smem, s);
+                   : dir == 2 ? tma_dir<2, true>(a, map, blocks, threads, smem, s)
+                              : cudaErrorInvalidValue;      // x: one tile per block only
+        return dir == 0 ? tma_dir<0, false>(a, map, blocks, threads, smem, s)
+               : dir == 1 ? tma_dir<1, false>(a, map, blocks, threads, smem, s)
+                          : tma_dir<2, false>(a, map, blocks, threads, smem, s);
     }
     // ensemble y/z sweep with TMA-staged input boxes (one block per tile)
     template <int DIR>
@@ -152,8 +154,10 @@ struct SweepVariant {
     static int tma_per_sm(int dir, int persist, int threads, size_t smem)
     {
         if (persist)
-            return dir == 1 ? tma_per_sm_dir<1, true>(threads, smem) : tma_per_sm_dir<2, true>(threads, smem);
-        return dir == 1 ? tma_per_sm_dir<1, false>(threads, smem) : tma_per_sm_dir<2, false>(threads, smem);
+            return dir == 1 ? tma_per_sm_dir<1, true>(threads, smem)
+                   : dir == 2 ? tma_per_sm_dir<2, true>(threads, smem) : 0;
+        return dir == 0 ? tma_per_sm_dir<0, false>(threads, smem)
+               : dir == 1 ? tma_per_sm_dir<1, false>(threads, smem) : tma_per_sm_dir<2, false>(threads, smem);
     }
     static cudaError_t single(int dir, const SweepArgs &a, const Tile &t, cudaStream_t s)
     {

@@ -131,8 +131,13 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeTiledFn tensor_map_encoder();
-// bytes of a tile's staged input box, padded to 1 KB (the exchange arrays follow it)
-inline size_t stage_pad_bytes(const Tile &t) { return ((size_t)8 * t.NP * t.L * sizeof(double) + 1023) / 1024 * 1024; }
+// bytes of a tile's staged input box along direction d, padded to 1 KB (the
+// exchange arrays follow it); x boxes hold NP + 2 cells per lane row
+inline size_t stage_pad_bytes(const Tile &t, int d = 1)
+{
+    const size_t rows = (size_t)(d == 0 ? t.NP + 2 : t.NP) * t.L;
+    return (8 * rows * sizeof(double) + 1023) / 1024 * 1024;
+}
 extern const SweepLaunchers k_sweep_fp64, k_sweep_fp64_exact, k_sweep_mixed;
 inline const SweepLaunchers &sweep_launchers(ppmlr_precision p)
 {

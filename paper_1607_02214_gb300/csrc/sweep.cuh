@@ -359,6 +359,19 @@ enum : int {
     SB0 = 13, SC0 = 21
 };
 
+// Layout of a tile's input box staged in shared memory (8 arrays).  y/z
+// sweeps: NP positions x L lanes in slot order (position-major, lanes
+// consecutive x cells).  x sweep: the box starts one cell before the tile's
+// first position so that the copy starts on an even x (16-byte aligned) and
+// holds NP + 2 cells per lane row, lane-major.
+template <int DIR>
+__device__ __forceinline__ int stage_index(int l, int ps, int NP, int L)
+{
+    return DIR == 0 ? l * (NP + 2) + ps + 1 : ps * L + l;
+}
+template <int DIR>
+__device__ __forceinline__ int stage_array_stride(int NP, int L) { return DIR == 0 ? (NP + 2) * L : NP * L; }
+
 // One tile of one sweep, processed by the calling block.  `a` describes the
 // domain (the single-domain kernel passes its launch argument, the ensemble
 // kernel a per-instance copy in shared memory); `tile` is the tile index
@@ -465,9 +478,9 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         if (!fixed) {
             const int ps = src - (g0 - GH);                 // position of the source cell in the box
             if (stage && ps >= 0 && ps < NP) {
-                const int slot = DIR == 0 ? l * NP + ps : ps * L + l;
+                const int slot = stage_index<DIR>(l, ps, NP, L), sv = stage_array_stride<DIR>(NP, L);
 #pragma unroll
-                for (int v = 0; v < 8; v++) Uc[v] = stage[v * NT + slot];
+                for (int v = 0; v < 8; v++) Uc[v] = stage[v * sv + slot];
             } else {
                 const long long gi = base + (long long)src * stride;
 #pragma unroll
@@ -525,9 +538,9 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             df q[8];
             const int ps = src - (g0 - GH);                 // position of the source cell in the box
             if (stage && ps >= 0 && ps < NP) {
-                const int slot = DIR == 0 ? l * NP + ps : ps * L + l;
+                const int slot = stage_index<DIR>(l, ps, NP, L), sv = stage_array_stride<DIR>(NP, L);
 #pragma unroll
-                for (int v = 0; v < 8; v++) q[v] = split_double(stage[v * NT + slot]);
+                for (int v = 0; v < 8; v++) q[v] = split_double(stage[v * sv + slot]);
             } else {
                 const long long gi = base + (long long)src * stride;
 #pragma unroll
@@ -847,8 +860,9 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         const long long gi = base + (long long)g * stride;
         double Un[8];
         if (stage) {
+            const int slot = stage_index<DIR>(l, p, NP, L), sv = stage_array_stride<DIR>(NP, L);
 #pragma unroll
-            for (int v = 0; v < 8; v++) Un[v] = stage[v * NT + s];
+            for (int v = 0; v < 8; v++) Un[v] = stage[v * sv + slot];
         } else {
 #pragma unroll
             for (int v = 0; v < 8; v++) Un[v] = __ldg(Uin + v * vs + gi);
@@ -969,12 +983,21 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, i
 template <typename R> struct MaxThreads { static constexpr int value = MAXT; };
 template <> struct MaxThreads<double> { static constexpr int value = MAXT_F64; };
 
-// Box origin (x, y, z) of a tile of the y or z sweep: lanes along x from
-// xg * L, positions along the sweep axis from g0 - GH.
+// Box origin (x, y, z) of a tile.  y/z sweeps: lanes along x from xg * L,
+// positions along the sweep axis from g0 - GH.  x sweep: positions from
+// g0 - GH - 1 (even: C is even for this form), lanes = L consecutive pencils
+// of one z plane (ny is a multiple of L for this form).
 template <int DIR>
 __device__ __forceinline__ void tile_box_origin(const SweepArgs &a, int tile, int &cx, int &cy, int &cz)
 {
     const int chunk = tile % a.nchunk, grp = tile / a.nchunk;
+    if (DIR == 0) {
+        const int q = grp * a.L;
+        cx = chunk * a.C - GH - 1;
+        cy = q % a.n[1];
+        cz = q / a.n[1];
+        return;
+    }
     const int xg = grp % a.ngx, t = grp / a.ngx;
     cx = xg * a.L;
     if (DIR == 1) { cy = chunk * a.C - GH; cz = t; }
@@ -986,7 +1009,7 @@ __device__ __forceinline__ void tile_box_origin(const SweepArgs &a, int tile, in
 template <typename R, bool PERSIST> struct TmaMinBlocks { static constexpr int value = 1; };
 template <bool PERSIST> struct TmaMinBlocks<float, PERSIST> { static constexpr int value = 2; };
 
-// Single domain, y or z sweep, input staged by TMA.  PERSIST: each block
+// Single domain, input staged by TMA (any direction).  PERSIST: each block
 // takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...; while it computes one
 // tile, the tensor memory accelerator copies the next tile's input box (all 8
 // state arrays, NP positions x L lanes) into the other of two shared buffers.
@@ -999,13 +1022,12 @@ __global__ void __launch_bounds__(MaxThreads<R>::value, TmaMinBlocks<R, PERSIST>
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long bar[2];
-    const int NT = a.NP * a.L;
-    const size_t stage_bytes = (size_t)8 * NT * sizeof(double);
+    const size_t stage_bytes = (size_t)8 * stage_array_stride<DIR>(a.NP, a.L) * sizeof(double);
     const size_t stage_pad = (stage_bytes + 1023) / 1024 * 1024;
     double *stage0 = reinterpret_cast<double *>(smem_raw);
     double *stage1 = reinterpret_cast<double *>(smem_raw + (PERSIST ? stage_pad : 0));
     unsigned char *work = smem_raw + (PERSIST ? 2 : 1) * stage_pad;
-    const int ntiles = a.nchunk * a.ngx * (DIR == 1 ? a.n[2] : a.n[1]);
+    const int ntiles = DIR == 0 ? a.nchunk * a.ngx : a.nchunk * a.ngx * (DIR == 1 ? a.n[2] : a.n[1]);
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);

@@ -30,8 +30,10 @@ CASES = {
     "periodic_ragged": lambda: periodic_random((38, 29, 23), 4),
     "chunked": lambda: periodic_random((6, 300, 290), 8),
 }
-# forced (axis, C, L): three chunks per y and z pencil, the last one ragged
-TILES = {"chunked": [(1, 100, 2), (2, 97, 2)]}
+# forced (axis, C, L).  x: C even and L dividing ny (the x-sweep box holds L
+# pencils of one z plane); chunked y/z: three chunks per pencil, the last ragged
+TILES = {"magnetosphere": [(0, 48, 4)], "periodic_ragged": [(0, 38, 1)],
+         "chunked": [(0, 6, 4), (1, 100, 2), (2, 97, 2)]}
 
 
 @pytest.mark.parametrize("precision", [ppmlr.PPMLR_FP64_EXACT, ppmlr.PPMLR_FP64, ppmlr.PPMLR_MIXED])
@@ -46,13 +48,14 @@ def test_tma_forms_match_plain(case, precision, form):
         got.set_tiles(axis, C, L)
         assert got.tiles()[0][axis] == C and got.tiles()[1][axis] == L
     used, why = 0, []
-    for axis in (1, 2):
+    for axis in (0, 1, 2):
         if got.set_sweep_form(axis, form, raise_on_error=False) == ppmlr.PPMLR_OK:
             used += 1
         else:
             why.append(ppmlr.load().ppmlr_last_error(got._h).decode())
-    assert used >= 1, why
-    assert got.sweep_forms()[1:] != [0, 0]
+    assert used >= (3 if form == 2 else 2), why       # x has the one-tile form only
+    assert got.sweep_forms()[1:] == [form, form]
+    assert got.sweep_forms()[0] == (form if form == 2 else 0)
     for _ in range(3):
         dt = ref.cfl_dt(0.4)
         ref.step(dt)
