@@ -291,16 +291,17 @@ ppmlr_status ppmlr_ensemble_time_kernels(ppmlr_ens *ens, double cfl, int nsteps,
  * the tiles of all instances and the launch form (0: persistent blocks taking
  * tiles from a work counter; 1: one block per tile, arguments from a device
  * table; 2: one block per tile, arguments of all instances in the kernel
- * parameter, up to 64 instances; 3: y/z only, one block per tile with the
- * input box staged by TMA), timed out of place; best_ms: 3 entries or NULL. */
+ * parameter, up to 64 instances; 3: one block per tile with the input box
+ * staged by TMA), timed out of place; best_ms: 3 entries or NULL. */
 ppmlr_status ppmlr_ensemble_autotune(ppmlr_ens *ens, double *best_ms);
 /* Fix the launch of one sweep direction instead of autotuning it: form 0 =
  * persistent blocks taking tiles from a work counter, 1 = one block per tile
  * (arguments from a device table), 2 = one block per tile (arguments of all
  * instances in the kernel parameter; at most 64 instances), 3 = one block per
- * tile of a y or z sweep with the tile's input box staged by the tensor
- * memory accelerator through per-instance tensor maps (every instance needs
- * nx even and at most 256 positions per tile); budget = positions x lanes per
+ * tile with the tile's input box staged by the tensor memory accelerator
+ * through per-instance tensor maps (every instance needs nx even and at most
+ * 256 positions per tile; along x also C even and ny a multiple of the
+ * lanes); budget = positions x lanes per
  * tile (15..448 for the FP64 forms, ..512 for PPMLR_MIXED).  Drops the step
  * graphs.  PPMLR_E_INVALID (launch unchanged) when the form does not fit. */
 ppmlr_status ppmlr_ensemble_set_launch(ppmlr_ens *ens, int axis, int form, int budget);

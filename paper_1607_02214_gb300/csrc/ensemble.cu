@@ -86,20 +86,27 @@ static size_t real_size(const ppmlr_ens *e) { return e->prec == PPMLR_MIXED ? si
 // false (nothing changed) when `mode` cannot serve every instance.
 static bool plan_direction(ppmlr_ens *e, int d, int maxt, int mode)
 {
-    if (mode == 3) {     // TMA staging: y/z only, every instance's box within the copy engine's rules
-        if (d == 0 || !tensor_map_encoder()) return false;
+    if (mode == 3) {     // TMA staging: every instance's box within the copy engine's rules
+        if (!tensor_map_encoder()) return false;
         size_t sm = 0;
         int thr = 32;
         for (int i = 0; i < e->count; i++) {
             const int *n = &e->n[3 * i];
             int nchunk = 1, C = n[d];
             while (C + 2 * GH > maxt) { nchunk++; C = (n[d] + nchunk - 1) / nchunk; }
-            int L = maxt / (C + 2 * GH), p2 = 1;
-            while (p2 * 2 <= L && p2 * 2 <= 16) p2 *= 2;
-            while (p2 > 1 && p2 / 2 >= n[0]) p2 /= 2;
-            const Tile t = make_tile(d, n, real_size(e), C, p2);
-            if (t.L < 2 || (t.L & 1) || t.NP > 256 || (n[0] & 1)) return false;
-            sm = std::max(sm, stage_pad_bytes(t) + t.smem);
+            int L = maxt / (C + 2 * GH);
+            if (L < 1) L = 1;
+            if (d != 0) {
+                int p2 = 1;
+                while (p2 * 2 <= L && p2 * 2 <= 16) p2 *= 2;
+                while (p2 > 1 && p2 / 2 >= n[0]) p2 /= 2;
+                L = p2;
+            }
+            const Tile t = make_tile(d, n, real_size(e), C, L);
+            if (n[0] & 1) return false;
+            if (d == 0 && ((t.C & 1) || t.NP + 2 > 256 || n[1] % t.L)) return false;   // x: even origin, one z plane
+            if (d != 0 && (t.L < 2 || (t.L & 1) || t.NP > 256)) return false;
+            sm = std::max(sm, stage_pad_bytes(t, d) + t.smem);
             thr = std::max(thr, t.threads);
         }
         if (sm > 224 * 1024 || sweep_launchers(e->prec).ens_tma_per_sm(d, thr, sm) < 1) return false;
@@ -126,7 +133,7 @@ static bool plan_direction(ppmlr_ens *e, int d, int maxt, int mode)
         Tile t = make_tile(d, n, real_size(e), C, L);
         e->tiles[d].push_back(t);
         if (t.threads > thr) thr = t.threads;
-        const size_t need = mode == 3 ? stage_pad_bytes(t) + t.smem : t.smem;
+        const size_t need = mode == 3 ? stage_pad_bytes(t, d) + t.smem : t.smem;
         if (need > sm) sm = need;
         total += t.ntiles;
     }
@@ -141,7 +148,8 @@ static bool plan_direction(ppmlr_ens *e, int d, int maxt, int mode)
 }
 
 // Tensor maps of every instance's two state sets for the TMA form along d:
-// a 4D view (x, y, z, variable) with box L lanes x NP positions x 8 arrays.
+// a 4D view (x, y, z, variable) with box L lanes x NP positions x 8 arrays
+// (x: NP + 2 cells x L pencils x 8 arrays).
 static ppmlr_status upload_maps(ppmlr_ens *e, int d)
 {
     std::vector<CUtensorMap> maps(2 * (size_t)e->count);
@@ -153,6 +161,7 @@ static ppmlr_status upload_maps(ppmlr_ens *e, int d)
         const cuuint64_t strides[3] = {(cuuint64_t)n[0] * 8, (cuuint64_t)n[0] * n[1] * 8, (cuuint64_t)vs * 8};
         cuuint32_t box[4] = {(cuuint32_t)t.L, 1, 1, 8};
         box[d] = (cuuint32_t)t.NP;
+        if (d == 0) { box[0] = (cuuint32_t)(t.NP + 2); box[1] = (cuuint32_t)t.L; }
         const cuuint32_t es[4] = {1, 1, 1, 1};
         for (int b = 0; b < 2; b++) {
             void *base = b == 0 ? e->A[8 * i] : e->B[8 * i];

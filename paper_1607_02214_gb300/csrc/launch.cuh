@@ -118,25 +118,30 @@ struct SweepVariant {
                                size_t smem, cudaStream_t s)
     {
         static bool attr[3] = {false, false, false};
-        if (dir < 1 || dir > 2) return cudaErrorInvalidValue;
+        if (dir < 0 || dir > 2) return cudaErrorInvalidValue;
         if (!attr[dir]) {
-            cudaError_t r = dir == 1 ? allow_ens_tma_smem<1>() : allow_ens_tma_smem<2>();
+            cudaError_t r = dir == 0 ? allow_ens_tma_smem<0>() : dir == 1 ? allow_ens_tma_smem<1>()
+                                                                          : allow_ens_tma_smem<2>();
             if (r != cudaSuccess) return r;
             attr[dir] = true;
         }
-        if (dir == 1) sweep_ensemble_tma_kernel<1, R, EX><<<blocks, threads, smem, s>>>(e, maps);
+        if (dir == 0) sweep_ensemble_tma_kernel<0, R, EX><<<blocks, threads, smem, s>>>(e, maps);
+        else if (dir == 1) sweep_ensemble_tma_kernel<1, R, EX><<<blocks, threads, smem, s>>>(e, maps);
         else sweep_ensemble_tma_kernel<2, R, EX><<<blocks, threads, smem, s>>>(e, maps);
         return cudaGetLastError();
     }
+    template <int DIR>
+    static int ens_tma_per_sm_dir(int threads, size_t smem)
+    {
+        if (allow_ens_tma_smem<DIR>() != cudaSuccess) return 0;
+        int n = 0;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_ensemble_tma_kernel<DIR, R, EX>, threads,
+                                                             smem) == cudaSuccess ? n : 0;
+    }
     static int ens_tma_per_sm(int dir, int threads, size_t smem)
     {
-        if (dir < 1 || dir > 2) return 0;
-        if ((dir == 1 ? allow_ens_tma_smem<1>() : allow_ens_tma_smem<2>()) != cudaSuccess) return 0;
-        int n = 0;
-        cudaError_t r = dir == 1
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_ensemble_tma_kernel<1, R, EX>, threads, smem)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_ensemble_tma_kernel<2, R, EX>, threads, smem);
-        return r == cudaSuccess ? n : 0;
+        return dir == 0 ? ens_tma_per_sm_dir<0>(threads, smem)
+               : dir == 1 ? ens_tma_per_sm_dir<1>(threads, smem) : ens_tma_per_sm_dir<2>(threads, smem);
     }
     static cudaError_t dipole_table(double M, const int n[3], const double *cx, const double *cy, const double *cz,
                                     double *bd, long long vs, cudaStream_t s)

@@ -1143,8 +1143,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_grid_kern
     sweep_tile<DIR, R, EX, const SweepArgs>(args, t - __ldg(e.first_tile + lo), smem_raw, e.flip);
 }
 
-// Ensemble, one block per tile of a y or z sweep with the tile's input box
-// staged by TMA: the block finds its instance, copies its arguments to shared
+// Ensemble, one block per tile with the tile's input box staged by TMA: the block finds its instance, copies its arguments to shared
 // memory and loads the box through that instance's tensor map (maps[2 * i +
 // b], b = the buffer holding the input: 0 = the instance's first state set,
 // 1 = its second; the array lives in global memory, written before the
@@ -1171,7 +1170,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_tma_kerne
     }
     __syncthreads();
     const int tile = t - __ldg(e.first_tile + lo);
-    const size_t stage_bytes = (size_t)8 * args.NP * args.L * sizeof(double);
+    const size_t stage_bytes = (size_t)8 * stage_array_stride<DIR>(args.NP, args.L) * sizeof(double);
     const size_t stage_pad = (stage_bytes + 1023) / 1024 * 1024;
     double *stage = reinterpret_cast<double *>(smem_raw);
     if (threadIdx.x == 0) {

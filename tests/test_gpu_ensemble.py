@@ -111,9 +111,10 @@ def test_ensemble_tma_form_matches_the_other_forms(precision):
     probs = small_ensemble(5)
     a = ppmlr.Ensemble(probs, precision=precision)
     b = ppmlr.Ensemble(probs, precision=precision)
+    b.set_launch(0, 3, 124)                          # 2 pencils per x tile: divides every ny
     for axis in (1, 2):
-        b.set_launch(axis, 3, 256)                   # TMA-staged y/z boxes, per-instance tensor maps
-    assert b.tiles()[1] // 1000 == 3 and b.tiles()[2] // 1000 == 3
+        b.set_launch(axis, 3, 256)                   # TMA-staged boxes, per-instance tensor maps
+    assert [t // 1000 for t in b.tiles()] == [3, 3, 3]
     for i, p in enumerate(probs):
         a.set_state(i, p.U0)
         b.set_state(i, p.U0)
@@ -126,6 +127,7 @@ def test_ensemble_tma_form_matches_the_other_forms(precision):
         else:
             tol = 1e-12 if precision == ppmlr.PPMLR_FP64 else 1e-6
             assert np.max(rel_l1(b.get_state(i), a.get_state(i))) <= tol, i
-    assert b.set_launch(0, 3, 256, raise_on_error=False) == ppmlr.PPMLR_E_INVALID   # no TMA form along x
     odd = ppmlr.Ensemble([inputs.magnetosphere(n=(41, 30, 30), h0=1.0)], precision=precision)
     assert odd.set_launch(1, 3, 256, raise_on_error=False) == ppmlr.PPMLR_E_INVALID  # nx odd
+    skew = ppmlr.Ensemble([inputs.magnetosphere(n=(40, 30, 30), h0=1.0)], precision=precision)
+    assert skew.set_launch(0, 3, 216, raise_on_error=False) == ppmlr.PPMLR_E_INVALID  # 4 lanes do not divide ny
