@@ -65,6 +65,7 @@ def lib():
         L.orc_riemann.argtypes = [_dp, _dp, ctypes.c_double, ctypes.c_double, _dp]
         L.orc_riemann_nl.argtypes = [_dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp]
         L.orc_set_riemann.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_set_steepening.argtypes = [ctypes.c_void_p, ctypes.c_int]
         _lib = L
     return _lib
 
@@ -147,6 +148,10 @@ class Oracle:
     @step_count.setter
     def step_count(self, s):
         lib().orc_set_step_count(self._h, int(s))
+
+    def set_steepening(self, on):
+        """Contact steepening of the remapped densities (Colella & Woodward 1984)."""
+        lib().orc_set_steepening(self._h, int(bool(on)))
 
     def set_riemann(self, iters):
         """0: two-wave Riemann solver; k > 0: k two-shock Newton steps on the

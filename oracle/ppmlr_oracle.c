@@ -52,6 +52,8 @@ enum { FLAG_CFL = 1, FLAG_NONFINITE = 2 };
 
 /* Flattening constants of Colella & Woodward (1984), Appendix A. */
 static const double FLAT_EPS = 0.33, FLAT_W1 = 0.75, FLAT_W2 = 10.0;
+/* Contact-steepening constants of Colella & Woodward (1984), Sec. 1. */
+static const double ST_ETA1 = 20.0, ST_ETA2 = 0.05, ST_EPS = 0.01, ST_K0 = 0.1;
 
 typedef struct {
     int n[3];
@@ -66,6 +68,7 @@ typedef struct {
     double p_min;
     int powell;
     int riemann_iters;       /* 0: two-wave Riemann solver; k > 0: k two-shock Newton steps */
+    int steepen;             /* 1: contact steepening in the remap */
     double *U;               /* [8][nz][ny][nx], x fastest */
     double *Unew;
     long long floors;
@@ -339,6 +342,7 @@ long long orc_floor_hits(const orc_ctx *c) { return c->floors; }
 long long orc_step_count(const orc_ctx *c) { return c->steps; }
 void orc_set_step_count(orc_ctx *c, long long s) { c->steps = s; }
 void orc_set_riemann(orc_ctx *c, int iters) { c->riemann_iters = iters > 0 ? iters : 0; }
+void orc_set_steepening(orc_ctx *c, int on) { c->steepen = on ? 1 : 0; }
 
 int orc_set_threads(int t)
 {
@@ -390,13 +394,16 @@ typedef struct {
     double *Bnf;
     double *dxL, *rq[NREC], *dC[NREC];  /* Lagrangian width, remap densities, content increments */
     double *F[NREC];                    /* remap flux through Eulerian edge i+1/2 */
+    double *slq[NREC], *d2, *eta;       /* contact steepening: limited slopes of the remap densities,
+                                           second differences of rho^L, weights */
     double *tmp;
 } pencil_buf;
 
 static void pb_alloc(pencil_buf *b, int NP)
 {
     size_t s = sizeof(double) * (size_t)NP;
-    double **all[] = {&b->dx, &b->pos, &b->Bn, &b->Pt, &b->W, &b->ft, &b->f, &b->Bnf, &b->dxL, &b->tmp};
+    double **all[] = {&b->dx, &b->pos, &b->Bn, &b->Pt, &b->W, &b->ft, &b->f, &b->Bnf, &b->dxL, &b->tmp,
+                      &b->d2, &b->eta};
     for (size_t k = 0; k < sizeof(all) / sizeof(all[0]); k++) *all[k] = (double *)malloc(s);
     for (int v = 0; v < NVAR; v++) b->U[v] = (double *)malloc(s);
     for (int v = 0; v < 3; v++) b->Bd[v] = (double *)malloc(s);
@@ -406,12 +413,13 @@ static void pb_alloc(pencil_buf *b, int NP)
         b->q[v] = (double *)malloc(s); b->edge[v] = (double *)malloc(s);
         b->aL[v] = (double *)malloc(s); b->aR[v] = (double *)malloc(s); b->a6[v] = (double *)malloc(s);
         b->rq[v] = (double *)malloc(s); b->dC[v] = (double *)malloc(s); b->F[v] = (double *)malloc(s);
+        b->slq[v] = (double *)malloc(s);
     }
 }
 
 static void pb_free(pencil_buf *b)
 {
-    double *all[] = {b->dx, b->pos, b->Bn, b->Pt, b->W, b->ft, b->f, b->Bnf, b->dxL, b->tmp};
+    double *all[] = {b->dx, b->pos, b->Bn, b->Pt, b->W, b->ft, b->f, b->Bnf, b->dxL, b->tmp, b->d2, b->eta};
     for (size_t k = 0; k < sizeof(all) / sizeof(all[0]); k++) free(all[k]);
     for (int v = 0; v < NVAR; v++) free(b->U[v]);
     for (int v = 0; v < 3; v++) free(b->Bd[v]);
@@ -419,7 +427,7 @@ static void pb_free(pencil_buf *b)
     for (int v = 0; v < NTR; v++) { free(b->sl[v]); free(b->sr[v]); }
     for (int v = 0; v < NREC; v++) {
         free(b->q[v]); free(b->edge[v]); free(b->aL[v]); free(b->aR[v]); free(b->a6[v]);
-        free(b->rq[v]); free(b->dC[v]); free(b->F[v]);
+        free(b->rq[v]); free(b->dC[v]); free(b->F[v]); free(b->slq[v]);
     }
 }
 
@@ -589,9 +597,50 @@ static void sweep_pencil(orc_ctx *c, int d, int j, int k, double dt, pencil_buf 
         int n4 = NP - 8;
         orc_ppm_edges(n4, b->dxL + 4, b->rq[v] + 4, 1, b->edge[v] + 4);
     }
+    /* contact steepening (option) [R: Colella & Woodward (1984), Sec. 1,
+     * applied in the remap, where contacts move across the fixed grid].  The
+     * weight eta of zone p comes from the Lagrangian density on the Lagrangian
+     * widths: its second differences d2 must change sign across the zone, its
+     * jump exceed ST_EPS of the smaller neighbour, and the zone must not sit
+     * in a shock (total-pressure jump of the sweep input, relative, times
+     * gamma ST_K0, at least the relative density jump).  The same eta blends
+     * the parabola ends of all seven densities towards the one-sided values
+     * a_{p-1} + slope_{p-1}/2 and a_{p+1} - slope_{p+1}/2, so that quantities
+     * that are affine in the density across a contact stay consistent. */
+    if (c->steepen) {
+        for (int v = 0; v < NREC; v++)
+            for (int p = 5; p <= NP - 6; p++)
+                b->slq[v][p] = ppm_limit(b->rq[v] + 4, p - 4, ppm_slope(b->dxL + 4, b->rq[v] + 4, p - 4));
+        const double *r = b->rq[0], *w = b->dxL;
+        for (int p = 5; p <= NP - 6; p++)
+            b->d2[p] = ((r[p + 1] - r[p]) / (w[p + 1] + w[p]) - (r[p] - r[p - 1]) / (w[p] + w[p - 1])) /
+                       (w[p - 1] + w[p] + w[p + 1]);
+        for (int p = 6; p <= NP - 7; p++) {
+            double eta = 0.0;
+            double dr = r[p + 1] - r[p - 1];
+            double rmin = fabs(r[p + 1]) < fabs(r[p - 1]) ? fabs(r[p + 1]) : fabs(r[p - 1]);
+            double Pp = b->Pt[p + 1], Pm = b->Pt[p - 1], rp = b->q[0][p + 1], rm = b->q[0][p - 1];
+            int shock = gam * ST_K0 * fabs(Pp - Pm) / (Pp < Pm ? Pp : Pm) >= fabs(rp - rm) / (rp < rm ? rp : rm);
+            if (b->d2[p + 1] * b->d2[p - 1] < 0.0 && fabs(dr) - ST_EPS * rmin > 0.0 && !shock) {
+                double xl = 0.5 * (w[p - 1] + w[p]), xr = 0.5 * (w[p] + w[p + 1]);
+                double et = -(b->d2[p + 1] - b->d2[p - 1]) / dr * (xl * xl * xl + xr * xr * xr) / (xl + xr);
+                eta = ST_ETA1 * (et - ST_ETA2);
+                if (eta < 0.0) eta = 0.0;
+                if (eta > 1.0) eta = 1.0;
+            }
+            b->eta[p] = eta;
+        }
+    }
     for (int p = 6; p <= NP - 7; p++) {
         for (int v = 0; v < NREC; v++) {
             double l = b->edge[v][p - 1], r = b->edge[v][p], a6;
+            if (c->steepen && b->eta[p] > 0.0) {
+                double eta = b->eta[p];
+                double ld = b->rq[v][p - 1] + 0.5 * b->slq[v][p - 1];
+                double rd = b->rq[v][p + 1] - 0.5 * b->slq[v][p + 1];
+                l = l * (1.0 - eta) + eta * ld;
+                r = r * (1.0 - eta) + eta * rd;
+            }
             ppm_monotone(b->rq[v][p], &l, &r, &a6);
             b->aL[v][p] = l; b->aR[v][p] = r; b->a6[v][p] = a6;
         }

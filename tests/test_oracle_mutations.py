@@ -47,9 +47,14 @@ MUTANTS = {
     "two_shock_slope": ("double ZL = 2.0 * WLk * WLk * WLk / (WLk * WLk + CL * CL);", "double ZL = WLk;"),
     "two_shock_curve_sign": ("double uRk = R[1] + (Pc - PR) / WRk;", "double uRk = R[1] - (Pc - PR) / WRk;"),
     "two_shock_final_speed": ("WR = CR * sqrt(1.0 + a * (Pc / PR - 1.0));\n    }", "WR = CR;\n    }"),
+    "steepen_one_sided_right": ("double rd = b->rq[v][p + 1] - 0.5 * b->slq[v][p + 1];",
+                                "double rd = b->rq[v][p + 1] + 0.5 * b->slq[v][p + 1];"),
+    "steepen_density_only": ("if (c->steepen && b->eta[p] > 0.0) {", "if (c->steepen && b->eta[p] > 0.0 && v == 0) {"),
+    "steepen_curvature_test": ("if (b->d2[p + 1] * b->d2[p - 1] < 0.0 &&", "if (b->d2[p + 1] * b->d2[p - 1] > 0.0 &&"),
 }
 
 PINS = ["tests/test_oracle_ppm.py", "tests/test_oracle_riemann.py", "tests/test_oracle_riemann_nl.py",
+        "tests/test_oracle_steepening.py",
         "tests/test_oracle_sources.py",
         "tests/test_oracle_scheme.py", "tests/test_golden.py"]
 
