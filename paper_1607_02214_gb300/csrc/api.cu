@@ -55,6 +55,7 @@ struct ppmlr_ctx {
     // plus the explicit dt of ppmlr_step, summed on the host
     double t_host;
     int riemann_iters;              // 0: two-wave Riemann solver; k > 0: k two-shock Newton steps
+    int steepen;                    // 1: contact steepening in the remap
     std::vector<double> edges[3];   // host copies of the grid edges (checkpoint validation)
     // graph replay of ppmlr_run: one executable graph per starting step
     // parity, input buffer, length and CFL number; dropped when the tiles or
@@ -322,6 +323,7 @@ ppmlr_status ppmlr_create(const ppmlr_grid *grid, double gamma, const ppmlr_bc *
     c->timing = false;
     c->t_host = 0.0;
     c->riemann_iters = 0;
+    c->steepen = 0;
     c->cap = nullptr;
     for (int d = 0; d < 3; d++) c->edges[d].assign(grid->edges[d], grid->edges[d] + grid->n[d] + 1);
     if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return PPMLR_E_CUDA; }
@@ -527,6 +529,7 @@ static ppmlr_status launch_one_sweep(ppmlr_ctx *c, int d, double dt, const doubl
     a.powell = c->bc.powell ? 1 : 0;
     a.do_src = (a.M != 0.0 || a.powell) ? 1 : 0;
     a.riemann_iters = c->riemann_iters;
+    a.steepen = c->steepen;
     a.dt = dt; a.dt_dev = dt_dev;
     a.bd = c->bd;
     if (c->prec != PPMLR_MIXED) { a.iw = c->iw[d]; a.ih = c->ih[d]; }
@@ -775,6 +778,14 @@ ppmlr_status ppmlr_set_riemann_solver(ppmlr_ctx *c, int iters)
     if (!c) return PPMLR_E_INVALID;
     if (iters < 0 || iters > 16) return fail(c, PPMLR_E_INVALID, "set_riemann_solver: iters must be in [0, 16]");
     c->riemann_iters = iters;
+    drop_graphs(c);
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_set_steepening(ppmlr_ctx *c, int on)
+{
+    if (!c) return PPMLR_E_INVALID;
+    c->steepen = on ? 1 : 0;
     drop_graphs(c);
     return PPMLR_OK;
 }

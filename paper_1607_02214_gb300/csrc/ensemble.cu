@@ -31,6 +31,7 @@ struct ppmlr_ens {
     std::vector<long long> ncell;
     std::vector<ppmlr_bc> bc;
     int riemann_iters;           // 0: two-wave Riemann solver; k > 0: k two-shock Newton steps
+    int steepen;                 // 1: contact steepening in the remap
     double *state;               // all instances, A and B sets
     std::vector<double *> A, B;  // 8 per instance
     double *geo;                 // per instance: w[3], c[3] (double)
@@ -211,6 +212,7 @@ static ppmlr_status upload_direction(ppmlr_ens *e, int d)
         a.powell = b.powell ? 1 : 0;
         a.do_src = (a.M != 0.0 || a.powell) ? 1 : 0;
         a.riemann_iters = e->riemann_iters;
+        a.steepen = e->steepen;
         a.dt = 0.0; a.dt_dev = e->dt + i;
         a.flags = e->flags; a.floors = e->floors;
         a.gammaf = (float)a.gamma; a.p_minf = (float)a.p_min; a.Mf = (float)a.M; a.r_innerf = (float)a.r_inner;
@@ -676,6 +678,18 @@ ppmlr_status ppmlr_ensemble_set_launch(ppmlr_ens *e, int axis, int form, int bud
         return efail(e, PPMLR_E_INVALID, "set_launch: the TMA form does not fit every instance along this axis");
     ppmlr_status st = upload_direction(e, axis);
     if (st != PPMLR_OK) return st;
+    drop_graphs(e);
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_ensemble_set_steepening(ppmlr_ens *e, int on)
+{
+    if (!e) return PPMLR_E_INVALID;
+    e->steepen = on ? 1 : 0;
+    for (int d = 0; d < 3; d++) {
+        ppmlr_status st = upload_direction(e, d);
+        if (st != PPMLR_OK) return st;
+    }
     drop_graphs(e);
     return PPMLR_OK;
 }

@@ -40,6 +40,7 @@ struct SweepArgs {
     double inner[8];           // rho, vx, vy, vz, -, -, -, p
     int powell, do_src;
     int riemann_iters;         // 0: two-wave Riemann solver; k > 0: k two-shock Newton steps
+    int steepen;               // 1: contact steepening of the remapped densities
     double dt;                 // used when dt_dev == nullptr
     const double *dt_dev;
     const double *bd;          // FP64 forms: dipole table (component k at bd + k * vs + cell) or null

@@ -352,12 +352,21 @@ __device__ __forceinline__ R edge_value(const EdgeCoef<R> &k, R a0, R a1, R dmi,
 //  P6 reads C, writes B (7 Lagrangian densities, Lagrangian width);
 //  P7 reads B, writes A[0..6] (7 remap slopes);
 //  P8 reads A, B, writes C (7 remap interface values);
-//  P9 reads C, writes B[0..6] (remap flux through each Eulerian edge);
-//  P10 reads B and writes the new state.
+//  P9 reads C (and, steepening, A[0..6] and B of the neighbours), writes the
+//     remap flux through each Eulerian edge (flux_slot);
+//  P10 reads the fluxes and writes the new state.
 enum : int {
     A_RHO = 0, A_U, A_V1, A_V2, A_B1, A_B2, A_P, A_DM, A_PT, A_BN, A_AX, A_AY, A_AZ,
     SB0 = 13, SC0 = 21
 };
+// P7 -> P8: second differences of the Lagrangian density (contact steepening)
+// in the pad value NSM; P9 -> P10: the remap fluxes in values that are free
+// by then (A_DM .. A_AZ and the pad), so that P9 can still read its
+// neighbours' remap densities and slopes.
+__device__ __forceinline__ constexpr int flux_slot(int v) { return v < 6 ? A_DM + v : NSM; }
+
+// Contact-steepening constants (Colella & Woodward 1984, Sec. 1).
+constexpr double ST_ETA1 = 20.0, ST_ETA2 = 0.05, ST_EPS = 0.01, ST_K0 = 0.1;
 
 // Layout of a tile's input box staged in shared memory (8 arrays).  y/z
 // sweeps: NP positions x L lanes in slot order (position-major, lanes
@@ -644,6 +653,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     // ---------------- P3: interface values, flattening coefficient ----------------
     R edg[7];
     R flat = 0;
+    bool shock_k = false;      // contact steepening: this zone sits in a shock
     if (act && p >= 1 && p <= NPe - 3) {
         EdgeCoef<R> k = edge_coef<R, EX>(SM(A_DM, s - PS), dm, SM(A_DM, s + PS), SM(A_DM, s + 2 * PS));
         const R own[7] = {rho, u, v1, v2, B1, B2, pr};
@@ -656,6 +666,10 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             R up = SM(A_PT, s + PS) - SM(A_PT, s - PS) < R(0) ? SM(SB0 + 7, s + PS) : SM(SB0 + 7, s - PS);
             R ft = SM(SB0 + 7, s);
             flat = ft > up ? ft : up;
+        }
+        if (a.steepen) {   // shock exclusion of contact steepening: relative total-pressure jump vs density jump
+            const R Pp = SM(A_PT, s + PS), Pm = SM(A_PT, s - PS), rp = SM(A_RHO, s + PS), rm = SM(A_RHO, s - PS);
+            shock_k = gam * R(ST_K0) * K<R>::ab(Pp - Pm) / (Pp < Pm ? Pp : Pm) >= K<R>::ab(rp - rm) / (rp < rm ? rp : rm);
         }
     }
     __syncthreads();
@@ -811,17 +825,37 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             rmv[v] = limit_slope<R, EX>(SM(SB0 + v, s - PS), qL[v], SM(SB0 + v, s + PS), k.c1, k.c2, k.c3);
             SM(v, s) = rmv[v];
         }
+        if (a.steepen) {   // second difference of the Lagrangian density on the Lagrangian widths
+            const R rl = SM(SB0, s - PS), rr = SM(SB0, s + PS), wl = SM(SB0 + 7, s - PS), wr = SM(SB0 + 7, s + PS);
+            SM(NSM, s) = ((rr - qL[0]) / (wr + dxL) - (qL[0] - rl) / (dxL + wl)) / (wl + dxL + wr);
+        }
     }
     __syncthreads();
 
     // ---------------- P8: remap interface values ----------------
     R red[7];
+    R eta_k = 0;               // contact-steepening weight of this zone
     if (act && p >= 5 && p <= NPe - 7) {
         EdgeCoef<R> k = edge_coef<R, EX>(SM(SB0 + 7, s - PS), dxL, SM(SB0 + 7, s + PS), SM(SB0 + 7, s + 2 * PS));
 #pragma unroll
         for (int v = 0; v < 7; v++) {
             red[v] = edge_value<R>(k, qL[v], SM(SB0 + v, s + PS), rmv[v], SM(v, s + PS));
             SM(SC0 + v, s) = red[v];
+        }
+        if (a.steepen && p >= 6 && !shock_k) {   // contact weight of this zone
+            const R dp2 = SM(NSM, s + PS), dm2 = SM(NSM, s - PS);
+            const R rr = SM(SB0, s + PS), rl = SM(SB0, s - PS);
+            const R dr = rr - rl;
+            const R rmin = K<R>::ab(rr) < K<R>::ab(rl) ? K<R>::ab(rr) : K<R>::ab(rl);
+            if (dp2 * dm2 < R(0) && K<R>::ab(dr) - R(ST_EPS) * rmin > R(0)) {
+                const R wl = SM(SB0 + 7, s - PS), wr = SM(SB0 + 7, s + PS);
+                const R xl = R(0.5) * (wl + dxL), xr = R(0.5) * (dxL + wr);
+                const R et = -(dp2 - dm2) / dr * (xl * xl * xl + xr * xr * xr) / (xl + xr);
+                R e = R(ST_ETA1) * (et - R(ST_ETA2));
+                if (e < R(0)) e = R(0);
+                if (e > R(1)) e = R(1);
+                eta_k = e;
+            }
         }
     }
     __syncthreads();
@@ -833,6 +867,12 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         for (int v = 0; v < 7; v++) {
             pl[v] = SM(SC0 + v, s - PS);
             pr_[v] = red[v];
+            if (eta_k > R(0)) {   // steepened ends: towards the neighbours' one-sided values
+                const R ld = SM(SB0 + v, s - PS) + R(0.5) * SM(v, s - PS);
+                const R rd = SM(SB0 + v, s + PS) - R(0.5) * SM(v, s + PS);
+                pl[v] = pl[v] * (R(1) - eta_k) + eta_k * ld;
+                pr_[v] = pr_[v] * (R(1) - eta_k) + eta_k * rd;
+            }
             p6[v] = monotone<R, EX>(qL[v], pl[v], pr_[v]);
         }
         if (p <= NPe - 8) {                       // edge p+1/2: donor is this zone when del >= 0
@@ -840,17 +880,17 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
                 R y = EX ? del_p / dxL : del_p * idxL_k;
                 if (!gt0<R, EX>(R(1) - y)) atomicOr(a.flags, FLAG_CFL);
 #pragma unroll
-                for (int v = 0; v < 7; v++) SM(SB0 + v, s) = del_p * avg_right<R>(pl[v], pr_[v], p6[v], y);
+                for (int v = 0; v < 7; v++) SM(flux_slot(v), s) = del_p * avg_right<R>(pl[v], pr_[v], p6[v], y);
             } else if (!lt0<R, EX>(del_p)) {
 #pragma unroll
-                for (int v = 0; v < 7; v++) SM(SB0 + v, s) = R(0);
+                for (int v = 0; v < 7; v++) SM(flux_slot(v), s) = R(0);
             }
         }
         if (p >= 7 && lt0<R, EX>(del_m)) {       // edge p-1/2: donor is this zone when del < 0
             R y = EX ? -del_m / dxL : -del_m * idxL_k;
             if (!gt0<R, EX>(R(1) - y)) atomicOr(a.flags, FLAG_CFL);
 #pragma unroll
-            for (int v = 0; v < 7; v++) SM(SB0 + v, s - PS) = del_m * avg_left<R>(pl[v], pr_[v], p6[v], y);
+            for (int v = 0; v < 7; v++) SM(flux_slot(v), s - PS) = del_m * avg_left<R>(pl[v], pr_[v], p6[v], y);
         }
     }
     __syncthreads();
@@ -874,8 +914,8 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
 #pragma unroll
             for (int v = 0; v < 7; v++) {
                 double dU;
-                if constexpr (EX) dU = (dCv[v] + SM(SB0 + v, s - PS) - SM(SB0 + v, s)) / dx;
-                else dU = (dCv[v] + SM(SB0 + v, s - PS) - SM(SB0 + v, s)) * idx;
+                if constexpr (EX) dU = (dCv[v] + SM(flux_slot(v), s - PS) - SM(flux_slot(v), s)) / dx;
+                else dU = (dCv[v] + SM(flux_slot(v), s - PS) - SM(flux_slot(v), s)) * idx;
                 Un[cmap[v]] = Un[cmap[v]] + dU;
             }
             if (a.do_src) {
@@ -891,7 +931,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             const R idx = R(1) / a.wf[g + GH];
             R dU[8];
 #pragma unroll
-            for (int v = 0; v < 7; v++) dU[cmap[v]] = (dCv[v] + SM(SB0 + v, s - PS) - SM(SB0 + v, s)) * idx;
+            for (int v = 0; v < 7; v++) dU[cmap[v]] = (dCv[v] + SM(flux_slot(v), s - PS) - SM(flux_slot(v), s)) * idx;
             dU[4 + DIR] = R(0);
             if (a.do_src) {
                 dU[1 + DIR] += dtr * src_m[0]; dU[1 + T1] += dtr * src_m[1]; dU[1 + T2] += dtr * src_m[2];

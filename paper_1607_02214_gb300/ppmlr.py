@@ -64,6 +64,8 @@ SIGNATURES = [
     ("ppmlr_set_tiles", c_int, [c_void_p, c_int, c_int, c_int]),
     ("ppmlr_run", c_int, [c_void_p, c_double, c_longlong, c_int]),
     ("ppmlr_set_riemann_solver", c_int, [c_void_p, c_int]),
+    ("ppmlr_set_steepening", c_int, [c_void_p, c_int]),
+    ("ppmlr_ensemble_set_steepening", c_int, [c_void_p, c_int]),
     ("ppmlr_get_time", c_int, [c_void_p, POINTER(c_double)]),
     ("ppmlr_set_time", c_int, [c_void_p, c_double]),
     ("ppmlr_checkpoint_save", c_int, [c_void_p, ctypes.c_char_p]),
@@ -274,6 +276,10 @@ class Context:
         fast mode (nonlinear variant)."""
         return self._check(load().ppmlr_set_riemann_solver(self._h, int(iters)))
 
+    def set_steepening(self, on):
+        """Contact steepening of the remapped densities (default off)."""
+        return self._check(load().ppmlr_set_steepening(self._h, int(bool(on))))
+
     def run(self, cfl, nsteps, graph_steps=16):
         """nsteps device-dt steps (as step_cfl), replayed from CUDA graphs of
         graph_steps steps (0: direct launches)."""
@@ -431,6 +437,10 @@ class Ensemble:
     def set_riemann_solver(self, iters):
         """0: two-wave Riemann solver; k > 0: k two-shock Newton steps."""
         return self._check(load().ppmlr_ensemble_set_riemann_solver(self._h, int(iters)))
+
+    def set_steepening(self, on):
+        """Contact steepening of every instance's remap (default off)."""
+        return self._check(load().ppmlr_ensemble_set_steepening(self._h, int(bool(on))))
 
     def set_launch(self, axis, form, budget, raise_on_error=True):
         """Fix one direction's launch form (0..3) and tile budget."""
