@@ -286,10 +286,11 @@ def run_ours(args, rank, world, dist):
     def max_ranks(x):
         return max_over_ranks(x, dist, "cuda")
 
-    def timed_run(precision, steps, warmup, with_clocks=False, riemann_iters=0):
+    def timed_run(precision, steps, warmup, with_clocks=False, riemann_iters=0, steepen=False):
         ctx = ppmlr.Context.from_problem(prob, precision)
         ctx.set_state(U0)
         ctx.set_riemann_solver(riemann_iters)
+        ctx.set_steepening(steepen)
         if args.launch_config and precision == prec:
             for axis, (C, L, form) in enumerate(args.launch_config):
                 ctx.set_tiles(axis, C, L)
@@ -416,6 +417,14 @@ def run_ours(args, rank, world, dist):
             nl[key] = {"value": world * cells * nsteps / (nms * 1e-3), "ms_per_step": nms / nsteps}
             nctx.close()
         extra["riemann_two_shock"] = nl
+        st = {}
+        for key, p in (("fp64", ppmlr.PPMLR_FP64), ("mixed", ppmlr.PPMLR_MIXED)):
+            nsteps = max(3, args.steps // 4) if key == "fp64" else args.steps
+            sctx, sms, _, _, _ = timed_run(p, nsteps, args.warmup, steepen=True)
+            sms = max_ranks(sms)
+            st[key] = {"value": world * cells * nsteps / (sms * 1e-3), "ms_per_step": sms / nsteps}
+            sctx.close()
+        extra["contact_steepening"] = st
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
