@@ -40,7 +40,8 @@ typedef enum {
     PPMLR_E_OOM = 3,        /* device allocation failed */
     PPMLR_E_NONFINITE = 4,  /* a sweep produced a non-finite conserved value */
     PPMLR_E_CFL = 5,        /* dt too large: a Lagrangian width <= 0 or a remap sliver >= one zone */
-    PPMLR_E_TIMEOUT = 6     /* a bounded device wait (TMA copy completion) gave up */
+    PPMLR_E_TIMEOUT = 6,    /* a bounded device wait (TMA copy completion) gave up */
+    PPMLR_E_BOUNDS = 7      /* checked build (-DPPMLR_CHECK) only: a kernel index left its array */
 } ppmlr_status;
 
 typedef enum {

@@ -38,17 +38,23 @@ def _sources():
         [os.path.join(HERE, "..", "include", "ppmlr.h")]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+# bounds-checked build (-DPPMLR_CHECK): every kernel index of the sweeps is
+# tested against its array; for the tests, not for timing
+LIB_CHECK = os.path.join(HERE, "libppmlr_gb300_check.so")
+OUT_CHECK = os.path.join(HERE, "_build_check")
+
+
+def up_to_date(lib=LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(s) <= t for s in _sources())
 
 
-def _compile(unit, verbose):
+def _compile(unit, verbose, check=False):
     src = os.path.join(CSRC, unit)
-    obj = os.path.join(OUT, unit.replace(".cu", ".o"))
-    cmd = [NVCC, *COMMON, *UNITS[unit], "-c", src, "-o", obj]
+    obj = os.path.join(OUT_CHECK if check else OUT, unit.replace(".cu", ".o"))
+    cmd = [NVCC, *COMMON, *UNITS[unit], *(["-DPPMLR_CHECK"] if check else []), "-c", src, "-o", obj]
     if verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -57,23 +63,26 @@ def _compile(unit, verbose):
     return obj, r.stderr
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, check: bool = False) -> str:
+    """Build the library (check=True: the bounds-checked variant, a separate
+    file); returns its path."""
+    lib = LIB_CHECK if check else LIB
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(OUT_CHECK if check else OUT, exist_ok=True)
     with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
-        results = list(ex.map(lambda u: _compile(u, verbose), UNITS))
+        results = list(ex.map(lambda u: _compile(u, verbose, check), UNITS))
     if verbose:
         for _, log in results:
             sys.stderr.write(log)
     objs = [o for o, _ in results]
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     r = subprocess.run([NVCC, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, check="--check" in sys.argv))

@@ -480,6 +480,7 @@ static ppmlr_status read_flags(ppmlr_ctx *c)
     CK(c, cudaStreamSynchronize(c->stream), "stream sync");
     if (f) {
         CK(c, cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream), "flags reset");
+        if (f & FLAG_BOUNDS) return fail(c, PPMLR_E_BOUNDS, "checked build: a kernel index left its array");
         if (f & FLAG_TIMEOUT) return fail(c, PPMLR_E_TIMEOUT, "a bounded device wait gave up");
         if (f & FLAG_NONFINITE) return fail(c, PPMLR_E_NONFINITE, "a sweep produced a non-finite state");
         return fail(c, PPMLR_E_CFL, "time step too large for the CFL condition");

@@ -487,6 +487,8 @@ static ppmlr_status ens_flags(ppmlr_ens *e)
     ECK(e, cudaStreamSynchronize(e->stream), "stream sync");
     if (f) {
         ECK(e, cudaMemsetAsync(e->flags, 0, sizeof(int), e->stream), "flags reset");
+        if (f & FLAG_BOUNDS) return efail(e, PPMLR_E_BOUNDS, "checked build: a kernel index left its array");
+        if (f & FLAG_TIMEOUT) return efail(e, PPMLR_E_TIMEOUT, "a bounded device wait gave up");
         if (f & FLAG_NONFINITE) return efail(e, PPMLR_E_NONFINITE, "a sweep produced a non-finite state");
         return efail(e, PPMLR_E_CFL, "time step too large for the CFL condition");
     }

@@ -17,7 +17,7 @@ constexpr int NSMP = 29;       // slot pitch in values: odd, so consecutive slot
 constexpr int MAXT = 512;      // threads per tile (one thread per cell position and lane), mixed path
 constexpr int MAXT_F64 = 448;  // FP64 path: fewer threads, up to 146 registers each
 
-enum : int { FLAG_CFL = 1, FLAG_NONFINITE = 2, FLAG_TIMEOUT = 4 };
+enum : int { FLAG_CFL = 1, FLAG_NONFINITE = 2, FLAG_TIMEOUT = 4, FLAG_BOUNDS = 8 };
 
 // Arguments of one sweep launch (passed by value).
 struct SweepArgs {

@@ -31,6 +31,17 @@
 
 namespace ppmlr {
 
+// Checked build (-DPPMLR_CHECK): every shared-memory, staged-box, geometry and
+// state index of the tile body is tested against the extent of its array; an
+// out-of-range index raises FLAG_BOUNDS (status PPMLR_E_BOUNDS) and the access
+// goes to element 0 of the same array instead.  The plain build compiles the
+// bare index.
+#ifdef PPMLR_CHECK
+#define CHK(i, n) ((i) >= 0 && (i) < (n) ? (i) : (atomicOr(a.flags, FLAG_BOUNDS), 0))
+#else
+#define CHK(i, n) (i)
+#endif
+
 template <typename R> struct K;
 template <> struct K<double> {
     static __device__ __forceinline__ double sq(double x) { return sqrt(x); }
@@ -409,7 +420,12 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     const int L = L_, NP = NP_, NT = NP * L;
     const int PS = DIR == 0 ? 1 : L;
     const int s = threadIdx.x;
-#define SM(k, slot) sm[(slot) * NSMP + (k)]
+    // extents for the checked build: cells of the domain, ghost-extended
+    // positions along the sweep axis and across it
+    const long long NCELL = (long long)a.n[0] * a.n[1] * a.n[2];
+    const int NG = a.N + 2 * GH, NG0 = a.n[0] + 2 * GH, NG1 = a.n[1] + 2 * GH, NG2 = a.n[2] + 2 * GH;
+    (void)NCELL; (void)NG; (void)NG0; (void)NG1; (void)NG2;
+#define SM(k, slot) sm[CHK((slot) * NSMP + (k), NT * NSMP)]
 
     // ---- tile decode ----
     const int chunk = tile % a.nchunk;
@@ -453,15 +469,15 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     bool floored = false;
     const bool out_cell = act && p >= GH && p < GH + Ce;
     if (act && F64) {
-        dx = a.w[g + GH];
-        pos[0] = a.cx[(DIR == 0 ? g : ix) + GH];
-        pos[1] = a.cy[(DIR == 1 ? g : iy) + GH];
-        pos[2] = a.cz[(DIR == 2 ? g : iz) + GH];
+        dx = a.w[CHK(g + GH, NG)];
+        pos[0] = a.cx[CHK((DIR == 0 ? g : ix) + GH, NG0)];
+        pos[1] = a.cy[CHK((DIR == 1 ? g : iy) + GH, NG1)];
+        pos[2] = a.cz[CHK((DIR == 2 ? g : iz) + GH, NG2)];
         if (a.bd && g >= 0 && g < a.N) {      // interior cell: the dipole table
             const long long gi = base + (long long)g * stride;
-            Bdg[0] = __ldg(a.bd + gi);
-            Bdg[1] = __ldg(a.bd + a.vs + gi);
-            Bdg[2] = __ldg(a.bd + 2 * a.vs + gi);
+            Bdg[0] = __ldg(a.bd + CHK(gi, NCELL));
+            Bdg[1] = __ldg(a.bd + a.vs + CHK(gi, NCELL));
+            Bdg[2] = __ldg(a.bd + 2 * a.vs + CHK(gi, NCELL));
         } else {
             dipole<EX>(a.M, pos[0], pos[1], pos[2], Bdg);
         }
@@ -489,11 +505,11 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             if (stage && ps >= 0 && ps < NP) {
                 const int slot = stage_index<DIR>(l, ps, NP, L), sv = stage_array_stride<DIR>(NP, L);
 #pragma unroll
-                for (int v = 0; v < 8; v++) Uc[v] = stage[v * sv + slot];
+                for (int v = 0; v < 8; v++) Uc[v] = stage[CHK(v * sv + slot, 8 * sv)];
             } else {
                 const long long gi = base + (long long)src * stride;
 #pragma unroll
-                for (int v = 0; v < 8; v++) Uc[v] = __ldg(Uin + v * vs + gi);
+                for (int v = 0; v < 8; v++) Uc[v] = __ldg(Uin + v * vs + CHK(gi, NCELL));
             }
         }
         double rd = Uc[0];
@@ -520,10 +536,10 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     } else if (act) {
         // mixed path: float geometry, float dipole, integer double->float
         // splits and a double-float pressure recovery (no FP64 instructions)
-        const float dxf = a.wf[g + GH];
-        const float px = a.cxf[(DIR == 0 ? g : ix) + GH];
-        const float py = a.cyf[(DIR == 1 ? g : iy) + GH];
-        const float pz = a.czf[(DIR == 2 ? g : iz) + GH];
+        const float dxf = a.wf[CHK(g + GH, NG)];
+        const float px = a.cxf[CHK((DIR == 0 ? g : ix) + GH, NG0)];
+        const float py = a.cyf[CHK((DIR == 1 ? g : iy) + GH, NG1)];
+        const float pz = a.czf[CHK((DIR == 2 ? g : iz) + GH, NG2)];
         float Bdf[3];
         dipole_f(a.Mf, px, py, pz, Bdf);
         Bd0 = Bdf[DIR]; Bd1 = Bdf[T1]; Bd2 = Bdf[T2];
@@ -549,11 +565,11 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             if (stage && ps >= 0 && ps < NP) {
                 const int slot = stage_index<DIR>(l, ps, NP, L), sv = stage_array_stride<DIR>(NP, L);
 #pragma unroll
-                for (int v = 0; v < 8; v++) q[v] = split_double(stage[v * sv + slot]);
+                for (int v = 0; v < 8; v++) q[v] = split_double(stage[CHK(v * sv + slot, 8 * sv)]);
             } else {
                 const long long gi = base + (long long)src * stride;
 #pragma unroll
-                for (int v = 0; v < 8; v++) q[v] = split_double(__ldg(Uin + v * vs + gi));
+                for (int v = 0; v < 8; v++) q[v] = split_double(__ldg(Uin + v * vs + CHK(gi, NCELL)));
             }
             float prf = pressure_df(q[0], q[1 + DIR], q[1 + T1], q[1 + T2], q[4 + DIR], q[4 + T1], q[4 + T2],
                                     q[7], gm1);
@@ -616,9 +632,9 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             const bool h_table = F64 && !EX && a.ih;
             R h = R(1);
             if constexpr (F64) {
-                if (!h_table) h = R(0.5) * R(a.w[g + GH - 1]) + R(dx) + R(0.5) * R(a.w[g + GH + 1]);
+                if (!h_table) h = R(0.5) * R(a.w[CHK(g + GH - 1, NG)]) + R(dx) + R(0.5) * R(a.w[CHK(g + GH + 1, NG)]);
             } else {
-                h = R(0.5) * a.wf[g + GH - 1] + a.wf[g + GH] + R(0.5) * a.wf[g + GH + 1];
+                h = R(0.5) * a.wf[CHK(g + GH - 1, NG)] + a.wf[CHK(g + GH, NG)] + R(0.5) * a.wf[CHK(g + GH + 1, NG)];
             }
             R DB0, DB1, DB2, DA1, DA2;
             if constexpr (EX) {
@@ -628,7 +644,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
                 DA1 = (SM(A_AY, s + PS) - SM(A_AY, s - PS)) / h;
                 DA2 = (SM(A_AZ, s + PS) - SM(A_AZ, s - PS)) / h;
             } else {
-                const R ih = h_table ? R(a.ih[g + GH]) : R(1) / h;
+                const R ih = h_table ? R(a.ih[CHK(g + GH, NG)]) : R(1) / h;
                 DB0 = (SM(A_BN, s + PS) - SM(A_BN, s - PS)) * ih;
                 DB1 = (SM(A_B1, s + PS) - SM(A_B1, s - PS)) * ih;
                 DB2 = (SM(A_B2, s + PS) - SM(A_B2, s - PS)) * ih;
@@ -776,7 +792,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         R lb1 = SM(SC0 + 4, s - PS), lb2 = SM(SC0 + 5, s - PS), lfe = SM(SC0 + 6, s - PS);
         R dxr;
         if constexpr (F64) dxr = R(dx);
-        else dxr = a.wf[g + GH];
+        else dxr = a.wf[CHK(g + GH, NG)];
         dxL = dxr + dtr * (rs_u - lu);
         if (!gt0<R, EX>(dxL)) atomicOr(a.flags, FLAG_CFL);
         R bv1 = dtr * (rs_b1 - lb1);
@@ -902,15 +918,15 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         if (stage) {
             const int slot = stage_index<DIR>(l, p, NP, L), sv = stage_array_stride<DIR>(NP, L);
 #pragma unroll
-            for (int v = 0; v < 8; v++) Un[v] = stage[v * sv + slot];
+            for (int v = 0; v < 8; v++) Un[v] = stage[CHK(v * sv + slot, 8 * sv)];
         } else {
 #pragma unroll
-            for (int v = 0; v < 8; v++) Un[v] = __ldg(Uin + v * vs + gi);
+            for (int v = 0; v < 8; v++) Un[v] = __ldg(Uin + v * vs + CHK(gi, NCELL));
         }
         const int cmap[7] = {0, 1 + DIR, 1 + T1, 1 + T2, 4 + T1, 4 + T2, 7};
         const R dCv[7] = {R(0), dC[0], dC[1], dC[2], dC[3], dC[4], dC[5]};
         if constexpr (F64) {
-            const double idx = EX ? 0.0 : (a.iw ? a.iw[g + GH] : 1.0 / dx);
+            const double idx = EX ? 0.0 : (a.iw ? a.iw[CHK(g + GH, NG)] : 1.0 / dx);
 #pragma unroll
             for (int v = 0; v < 7; v++) {
                 double dU;
@@ -928,7 +944,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
                 Un[7] = Un[7] + dt * src_e;
             }
         } else {
-            const R idx = R(1) / a.wf[g + GH];
+            const R idx = R(1) / a.wf[CHK(g + GH, NG)];
             R dU[8];
 #pragma unroll
             for (int v = 0; v < 7; v++) dU[cmap[v]] = (dCv[v] + SM(flux_slot(v), s - PS) - SM(flux_slot(v), s)) * idx;
@@ -943,19 +959,19 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         }
         bool inner = false;
         if (a.inner_mask) {
-            inner = a.inner_mask[gi] != 0;
+            inner = a.inner_mask[CHK(gi, NCELL)] != 0;
         } else if constexpr (F64) {
             inner = a.r_inner > 0.0 &&
                     pos[0] * pos[0] + pos[1] * pos[1] + pos[2] * pos[2] < a.r_inner * a.r_inner;
         } else if (a.r_innerf > 0.0f) {
             // float test with an exact double test for centres within 1e-5 of the sphere
-            const float px = a.cxf[(DIR == 0 ? g : ix) + GH], py = a.cyf[(DIR == 1 ? g : iy) + GH],
-                        pz = a.czf[(DIR == 2 ? g : iz) + GH];
+            const float px = a.cxf[CHK((DIR == 0 ? g : ix) + GH, NG0)], py = a.cyf[CHK((DIR == 1 ? g : iy) + GH, NG1)],
+                        pz = a.czf[CHK((DIR == 2 ? g : iz) + GH, NG2)];
             const float r2 = px * px + py * py + pz * pz, ri2 = a.r_innerf * a.r_innerf;
             if (r2 < ri2 * (1.0f - 1e-5f)) inner = true;
             else if (r2 < ri2 * (1.0f + 1e-5f)) {
-                const double x = a.cx[(DIR == 0 ? g : ix) + GH], y = a.cy[(DIR == 1 ? g : iy) + GH],
-                             z = a.cz[(DIR == 2 ? g : iz) + GH];
+                const double x = a.cx[CHK((DIR == 0 ? g : ix) + GH, NG0)], y = a.cy[CHK((DIR == 1 ? g : iy) + GH, NG1)],
+                             z = a.cz[CHK((DIR == 2 ? g : iz) + GH, NG2)];
                 inner = x * x + y * y + z * z < a.r_inner * a.r_inner;
             }
         }
@@ -972,7 +988,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
 #pragma unroll
         for (int v = 0; v < 8; v++) {   // non-finite test on the exponent bits (integer pipe)
             bad |= ((__double2hiint(Un[v]) >> 20) & 0x7FF) == 0x7FF;
-            Uout[v * vs + gi] = Un[v];
+            Uout[v * vs + CHK(gi, NCELL)] = Un[v];
         }
         if (bad) atomicOr(a.flags, FLAG_NONFINITE);
     }

@@ -14,13 +14,16 @@ from ctypes import POINTER, c_double, c_int, c_longlong, c_void_p
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libppmlr_gb300.so")
+# PPMLR_LIBRARY selects another build of the same library (the bounds-checked
+# build the tests make with build.build(check=True)).
+LIB_PATH = os.environ.get("PPMLR_LIBRARY", os.path.join(HERE, "libppmlr_gb300.so"))
 
-PPMLR_OK, PPMLR_E_INVALID, PPMLR_E_CUDA, PPMLR_E_OOM, PPMLR_E_NONFINITE, PPMLR_E_CFL, PPMLR_E_TIMEOUT = range(7)
+(PPMLR_OK, PPMLR_E_INVALID, PPMLR_E_CUDA, PPMLR_E_OOM, PPMLR_E_NONFINITE, PPMLR_E_CFL, PPMLR_E_TIMEOUT,
+ PPMLR_E_BOUNDS) = range(8)
 PPMLR_FP64, PPMLR_MIXED, PPMLR_FP64_EXACT = 0, 1, 2
 PPMLR_BC_PERIODIC, PPMLR_BC_OUTFLOW, PPMLR_BC_INFLOW = 0, 1, 2
 STATUS_NAMES = {0: "PPMLR_OK", 1: "PPMLR_E_INVALID", 2: "PPMLR_E_CUDA", 3: "PPMLR_E_OOM",
-                4: "PPMLR_E_NONFINITE", 5: "PPMLR_E_CFL", 6: "PPMLR_E_TIMEOUT"}
+                4: "PPMLR_E_NONFINITE", 5: "PPMLR_E_CFL", 6: "PPMLR_E_TIMEOUT", 7: "PPMLR_E_BOUNDS"}
 
 
 class ppmlr_grid(ctypes.Structure):
