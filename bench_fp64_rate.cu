@@ -1,7 +1,7 @@
 // Arithmetic-pipe rates of this GPU, the denominators of the "alu" roofline
 // that bench.py reports for the FP64 sweeps: FP64 fused multiply-add, add and
-// multiply (one instruction each), FP64 division and square root (several
-// instruction slots each), FP32 fused multiply-add, and a double->float->double
+// multiply (one instruction each), FP64 division, square root and reciprocal
+// square root (several instruction slots each), FP32 fused multiply-add, and a double->float->double
 // round trip (the conversions also run on the FP64 pipe).
 //
 // Every thread runs eight independent dependency chains so that the pipe, not
@@ -21,7 +21,7 @@
         }                                                                              \
     } while (0)
 
-enum Op { DFMA, DADD, DMUL, DDIV, DSQRT, FFMA, F2F };
+enum Op { DFMA, DADD, DMUL, DDIV, DSQRT, DRSQRT, FFMA, F2F };
 
 template <int OP>
 __global__ void chains(double *out, int iters, double seed)
@@ -38,6 +38,7 @@ __global__ void chains(double *out, int iters, double seed)
             if (OP == DMUL) a[k] = a[k] * m;
             if (OP == DDIV) a[k] = c + 1.0 / a[k];
             if (OP == DSQRT) a[k] = sqrt(a[k]) + c;
+            if (OP == DRSQRT) a[k] = rsqrt(a[k]) + 1.0;
             if (OP == FFMA) {
 #pragma unroll
                 for (int r = 0; r < 8; r++) f[k] = fmaf(f[k], 0.999f, 1e-3f);
@@ -90,6 +91,7 @@ int main()
     rc |= measure<DMUL>("DMUL", 8, 2000, blocks, threads, out, sms);
     rc |= measure<DDIV>("DDIV", 8, 200, blocks, threads, out, sms);
     rc |= measure<DSQRT>("DSQRT", 8, 200, blocks, threads, out, sms);
+    rc |= measure<DRSQRT>("DRSQRT", 8, 200, blocks, threads, out, sms);
     rc |= measure<FFMA>("FFMA", 64, 2000, blocks, threads, out, sms);
     rc |= measure<F2F>("F2F", 8, 2000, blocks, threads, out, sms);   // round trips: two conversions and a DMUL each
     CK(cudaFree(out));

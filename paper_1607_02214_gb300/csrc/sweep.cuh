@@ -54,6 +54,21 @@ template <> struct K<float> {
     static __device__ __forceinline__ float rs(float x) { return rsqrtf(x); }
 };
 
+// Square root of a non-negative value.  Contracted FP64 form: x * rsqrt(x)
+// (the GB300's FP64 pipe spends ~5.9 slots on a reciprocal square root and
+// ~8.6 on a correctly rounded square root; this one is within a few ulp),
+// zero for x = 0; otherwise the library square root.
+template <typename R, bool EX>
+__device__ __forceinline__ R fsqrt(R x)
+{
+    if constexpr (!EX && std::is_same<R, double>::value) {
+        const double r = x * rsqrt(x);
+        return __double_as_longlong(x) > 0 ? r : 0.0;
+    } else {
+        return K<R>::sq(x);
+    }
+}
+
 // Fast magnetosonic speed squared along the normal (mu0 = 1).  EX: the
 // reference's expression; otherwise one reciprocal of rho shared by the three
 // quotients.
@@ -68,7 +83,7 @@ __device__ __forceinline__ R fast2(R rho, R p, R Bn, R B1, R B2, R gam)
         const R s = a2 + b2;
         R disc = s * s - R(4) * a2 * bn2;
         if (disc < R(0)) disc = R(0);
-        return R(0.5) * (s + K<R>::sq(disc));
+        return R(0.5) * (s + fsqrt<R, EX>(disc));
     }
     R a2 = gam * p / rho;
     R b2 = (Bn * Bn + B1 * B1 + B2 * B2) / rho;
@@ -124,8 +139,8 @@ __device__ __forceinline__ void two_shock(const int iters, const R uL, const R u
             P = Pc - f / (izL + izR);
         }
         const R Pc = P > R(0) ? P : R(0);
-        WL = CL * K<R>::sq(b + aL * Pc);
-        WR = CR * K<R>::sq(b + aR * Pc);
+        WL = CL * fsqrt<R, false>(b + aL * Pc);
+        WR = CR * fsqrt<R, false>(b + aR * Pc);
     }
 }
 
@@ -139,7 +154,7 @@ __device__ __forceinline__ R fast_impedance(R rho, R p, R Bn, R B1, R B2, R gam)
     const R S = gp + (Bn * Bn + B1 * B1 + B2 * B2);
     R D = S * S - R(4) * gp * (Bn * Bn);
     if (D < R(0)) D = R(0);
-    return K<R>::sq(rho * (R(0.5) * (S + K<R>::sq(D))));
+    return fsqrt<R, false>(rho * (R(0.5) * (S + fsqrt<R, false>(D))));
 }
 
 // Earth dipole along -z: B_d = M [3 (m.r) r - m r^2] / r^5, m = -z.
@@ -585,7 +600,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     }
     if (act) {
         R Pt = pr + R(0.5) * (Bn * Bn + B1 * B1 + B2 * B2);
-        W = rho * K<R>::sq(fast2<R, EX>(rho, pr, Bn, B1, B2, gam));
+        W = rho * fsqrt<R, EX>(fast2<R, EX>(rho, pr, Bn, B1, B2, gam));
         SM(A_RHO, s) = rho; SM(A_U, s) = u; SM(A_V1, s) = v1; SM(A_V2, s) = v2;
         SM(A_B1, s) = B1; SM(A_B2, s) = B2; SM(A_P, s) = pr; SM(A_DM, s) = dm;
         SM(A_PT, s) = Pt; SM(A_BN, s) = Bn;
@@ -707,7 +722,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             const R dtm = dtr / dm;
             dtm_k = dtm;
             yf = W * dtm;
-            ya = K<R>::sq(rho) * K<R>::ab(Bn) * dtm;
+            ya = fsqrt<R, EX>(rho) * K<R>::ab(Bn) * dtm;
         }
         const R own[7] = {rho, u, v1, v2, B1, B2, pr};
         R srv[9];
@@ -758,8 +773,8 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             Ps = (WR * PL + WL * PR + WL * WR * (sl[1] - Rs[1])) * iW;
         }
         R Ss = Ps - R(0.5) * Bnf * Bnf;
-        R ZL = K<R>::sq(sl[0]) * K<R>::ab(Bnf);
-        R ZR = K<R>::sq(Rs[0]) * K<R>::ab(Bnf);
+        R ZL = fsqrt<R, EX>(sl[0]) * K<R>::ab(Bnf);
+        R ZR = fsqrt<R, EX>(Rs[0]) * K<R>::ab(Bnf);
         R vs[2], ss[2];
         const R iZ = (EX || ZL + ZR == R(0)) ? R(0) : R(1) / (ZL + ZR);
 #pragma unroll
