@@ -54,6 +54,43 @@ template <> struct K<float> {
     static __device__ __forceinline__ float rs(float x) { return rsqrtf(x); }
 };
 
+// Sign and magnitude tests of doubles on the integer pipe (the GB300's FP64
+// pipe is its scarcest unit).  For finite values they decide exactly as the
+// floating-point comparisons they replace.
+__device__ __forceinline__ bool pos_d(double x) { return __double_as_longlong(x) > 0; }          // x > 0
+__device__ __forceinline__ bool neg_d(double x)                                                   // x < 0
+{
+    const long long b = __double_as_longlong(x);
+    return b < 0 && (b << 1) != 0;
+}
+__device__ __forceinline__ long long mag_d(double x) { return __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL; }
+__device__ __forceinline__ long long ord_d(double x)      // monotone map of finite doubles to integers
+{
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+// x * y > 0 (both non-zero, same sign; ignores underflow of the product)
+__device__ __forceinline__ bool same_sign_d(double x, double y)
+{
+    const long long a = __double_as_longlong(x), b = __double_as_longlong(y);
+    return (a ^ b) >= 0 && (a << 1) != 0 && (b << 1) != 0;
+}
+
+// x > 0 and x < 0 on the integer pipe for the fast double form, plain
+// comparisons otherwise.
+template <typename R, bool EX>
+__device__ __forceinline__ bool gt0(R x)
+{
+    if constexpr (!EX && std::is_same<R, double>::value) return pos_d(x);
+    else return x > R(0);
+}
+template <typename R, bool EX>
+__device__ __forceinline__ bool lt0(R x)
+{
+    if constexpr (!EX && std::is_same<R, double>::value) return neg_d(x);
+    else return x < R(0);
+}
+
 // Square root of a non-negative value.  Contracted FP64 form: x * rsqrt(x)
 // (the GB300's FP64 pipe spends ~5.9 slots on a reciprocal square root and
 // ~8.6 on a correctly rounded square root; this one is within a few ulp),
@@ -82,7 +119,8 @@ __device__ __forceinline__ R fast2(R rho, R p, R Bn, R B1, R B2, R gam)
         const R bn2 = Bn * Bn * ir;
         const R s = a2 + b2;
         R disc = s * s - R(4) * a2 * bn2;
-        if (disc < R(0)) disc = R(0);
+        if constexpr (!std::is_same<R, double>::value)      // (the double square root below returns 0 for disc <= 0)
+            if (disc < R(0)) disc = R(0);
         return R(0.5) * (s + fsqrt<R, EX>(disc));
     }
     R a2 = gam * p / rho;
@@ -131,14 +169,14 @@ __device__ __forceinline__ void two_shock(const int iters, const R uL, const R u
         const R iCL = R(1) / CL, iCR = R(1) / CR;
         R P = (WR * PL + WL * PR + WL * WR * (uL - uR)) / (WL + WR);
         for (int k = 0; k < iters; k++) {
-            const R Pc = P > R(0) ? P : R(0);
+            const R Pc = gt0<R, false>(P) ? P : R(0);
             const R rqL = K<R>::rs(b + aL * Pc), rqR = K<R>::rs(b + aR * Pc);
             const R rWL = rqL * iCL, rWR = rqR * iCR;         // 1 / W
             const R f = (uR - uL) + (Pc - PR) * rWR + (Pc - PL) * rWL;
             const R izL = R(0.5) * (R(1) + rqL * rqL) * rWL, izR = R(0.5) * (R(1) + rqR * rqR) * rWR;   // 1 / Z
             P = Pc - f / (izL + izR);
         }
-        const R Pc = P > R(0) ? P : R(0);
+        const R Pc = gt0<R, false>(P) ? P : R(0);
         WL = CL * fsqrt<R, false>(b + aL * Pc);
         WR = CR * fsqrt<R, false>(b + aR * Pc);
     }
@@ -152,8 +190,7 @@ __device__ __forceinline__ R fast_impedance(R rho, R p, R Bn, R B1, R B2, R gam)
 {
     const R gp = gam * p;
     const R S = gp + (Bn * Bn + B1 * B1 + B2 * B2);
-    R D = S * S - R(4) * gp * (Bn * Bn);
-    if (D < R(0)) D = R(0);
+    const R D = S * S - R(4) * gp * (Bn * Bn);          // fsqrt gives 0 for D <= 0
     return fsqrt<R, false>(rho * (R(0.5) * (S + fsqrt<R, false>(D))));
 }
 
@@ -179,43 +216,6 @@ __device__ __forceinline__ void dipole(double M, double x, double y, double z, d
     B[0] = M * (3.0 * mr * x) / r5;
     B[1] = M * (3.0 * mr * y) / r5;
     B[2] = M * (3.0 * mr * z + r2) / r5;
-}
-
-// Sign and magnitude tests of doubles on the integer pipe (the GB300's FP64
-// pipe is its scarcest unit).  For finite values they decide exactly as the
-// floating-point comparisons they replace.
-__device__ __forceinline__ bool pos_d(double x) { return __double_as_longlong(x) > 0; }          // x > 0
-__device__ __forceinline__ bool neg_d(double x)                                                   // x < 0
-{
-    const long long b = __double_as_longlong(x);
-    return b < 0 && (b << 1) != 0;
-}
-__device__ __forceinline__ long long mag_d(double x) { return __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL; }
-__device__ __forceinline__ long long ord_d(double x)      // monotone map of finite doubles to integers
-{
-    const long long b = __double_as_longlong(x);
-    return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
-}
-// x * y > 0 (both non-zero, same sign; ignores underflow of the product)
-__device__ __forceinline__ bool same_sign_d(double x, double y)
-{
-    const long long a = __double_as_longlong(x), b = __double_as_longlong(y);
-    return (a ^ b) >= 0 && (a << 1) != 0 && (b << 1) != 0;
-}
-
-// x > 0 and x < 0 on the integer pipe for the fast double form, plain
-// comparisons otherwise.
-template <typename R, bool EX>
-__device__ __forceinline__ bool gt0(R x)
-{
-    if constexpr (!EX && std::is_same<R, double>::value) return pos_d(x);
-    else return x > R(0);
-}
-template <typename R, bool EX>
-__device__ __forceinline__ bool lt0(R x)
-{
-    if constexpr (!EX && std::is_same<R, double>::value) return neg_d(x);
-    else return x < R(0);
 }
 
 // Limited PPM slope of zone i from its neighbours (Colella & Woodward 1984).
@@ -545,7 +545,10 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             rho = R(rd); u = R(mn * ir); v1 = R(m1 * ir); v2 = R(m2 * ir);
             e = R(E * ir);
         }
-        if (prd < a.p_min) { prd = a.p_min; floored = out_cell; }
+        // p_min >= 0: the floor test is a signed comparison of the bit patterns in
+        // the contracted form (integer pipe); the exact form compares doubles
+        const bool below = EX ? prd < a.p_min : __double_as_longlong(prd) < __double_as_longlong(a.p_min);
+        if (below) { prd = a.p_min; floored = out_cell; }
         Bn = R(bn); B1 = R(b1); B2 = R(b2); pr = R(prd);
         dm = R(rd * dx);
     } else if (act) {
@@ -631,7 +634,12 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             R Pp = SM(A_PT, s + PS), Pm = SM(A_PT, s - PS);
             R dP = Pp - Pm;
             R pmin = Pp < Pm ? Pp : Pm;
-            if (K<R>::ab(dP) > R(0.33) * pmin && SM(A_U, s - PS) - SM(A_U, s + PS) > R(0)) {
+            bool shock;
+            if constexpr (!EX && F64)      // the same tests on the bit patterns (integer pipe)
+                shock = mag_d(dP) > mag_d(R(0.33) * pmin) && pos_d(SM(A_U, s - PS) - SM(A_U, s + PS));
+            else
+                shock = K<R>::ab(dP) > R(0.33) * pmin && SM(A_U, s - PS) - SM(A_U, s + PS) > R(0);
+            if (shock) {
                 R den = SM(A_PT, s + 2 * PS) - SM(A_PT, s - 2 * PS);
                 R steep = den != R(0) ? dP / den : R(1);
                 R f = (steep - R(0.75)) * R(10);
@@ -694,9 +702,12 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             SM(SC0 + v, s) = edg[v];
         }
         if (p >= 3 && p <= NPe - 4) {
-            R up = SM(A_PT, s + PS) - SM(A_PT, s - PS) < R(0) ? SM(SB0 + 7, s + PS) : SM(SB0 + 7, s - PS);
+            R up = lt0<R, EX>(SM(A_PT, s + PS) - SM(A_PT, s - PS)) ? SM(SB0 + 7, s + PS) : SM(SB0 + 7, s - PS);
             R ft = SM(SB0 + 7, s);
-            flat = ft > up ? ft : up;
+            if constexpr (!EX && F64)      // ft, up in [0, 1]: ordered as their bit patterns
+                flat = __double_as_longlong(ft) > __double_as_longlong(up) ? ft : up;
+            else
+                flat = ft > up ? ft : up;
         }
         if (a.steepen) {   // shock exclusion of contact steepening: relative total-pressure jump vs density jump
             const R Pp = SM(A_PT, s + PS), Pm = SM(A_PT, s - PS), rp = SM(A_RHO, s + PS), rm = SM(A_RHO, s - PS);
@@ -776,12 +787,14 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         R ZL = fsqrt<R, EX>(sl[0]) * K<R>::ab(Bnf);
         R ZR = fsqrt<R, EX>(Rs[0]) * K<R>::ab(Bnf);
         R vs[2], ss[2];
-        const R iZ = (EX || ZL + ZR == R(0)) ? R(0) : R(1) / (ZL + ZR);
+        const R zsum = ZL + ZR;
+        const bool zero_z = (EX || !F64) ? zsum == R(0) : !pos_d(zsum);   // Z >= 0: zero or not
+        const R iZ = (EX || zero_z) ? R(0) : R(1) / zsum;
 #pragma unroll
         for (int t = 0; t < 2; t++) {
             R vL = sl[2 + t], vR = Rs[2 + t];
             R sL = Bnf * sl[7 + t], sR = Bnf * Rs[7 + t];
-            if (ZL + ZR == R(0)) {
+            if (zero_z) {
                 vs[t] = R(0.5) * (vL + vR);
                 ss[t] = R(0);
             } else if constexpr (EX) {
