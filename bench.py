@@ -49,14 +49,14 @@ BYTES_PER_CELL_SWEEP = 128      # read 8 FP64 + write 8 FP64
 # The FP64 sweeps and CFL pass also read the dipole table (24 B per cell) on
 # top of the state: traffic above the algorithmic 128 / 64 B by that much.
 NCU_TRAFFIC = {
-    "fp64:x": {"bytes_per_cell": 149.4, "src": "fdbb6dc302197b91"},
-    "fp64:y": {"bytes_per_cell": 149.8, "src": "fdbb6dc302197b91"},
-    "fp64:z": {"bytes_per_cell": 150.2, "src": "fdbb6dc302197b91"},
-    "fp64:cfl": {"bytes_per_cell": 88.4, "src": "b4ae1b00be01f3e2"},
-    "mixed:x": {"bytes_per_cell": 123.9, "src": "8b5949a23113de17"},
-    "mixed:y": {"bytes_per_cell": 124.9, "src": "8b5949a23113de17"},
-    "mixed:z": {"bytes_per_cell": 125.2, "src": "8b5949a23113de17"},
-    "mixed:cfl": {"bytes_per_cell": 64.4, "src": "c803d382b0ef521c"},
+    "fp64:x": {"bytes_per_cell": 149.5, "src": "9653af4d939c5c2c"},
+    "fp64:y": {"bytes_per_cell": 149.8, "src": "9653af4d939c5c2c"},
+    "fp64:z": {"bytes_per_cell": 149.9, "src": "9653af4d939c5c2c"},
+    "fp64:cfl": {"bytes_per_cell": 88.4, "src": "9d8c9755e4ea0be3"},
+    "mixed:x": {"bytes_per_cell": 123.9, "src": "2fcbe35f4e2c0a76"},
+    "mixed:y": {"bytes_per_cell": 124.9, "src": "2fcbe35f4e2c0a76"},
+    "mixed:z": {"bytes_per_cell": 125.2, "src": "2fcbe35f4e2c0a76"},
+    "mixed:cfl": {"bytes_per_cell": 64.4, "src": "9eec63ebf31e799b"},
 }
 
 
