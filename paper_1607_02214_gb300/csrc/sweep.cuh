@@ -252,23 +252,32 @@ __device__ __forceinline__ R limit_slope(R am, R a0, R ap, R c1, R c2, R c3)
 }
 
 // Monotonicity constraint of the parabola; returns a6 and updates l, r.
-// Fast double form: the extremum test as a sign test, and the two overshoot
+// Fast double form: the extremum test as a sign test, the two overshoot
 // tests da*m6 > da^2 and -da^2 > da*m6 as comparisons of m6 with +-da (the
-// constraint is continuous at both switch points).
+// constraint is continuous at both switch points), and a6 in closed form.
 template <typename R, bool EX = true>
 __device__ __forceinline__ R monotone(R ai, R &l, R &r)
 {
     if constexpr (!EX && std::is_same<R, double>::value) {
+        // a6 of the constrained parabola in closed form: 0 at an extremum,
+        // 3 (r - ai) after l = 3 ai - 2 r, 3 (l - ai) after r = 3 ai - 2 l,
+        // m6 itself when neither end moves
         if (!same_sign_d(r - ai, ai - l)) {
             l = ai; r = ai;
-        } else {
-            const double da = r - l;
-            const double m6 = 6.0 * (ai - 0.5 * (l + r));
-            const long long om = ord_d(m6), od = ord_d(da), onda = ord_d(-da);
-            if (pos_d(da) ? om > od : om < od) l = 3.0 * ai - 2.0 * r;
-            else if (pos_d(da) ? om < onda : om > onda) r = 3.0 * ai - 2.0 * l;
+            return 0.0;
         }
-        return 6.0 * (ai - 0.5 * (l + r));
+        const double da = r - l;
+        const double m6 = 6.0 * (ai - 0.5 * (l + r));
+        const long long om = ord_d(m6), od = ord_d(da), onda = ord_d(-da);
+        if (pos_d(da) ? om > od : om < od) {
+            l = 3.0 * ai - 2.0 * r;
+            return 3.0 * (r - ai);
+        }
+        if (pos_d(da) ? om < onda : om > onda) {
+            r = 3.0 * ai - 2.0 * l;
+            return 3.0 * (l - ai);
+        }
+        return m6;
     }
     if constexpr (!EX && std::is_same<R, float>::value) {   // branch-free: selects only
         const float da = r - l;
