@@ -218,23 +218,24 @@ __device__ __forceinline__ void dipole(double M, double x, double y, double z, d
     B[2] = M * (3.0 * mr * z + r2) / r5;
 }
 
-// Limited PPM slope of zone i from its neighbours (Colella & Woodward 1984).
+// Limited PPM slope of zone i from its neighbours (Colella & Woodward 1984):
+// da = c1 (c2 dp + c3 dm), limited to 2 min(|dm|, |dp|) and zero at an
+// extremum.  Contracted forms: c2 and c3 arrive with c1 folded in (c1 is not
+// used), and the two limits as one doubling of the smaller difference.
 template <typename R, bool EX = true>
 __device__ __forceinline__ R limit_slope(R am, R a0, R ap, R c1, R c2, R c3)
 {
     if constexpr (!EX && std::is_same<R, double>::value) {
         const double dp = ap - a0, dm = a0 - am;
-        const double da = c1 * (c2 * dp + c3 * dm);
         if (!same_sign_d(dp, dm)) return 0.0;
-        double m = fabs(da);
-        const double lim_m = 2.0 * fabs(dm), lim_p = 2.0 * fabs(dp);
-        if (mag_d(lim_m) < mag_d(m)) m = lim_m;
-        if (mag_d(lim_p) < mag_d(m)) m = lim_p;
+        const double da = c2 * dp + c3 * dm;
+        const double lim = 2.0 * __longlong_as_double(min(mag_d(dm), mag_d(dp)));
+        const double m = mag_d(lim) < mag_d(da) ? lim : fabs(da);
         return pos_d(da) ? m : (neg_d(da) ? -m : 0.0);
     }
     if constexpr (!EX && std::is_same<R, float>::value) {   // branch-free: min/max and selects
         const float dp = ap - a0, dm = a0 - am;
-        const float da = c1 * (c2 * dp + c3 * dm);
+        const float da = c2 * dp + c3 * dm;
         const float m = fminf(fabsf(da), 2.0f * fminf(fabsf(dm), fabsf(dp)));
         return dp * dm > 0.0f ? copysignf(m, da) : 0.0f;
     }
@@ -252,32 +253,34 @@ __device__ __forceinline__ R limit_slope(R am, R a0, R ap, R c1, R c2, R c3)
 }
 
 // Monotonicity constraint of the parabola; returns a6 and updates l, r.
-// Fast double form: the extremum test as a sign test, the two overshoot
-// tests da*m6 > da^2 and -da^2 > da*m6 as comparisons of m6 with +-da (the
-// constraint is continuous at both switch points), and a6 in closed form.
+// Fast double form, on the one-sided differences dl = ai - l, dr = r - ai
+// (da = dl + dr, a6 = 3 (dl - dr)): the extremum test is a sign test; with dl,
+// dr of one sign the overshoot tests da*a6 > da^2 and -da^2 > da*a6 reduce to
+// |dl| > 2 |dr| and |dr| > 2 |dl|, compared on the bit patterns with the
+// doubling as an exponent increment (exact for normal numbers; for a
+// subnormal difference the threshold moves by less than 2^-1021, and the
+// constraint is continuous at both switch points); the moved end and a6 then
+// have closed forms: l = ai - 2 dr, a6 = 3 dr, or r = ai + 2 dl, a6 = -3 dl.
 template <typename R, bool EX = true>
 __device__ __forceinline__ R monotone(R ai, R &l, R &r)
 {
     if constexpr (!EX && std::is_same<R, double>::value) {
-        // a6 of the constrained parabola in closed form: 0 at an extremum,
-        // 3 (r - ai) after l = 3 ai - 2 r, 3 (l - ai) after r = 3 ai - 2 l,
-        // m6 itself when neither end moves
-        if (!same_sign_d(r - ai, ai - l)) {
+        const double dl = ai - l, dr = r - ai;
+        if (!same_sign_d(dr, dl)) {
             l = ai; r = ai;
             return 0.0;
         }
-        const double da = r - l;
-        const double m6 = 6.0 * (ai - 0.5 * (l + r));
-        const long long om = ord_d(m6), od = ord_d(da), onda = ord_d(-da);
-        if (pos_d(da) ? om > od : om < od) {
-            l = 3.0 * ai - 2.0 * r;
-            return 3.0 * (r - ai);
+        constexpr long long twice = 1LL << 52;
+        const long long ml = mag_d(dl), mr = mag_d(dr);
+        if (ml > mr + twice) {
+            l = ai - 2.0 * dr;
+            return 3.0 * dr;
         }
-        if (pos_d(da) ? om < onda : om > onda) {
-            r = 3.0 * ai - 2.0 * l;
-            return 3.0 * (l - ai);
+        if (mr > ml + twice) {
+            r = ai + 2.0 * dl;
+            return -3.0 * dl;
         }
-        return m6;
+        return 3.0 * (dl - dr);
     }
     if constexpr (!EX && std::is_same<R, float>::value) {   // branch-free: selects only
         const float da = r - l;
@@ -318,18 +321,19 @@ __device__ __forceinline__ R avg_left(R l, R r, R a6, R y)
 // reconstructed variables).
 template <typename R> struct SlopeCoef { R c1, c2, c3; };
 // EX: three quotients as in the reference; otherwise one reciprocal of the
-// product of the three denominators.
+// product of the three denominators, and c1 folded into c2 and c3
+// (c1 c2 = x0 (2 xm + x0) / (d1 d2), c1 c3 = x0 (x0 + 2 xp) / (d1 d3);
+// c1 is returned as 1).
 template <typename R, bool EX = true>
 __device__ __forceinline__ SlopeCoef<R> slope_coef(R xm, R x0, R xp)
 {
     if constexpr (!EX) {
         const R d1 = xm + x0 + xp, d2 = xp + x0, d3 = xm + x0;
-        const R d23 = d2 * d3;
-        const R inv = R(1) / (d1 * d23);
+        const R q = x0 * (R(1) / (d1 * (d2 * d3)));
         SlopeCoef<R> k;
-        k.c1 = x0 * d23 * inv;
-        k.c2 = (R(2) * xm + x0) * (d1 * d3) * inv;
-        k.c3 = (x0 + R(2) * xp) * (d1 * d2) * inv;
+        k.c1 = R(1);
+        k.c2 = (R(2) * xm + x0) * d3 * q;
+        k.c3 = (x0 + R(2) * xp) * d2 * q;
         return k;
     }
     R s3 = xm + x0 + xp;
@@ -341,7 +345,8 @@ __device__ __forceinline__ SlopeCoef<R> slope_coef(R xm, R x0, R xp)
 }
 template <typename R> struct EdgeCoef { R k1, k2, k3, k4, k5; };
 // EX: the reference's five quotients; otherwise one reciprocal of the
-// product of the four denominators.
+// product of the four denominators, and k2 folded into the others (see
+// edge_value): k1 + k2 k3, k2 k4, k2 k5 are returned in k1, k4, k5.
 template <typename R, bool EX = true>
 __device__ __forceinline__ EdgeCoef<R> edge_coef(R x0, R x1, R x2, R x3)
 {
@@ -352,11 +357,11 @@ __device__ __forceinline__ EdgeCoef<R> edge_coef(R x0, R x1, R x2, R x3)
         const R r1 = d2 * d34 * inv, r2 = d1 * d34 * inv, r3 = d12 * d4 * inv, r4 = d12 * d3 * inv;
         const R z1 = (x0 + x1) * r1, z2 = (x3 + x2) * r2;
         EdgeCoef<R> k;
-        k.k1 = x1 * r3;
-        k.k2 = r4;
-        k.k3 = R(2) * x2 * x1 * r3 * (z1 - z2);
-        k.k4 = x1 * z1;
-        k.k5 = x2 * z2;
+        k.k1 = x1 * r3 * (R(1) + R(2) * x2 * r4 * (z1 - z2));
+        k.k2 = R(0);
+        k.k3 = R(0);
+        k.k4 = x1 * z1 * r4;
+        k.k5 = x2 * z2 * r4;
         return k;
     }
     R z1 = (x0 + x1) / (R(2) * x1 + x2);
@@ -370,10 +375,13 @@ __device__ __forceinline__ EdgeCoef<R> edge_coef(R x0, R x1, R x2, R x3)
     k.k5 = x2 * z2;
     return k;
 }
-template <typename R>
+// Interface value a_{i+1/2} = a0 + k1 d + k2 (k3 d - k4 dm_{i+1} + k5 dm_i),
+// d = a1 - a0; contracted forms with the folded coefficients of edge_coef.
+template <typename R, bool EX = true>
 __device__ __forceinline__ R edge_value(const EdgeCoef<R> &k, R a0, R a1, R dmi, R dmi1)
 {
-    R d = a1 - a0;
+    const R d = a1 - a0;
+    if constexpr (!EX) return a0 + k.k1 * d - k.k4 * dmi1 + k.k5 * dmi;
     return a0 + k.k1 * d + k.k2 * (k.k3 * d - k.k4 * dmi1 + k.k5 * dmi);
 }
 
@@ -707,7 +715,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         const R own[7] = {rho, u, v1, v2, B1, B2, pr};
 #pragma unroll
         for (int v = 0; v < 7; v++) {
-            edg[v] = edge_value<R>(k, own[v], SM(A_RHO + v, s + PS), dmv[v], SM(SB0 + v, s + PS));
+            edg[v] = edge_value<R, EX>(k, own[v], SM(A_RHO + v, s + PS), dmv[v], SM(SB0 + v, s + PS));
             SM(SC0 + v, s) = edg[v];
         }
         if (p >= 3 && p <= NPe - 4) {
@@ -746,10 +754,18 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         }
         const R own[7] = {rho, u, v1, v2, B1, B2, pr};
         R srv[9];
+        // contracted forms: no blend where the zone is not flattened (flat is +0;
+        // the double test on its bit pattern)
+        bool blend = true;
+        if constexpr (!EX && F64) blend = __double_as_longlong(flat) != 0;
+        else if constexpr (!EX) blend = flat != R(0);
 #pragma unroll
         for (int v = 0; v < 7; v++) {
-            R lft = flat * own[v] + (R(1) - flat) * SM(SC0 + v, s - PS);
-            R rgt = flat * own[v] + (R(1) - flat) * edg[v];
+            R lft = SM(SC0 + v, s - PS), rgt = edg[v];
+            if (blend) {
+                lft = flat * own[v] + (R(1) - flat) * lft;
+                rgt = flat * own[v] + (R(1) - flat) * rgt;
+            }
             R a6 = monotone<R, EX>(own[v], lft, rgt);
             R y = (v == 2 || v == 3) ? ya : yf;
             sl[v] = avg_right<R>(lft, rgt, a6, y);
@@ -892,7 +908,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         EdgeCoef<R> k = edge_coef<R, EX>(SM(SB0 + 7, s - PS), dxL, SM(SB0 + 7, s + PS), SM(SB0 + 7, s + 2 * PS));
 #pragma unroll
         for (int v = 0; v < 7; v++) {
-            red[v] = edge_value<R>(k, qL[v], SM(SB0 + v, s + PS), rmv[v], SM(v, s + PS));
+            red[v] = edge_value<R, EX>(k, qL[v], SM(SB0 + v, s + PS), rmv[v], SM(v, s + PS));
             SM(SC0 + v, s) = red[v];
         }
         if (a.steepen && p >= 6 && !shock_k) {   // contact weight of this zone
