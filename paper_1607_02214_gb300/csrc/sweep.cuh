@@ -1183,9 +1183,23 @@ __global__ void __launch_bounds__(MaxThreads<R>::value, TmaMinBlocks<R, PERSIST>
     }
 }
 
+// Register cap of the single-domain kernel: the tile-size limit's share of
+// the register file, except for the contracted FP64 form, where a tighter
+// cap (a few spilled values) lets two blocks of the usual tile shapes reside
+// on an SM: 96 for the x sweep (2 x 288 threads), 72 for y and z
+// (2 x 416 threads).  Measured on GB300 at 256x192x192: x 18.1 -> 16.5 ms,
+// y and z 16.8 -> 15.9 ms per sweep.
+template <int DIR, typename R, bool EX> struct SweepRegCap {
+    static constexpr int value = 65536 / MaxThreads<R>::value;
+};
+template <int DIR> struct SweepRegCap<DIR, double, false> {
+    static constexpr int value = DIR == 0 ? 96 : 72;
+};
+static_assert(SweepRegCap<0, double, false>::value * MAXT_F64 <= 65536, "FP64 tile budget vs register cap");
+
 // Single domain: one block per tile.
 template <int DIR, typename R, bool EX>
-__global__ void __launch_bounds__(MaxThreads<R>::value) sweep_kernel(SweepArgs a)
+__global__ void __maxnreg__((SweepRegCap<DIR, R, EX>::value)) sweep_kernel(SweepArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     sweep_tile<DIR, R, EX, const SweepArgs>(a, blockIdx.x, smem_raw, 0);
