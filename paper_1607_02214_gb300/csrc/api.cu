@@ -598,6 +598,9 @@ static ppmlr_status launch_cfl_kernel(ppmlr_ctx *c, double cfl, bool advance_tim
     a.t_acc = advance_time ? c->dt_dev + 1 : nullptr;
     a.bd = c->bd;
     a.bd_vs = (long long)c->stride;
+    if (c->prec == PPMLR_FP64)
+        for (int d = 0; d < 3; d++) a.iw[d] = c->iw[d];
+    a.inner_mask = c->inner_mask;
     for (int d = 0; d < 3; d++) { a.wf[d] = c->wf[d]; a.cf[d] = c->cf[d]; }
     a.gammaf = (float)a.gamma; a.p_minf = (float)a.p_min; a.Mf = (float)a.M; a.r_innerf = (float)a.r_inner;
     int rec = timing_begin(c, 3);

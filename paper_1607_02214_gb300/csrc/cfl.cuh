@@ -6,8 +6,12 @@
 // (atomic ticket, no floating-point atomics) combines the per-block minima and
 // resets the ticket.  EX: the reference's expressions (cfl.cu, compiled
 // without contraction: bit-identical dt); otherwise the pressure once per cell,
-// one reciprocal of rho and square roots as x * rsqrt(x) (cfl_fp64.cu, with
-// contraction).
+// one reciprocal of rho, square roots as x * rsqrt(x), sign and order tests of
+// non-negative values on the integer pipe and, given the reciprocal widths,
+// the rate max (|v_d| + c_f,d) / dx_d in place of the quotients, inverted once
+// per thread (cfl_fp64.cu, with contraction).  Both forms take the inner
+// sphere from the per-cell mask when the context has one (computed on the
+// host with the reference's expression).
 #pragma once
 #include <math.h>
 
@@ -64,11 +68,16 @@ __device__ __forceinline__ void cfl_body(const CflArgs &a, const int bid, const 
     const long long nx = a.n[0], ny = a.n[1], nz = a.n[2];
     const long long ncell = nx * ny * nz;
     double best = INFINITY;
+    double rate = 0.0;        // contracted form with reciprocal widths: max rate of the thread's cells
     for (long long i = (long long)bid * blockDim.x + threadIdx.x; i < ncell;
          i += (long long)nb * blockDim.x) {
         const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / (nx * ny));
-        const double x = a.c[0][ix + GH], y = a.c[1][iy + GH], z = a.c[2][iz + GH];
-        if (a.r_inner > 0.0 && x * x + y * y + z * z < a.r_inner * a.r_inner) continue;
+        if (a.inner_mask) {
+            if (a.inner_mask[i]) continue;
+        } else if (a.r_inner > 0.0) {
+            const double x = a.c[0][ix + GH], y = a.c[1][iy + GH], z = a.c[2][iz + GH];
+            if (x * x + y * y + z * z < a.r_inner * a.r_inner) continue;
+        }
         double U[8];
 #pragma unroll
         for (int v = 0; v < 8; v++) U[v] = __ldg(a.U[v] + i);
@@ -78,6 +87,7 @@ __device__ __forceinline__ void cfl_body(const CflArgs &a, const int bid, const 
             Bd[1] = __ldg(a.bd + a.bd_vs + i);
             Bd[2] = __ldg(a.bd + 2 * a.bd_vs + i);
         } else {
+            const double x = a.c[0][ix + GH], y = a.c[1][iy + GH], z = a.c[2][iz + GH];
             double r2 = x * x + y * y + z * z;
             if (a.M != 0.0 && r2 != 0.0) {
                 double r = sqrt(r2);
@@ -110,24 +120,32 @@ __device__ __forceinline__ void cfl_body(const CflArgs &a, const int bid, const 
             const double ir = 1.0 / U[0];
             double pr = (a.gamma - 1.0) * (U[7] - 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) * ir
                                            - 0.5 * (U[4] * U[4] + U[5] * U[5] + U[6] * U[6]));
-            if (pr < a.p_min) pr = a.p_min;
+            if (__double_as_longlong(pr) < __double_as_longlong(a.p_min)) pr = a.p_min;   // p_min >= 0
             const double a2 = a.gamma * pr * ir;
             const double bp2 = (U[4] * U[4] + U[5] * U[5] + U[6] * U[6]) * ir;
             const double Bt[3] = {U[4] + Bd[0], U[5] + Bd[1], U[6] + Bd[2]};
             const double bt2 = (Bt[0] * Bt[0] + Bt[1] * Bt[1] + Bt[2] * Bt[2]) * ir;
 #pragma unroll
             for (int d = 0; d < 3; d++) {
+                // c1, c2 >= 0 and the rates >= 0: ordered as their bit patterns;
+                // sqrt_fast gives 0 for a negative discriminant
                 double s1 = a2 + bp2, s2 = a2 + bt2;
                 double q1 = s1 * s1 - 4.0 * a2 * (U[4 + d] * U[4 + d] * ir);
                 double q2 = s2 * s2 - 4.0 * a2 * (Bt[d] * Bt[d] * ir);
-                double c1 = 0.5 * (s1 + sqrt_fast(q1 > 0.0 ? q1 : 0.0));
-                double c2 = 0.5 * (s2 + sqrt_fast(q2 > 0.0 ? q2 : 0.0));
-                double cf = sqrt_fast(c1 > c2 ? c1 : c2);
-                double s = a.w[d][idx[d] + GH] / (fabs(U[1 + d] * ir) + cf);
-                if (s < best) best = s;
+                double c1 = 0.5 * (s1 + sqrt_fast(q1));
+                double c2 = 0.5 * (s2 + sqrt_fast(q2));
+                double cf = sqrt_fast(__double_as_longlong(c1) > __double_as_longlong(c2) ? c1 : c2);
+                if (a.iw[0]) {
+                    const double r = (fabs(U[1 + d] * ir) + cf) * a.iw[d][idx[d] + GH];
+                    if (__double_as_longlong(r) > __double_as_longlong(rate)) rate = r;
+                } else {
+                    double s = a.w[d][idx[d] + GH] / (fabs(U[1 + d] * ir) + cf);
+                    if (s < best) best = s;
+                }
             }
         }
     }
+    if (!EX && a.iw[0]) best = 1.0 / rate;     // no cell: 1 / 0 = inf, as the quotient form
     best = block_min(best);
     __shared__ bool last;
     if (threadIdx.x == 0) {

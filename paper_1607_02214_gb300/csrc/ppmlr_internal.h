@@ -93,6 +93,8 @@ struct CflArgs {
     double *t_acc;             // device scalar or null: the last block adds dt (simulated time)
     const double *bd;          // FP64 forms: dipole table of the domain (component k at bd + k * bd_vs) or null
     long long bd_vs;
+    const double *iw[3];       // contracted FP64 form: ghost-extended reciprocal widths, or null
+    const unsigned char *inner_mask;   // per cell: 1 inside the inner sphere, or null
 };
 
 // Tile shape of one sweep direction.

@@ -498,6 +498,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     double dx = 0.0, pos[3] = {0.0, 0.0, 0.0}, Bdg[3] = {0.0, 0.0, 0.0};
     R rho = 0, u = 0, v1 = 0, v2 = 0, Bn = 0, B1 = 0, B2 = 0, pr = 0, W = 0, dm = 0, e = 0;
     R Bd0 = 0, Bd1 = 0, Bd2 = 0;
+    R dtm_k = 0;               // contracted forms: dt / dm (P1 or P4 -> P6)
     bool floored = false;
     const bool out_cell = act && p >= GH && p < GH + Ce;
     if (act && F64) {
@@ -561,6 +562,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
                                      - 0.5 * (bn * bn + b1 * b1 + b2 * b2));
             rho = R(rd); u = R(mn * ir); v1 = R(m1 * ir); v2 = R(m2 * ir);
             e = R(E * ir);
+            if (a.iw) dtm_k = R(dt * ir * a.iw[CHK(g + GH, NG)]);    // dt / (rho dx) without a division
         }
         // p_min >= 0: the floor test is a signed comparison of the bit patterns in
         // the contracted form (integer pipe); the exact form compares doubles
@@ -620,7 +622,8 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     }
     if (act) {
         R Pt = pr + R(0.5) * (Bn * Bn + B1 * B1 + B2 * B2);
-        W = rho * fsqrt<R, EX>(fast2<R, EX>(rho, pr, Bn, B1, B2, gam));
+        if constexpr (F64 && !EX) W = fast_impedance<R>(rho, pr, Bn, B1, B2, gam);
+        else W = rho * fsqrt<R, EX>(fast2<R, EX>(rho, pr, Bn, B1, B2, gam));
         SM(A_RHO, s) = rho; SM(A_U, s) = u; SM(A_V1, s) = v1; SM(A_V2, s) = v2;
         SM(A_B1, s) = B1; SM(A_B2, s) = B2; SM(A_P, s) = pr; SM(A_DM, s) = dm;
         SM(A_PT, s) = Pt; SM(A_BN, s) = Bn;
@@ -693,15 +696,28 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             }
             R J0 = 0, J1 = -DB2, J2 = DB1;
             R cA0 = 0, cA1 = -DA2, cA2 = DA1;
-            src_m[0] = J1 * Bd2 - J2 * Bd1;
-            src_m[1] = J2 * Bd0 - J0 * Bd2;
-            src_m[2] = J0 * Bd1 - J1 * Bd0;
             R divB = DB0;
-            R pw = a.powell ? R(1) : R(0);
-            src_b[0] = cA0 - pw * u * divB;
-            src_b[1] = cA1 - pw * v1 * divB;
-            src_b[2] = cA2 - pw * v2 * divB;
-            src_e = u * src_m[0] + v1 * src_m[1] + v2 * src_m[2] + Bn * cA0 + B1 * cA1 + B2 * cA2;
+            if constexpr (EX) {
+                src_m[0] = J1 * Bd2 - J2 * Bd1;
+                src_m[1] = J2 * Bd0 - J0 * Bd2;
+                src_m[2] = J0 * Bd1 - J1 * Bd0;
+                R pw = a.powell ? R(1) : R(0);
+                src_b[0] = cA0 - pw * u * divB;
+                src_b[1] = cA1 - pw * v1 * divB;
+                src_b[2] = cA2 - pw * v2 * divB;
+                src_e = u * src_m[0] + v1 * src_m[1] + v2 * src_m[2] + Bn * cA0 + B1 * cA1 + B2 * cA2;
+            } else {            // the same terms without the products with J0 = cA0 = 0
+                src_m[0] = J1 * Bd2 - J2 * Bd1;
+                src_m[1] = J2 * Bd0;
+                src_m[2] = -(J1 * Bd0);
+                src_b[0] = R(0); src_b[1] = cA1; src_b[2] = cA2;
+                if (a.powell) {
+                    src_b[0] = -(u * divB);
+                    src_b[1] = cA1 - v1 * divB;
+                    src_b[2] = cA2 - v2 * divB;
+                }
+                src_e = u * src_m[0] + v1 * src_m[1] + v2 * src_m[2] + B1 * cA1 + B2 * cA2;
+            }
         }
     }
     __syncthreads();
@@ -733,9 +749,9 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     }
     __syncthreads();
 
-    // reciprocals kept from one phase to a later one (contracted forms only):
-    // dt / dm (P4 -> P6) and 1 / dxL (P6 -> P9)
-    R dtm_k = 0, idxL_k = 0;
+    // reciprocal kept from one phase to a later one (contracted forms only):
+    // 1 / dxL (P6 -> P9)
+    R idxL_k = 0;
 
     // ---------------- P4: parabolas and characteristic tracing ----------------
     // left state of interface p+1/2 (this zone, right end): kept in registers;
@@ -747,8 +763,8 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             yf = W * dtr / dm;
             ya = K<R>::sq(rho) * K<R>::ab(Bn) * dtr / dm;
         } else {
-            const R dtm = dtr / dm;
-            dtm_k = dtm;
+            if (!(F64 && a.iw)) dtm_k = dtr / dm;       // else from P1
+            const R dtm = dtm_k;
             yf = W * dtm;
             ya = fsqrt<R, EX>(rho) * K<R>::ab(Bn) * dtm;
         }
@@ -861,7 +877,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             qL[0] = rhoL; qL[1] = rhoL * uL; qL[2] = rhoL * v1L; qL[3] = rhoL * v2L;
             qL[4] = B1dx / dxL; qL[5] = B2dx / dxL; qL[6] = rhoL * eL;
         } else {
-            const R dtm = dtm_k, idxL = R(1) / dxL;     // dt / dm from P4 (same cells and value)
+            const R dtm = dtm_k, idxL = R(1) / dxL;     // dt / dm from P1 or P4
             idxL_k = idxL;
             R uL = u - (rs_S - lS) * dtm;
             R v1L = v1 + (rs_s1 - ls1) * dtm;
@@ -984,6 +1000,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             for (int v = 0; v < 7; v++) {
                 double dU;
                 if constexpr (EX) dU = (dCv[v] + SM(flux_slot(v), s - PS) - SM(flux_slot(v), s)) / dx;
+                else if (v == 0) dU = (SM(flux_slot(v), s - PS) - SM(flux_slot(v), s)) * idx;   // no Lagrangian term
                 else dU = (dCv[v] + SM(flux_slot(v), s - PS) - SM(flux_slot(v), s)) * idx;
                 Un[cmap[v]] = Un[cmap[v]] + dU;
             }
