@@ -66,6 +66,7 @@ def lib():
         L.orc_riemann_nl.argtypes = [_dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp]
         L.orc_set_riemann.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_set_steepening.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_set_inner_velocity.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         _lib = L
     return _lib
 
@@ -148,6 +149,15 @@ class Oracle:
     @step_count.setter
     def step_count(self, s):
         lib().orc_set_step_count(self._h, int(s))
+
+    def set_inner_velocity(self, v):
+        """Flow of the inner-sphere cells, (3, nz, ny, nx) or None (the fixed
+        inner state's own flow)."""
+        if v is None:
+            lib().orc_set_inner_velocity(self._h, None)
+            return
+        a = np.ascontiguousarray(v, dtype=np.float64)
+        lib().orc_set_inner_velocity(self._h, a.ctypes.data_as(ctypes.c_void_p))
 
     def set_steepening(self, on):
         """Contact steepening of the remapped densities (Colella & Woodward 1984)."""

@@ -69,6 +69,7 @@ typedef struct {
     int powell;
     int riemann_iters;       /* 0: two-wave Riemann solver; k > 0: k two-shock Newton steps */
     int steepen;             /* 1: contact steepening in the remap */
+    double *inner_v;         /* [3][nz][ny][nx] flow of the inner cells (ionosphere), or NULL: at rest */
     double *U;               /* [8][nz][ny][nx], x fastest */
     double *Unew;
     long long floors;
@@ -333,7 +334,17 @@ void orc_destroy(orc_ctx *c)
 {
     if (!c) return;
     for (int d = 0; d < 3; d++) { free(c->w[d]); free(c->c[d]); }
-    free(c->U); free(c->Unew); free(c);
+    free(c->inner_v); free(c->U); free(c->Unew); free(c);
+}
+
+/* Flow of the inner-sphere cells set by the ionosphere shell (Sec. II): v =
+ * 3 arrays of ncell values (x fastest), copied; NULL puts the inner state back
+ * at rest. */
+void orc_set_inner_velocity(orc_ctx *c, const double *v)
+{
+    if (!v) { free(c->inner_v); c->inner_v = NULL; return; }
+    if (!c->inner_v) c->inner_v = (double *)malloc(sizeof(double) * 3 * ncell(c));
+    memcpy(c->inner_v, v, sizeof(double) * 3 * ncell(c));
 }
 
 void orc_set_state(orc_ctx *c, const double *U) { memcpy(c->U, U, sizeof(double) * NVAR * ncell(c)); }
@@ -370,10 +381,15 @@ static int is_inner(const orc_ctx *c, double x, double y, double z)
     return c->r_inner > 0.0 && x * x + y * y + z * z < c->r_inner * c->r_inner;
 }
 
-static void inner_state(const orc_ctx *c, double *U)
+/* Fixed inner state of cell gi: density, pressure and flow of the
+ * configuration, B' = 0; the flow replaced by the ionosphere's when set. */
+static void inner_state(const orc_ctx *c, size_t gi, double *U)
 {
     const double zero[3] = {0.0, 0.0, 0.0};
-    prim_to_cons(c->inner[0], &c->inner[1], zero, c->inner[7], c->gamma, U);
+    double v[3] = {c->inner[1], c->inner[2], c->inner[3]};
+    if (c->inner_v)
+        for (int m = 0; m < 3; m++) v[m] = c->inner_v[(size_t)m * ncell(c) + gi];
+    prim_to_cons(c->inner[0], v, zero, c->inner[7], c->gamma, U);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -709,8 +725,8 @@ static void sweep_pencil(orc_ctx *c, int d, int j, int k, double dt, pencil_buf 
         }
         double xyz[3] = {tc[0], tc[1], tc[2]};
         xyz[d] = b->pos[p];
-        if (is_inner(c, xyz[0], xyz[1], xyz[2])) inner_state(c, Un);
         size_t gi = gidx(c, d, p - G, j, k);
+        if (is_inner(c, xyz[0], xyz[1], xyz[2])) inner_state(c, gi, Un);
         for (int v = 0; v < NVAR; v++) {
             if (!isfinite(Un[v])) *flags |= FLAG_NONFINITE;
             c->Unew[(size_t)v * ncell(c) + gi] = Un[v];
