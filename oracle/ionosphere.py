@@ -261,37 +261,39 @@ def potential_at(phi, x, y, z, r_inner, cfg):
     return out
 
 
-def inner_velocity(phi, edges, M, r_inner, cfg):
-    """E x B_d / |B_d|^2 on the cells inside the inner sphere, shape
-    (3, nz, ny, nx), zero elsewhere [R6]."""
+def inner_drift(phi, edges, M, r_inner, cfg):
+    """E = -grad Phi and v = E x B_d / |B_d|^2 on the cells inside the inner
+    sphere, each (3, nz, ny, nx), zero elsewhere [R6]."""
     cx, cy, cz = cell_centres(edges)
     nx, ny, nz = cx.size, cy.size, cz.size
+    E = np.zeros((3, nz, ny, nx))
     v = np.zeros((3, nz, ny, nx))
     Z, Y, X = np.meshgrid(cz, cy, cx, indexing="ij")
-    inner = X * X + Y * Y + Z * Z < r_inner * r_inner
-    for iz, iy, ix in zip(*np.nonzero(inner)):
-        x, y, z = cx[ix], cy[iy], cz[iz]
-        E = []
-        for d, (c, i, n) in enumerate(((cx, ix, nx), (cy, iy, ny), (cz, iz, nz))):
-            lo, hi = max(i - 1, 0), min(i + 1, n - 1)
-            pm = [x, y, z]
-            pp = [x, y, z]
-            pm[d], pp[d] = c[lo], c[hi]
-            fm = potential_at(phi, np.array([pm[0]]), np.array([pm[1]]), np.array([pm[2]]), r_inner, cfg)[0]
-            fp = potential_at(phi, np.array([pp[0]]), np.array([pp[1]]), np.array([pp[2]]), r_inner, cfg)[0]
-            E.append(-(fp - fm) / (c[hi] - c[lo]))
-        bx, by, bz = (float(b) for b in dipole(M, x, y, z))
-        b2 = bx * bx + by * by + bz * bz
-        if b2 == 0.0:
-            continue
-        v[0, iz, iy, ix] = (E[1] * bz - E[2] * by) / b2
-        v[1, iz, iy, ix] = (E[2] * bx - E[0] * bz) / b2
-        v[2, iz, iy, ix] = (E[0] * by - E[1] * bx) / b2
-    return v
+    iz, iy, ix = np.nonzero(X * X + Y * Y + Z * Z < r_inner * r_inner)
+    if iz.size == 0:
+        return E, v
+    x, y, z = cx[ix], cy[iy], cz[iz]
+    for d, (c, i, n) in enumerate(((cx, ix, nx), (cy, iy, ny), (cz, iz, nz))):
+        lo, hi = np.maximum(i - 1, 0), np.minimum(i + 1, n - 1)
+        pm = [x.copy(), y.copy(), z.copy()]
+        pp = [x.copy(), y.copy(), z.copy()]
+        pm[d], pp[d] = c[lo], c[hi]
+        fm = potential_at(phi, pm[0], pm[1], pm[2], r_inner, cfg)
+        fp = potential_at(phi, pp[0], pp[1], pp[2], r_inner, cfg)
+        E[d, iz, iy, ix] = -(fp - fm) / (c[hi] - c[lo])
+    bx, by, bz = dipole(M, x, y, z)
+    b2 = bx * bx + by * by + bz * bz
+    ok = b2 > 0.0
+    b2 = np.where(ok, b2, 1.0)
+    Ex, Ey, Ez = E[0, iz, iy, ix], E[1, iz, iy, ix], E[2, iz, iy, ix]
+    v[0, iz, iy, ix] = np.where(ok, (Ey * bz - Ez * by) / b2, 0.0)
+    v[1, iz, iy, ix] = np.where(ok, (Ez * bx - Ex * bz) / b2, 0.0)
+    v[2, iz, iy, ix] = np.where(ok, (Ex * by - Ey * bx) / b2, 0.0)
+    return E, v
 
 
 def couple(U, edges, M, r_inner, cfg):
     """One ionosphere solve: (inner-cell velocities, Phi, J_r)."""
     jr = radial_current(U, edges, M, r_inner, cfg)
     phi = solve_potential(jr, r_inner, cfg)
-    return inner_velocity(phi, edges, M, r_inner, cfg), phi, jr
+    return inner_drift(phi, edges, M, r_inner, cfg)[1], phi, jr

@@ -74,3 +74,43 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                         "--deselect", "tests/test_oracle_scheme.py::test_brio_wu_self_convergence", *PINS],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"planted mistake {name} passed every pin:\n{r.stdout[-2000:]}"
+
+
+# The ionosphere shell (oracle/ionosphere.py) against its own pins.
+IONO_SRC = os.path.join(ROOT, "oracle", "ionosphere.py")
+IONO_MUTANTS = {
+    "iono_source_sign": ("rhs = (cfg.r_iono * cfg.r_iono / cfg.sigma_p) * jr[h].reshape(-1)",
+                         "rhs = -(cfg.r_iono * cfg.r_iono / cfg.sigma_p) * jr[h].reshape(-1)"),
+    "iono_neumann_edge": ("A[row, row] -= sp / (s * dth * dth)       # odd ghost",
+                          "A[row, row] -= 0.0 * sp / (s * dth * dth)       # odd ghost"),
+    "iono_pole_flux": ("sm = math.sin(th[j] - 0.5 * dth) if j > 0 else 0.0",
+                       "sm = math.sin(th[j] - 0.5 * dth) if j > 0 else math.sin(0.5 * dth)"),
+    "iono_phi_term": ("A[row, row] -= 2.0 / (s * s * dph * dph)", "A[row, row] -= 2.0 / (s * dph * dph)"),
+    "iono_foot_exponent": ("s2i = np.where(r > 0.0, r_iono / np.where(r > 0.0, r, 1.0), np.inf) * s2",
+                           "s2i = np.where(r > 0.0, (r_iono / np.where(r > 0.0, r, 1.0)) ** 1.5, np.inf) * s2"),
+    "iono_hemisphere_swap": ("hemi = np.where(z >= 0.0, 0, 1)", "hemi = np.where(z >= 0.0, 1, 0)"),
+    "iono_no_tube_scaling": ("jr = jpar * (bi / bm) * (br / bi)", "jr = jpar * (br / bi)"),
+    "iono_radial_sign": ("jr = jpar * (bi / bm) * (br / bi)", "jr = -jpar * (bi / bm) * (br / bi)"),
+    "iono_curl_component": ("return dBz_dy - dBy_dz, dBx_dz - dBz_dx, dBy_dx - dBx_dy",
+                            "return dBz_dy - dBy_dz, dBz_dx - dBx_dz, dBy_dx - dBx_dy"),
+    "iono_interp_transpose": ("return (1.0 - fu[idx]) * P[j, k0[idx]] + fu[idx] * P[j, k1[idx]]",
+                              "return (1.0 - fu[idx]) * P[j, k1[idx]] + fu[idx] * P[j, k0[idx]]"),
+    "iono_drift_sign": ("v[0, iz, iy, ix] = np.where(ok, (Ey * bz - Ez * by) / b2, 0.0)",
+                        "v[0, iz, iy, ix] = np.where(ok, (Ez * by - Ey * bz) / b2, 0.0)"),
+    "iono_gradient_span": ("E[d, iz, iy, ix] = -(fp - fm) / (c[hi] - c[lo])",
+                           "E[d, iz, iy, ix] = -(fp - fm) / (2.0 * (c[hi] - c[lo]))"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(IONO_MUTANTS))
+def test_ionosphere_pins_catch_planted_mistake(name, tmp_path):
+    old, new = IONO_MUTANTS[name]
+    src = open(IONO_SRC).read()
+    assert src.count(old) == 1, f"mutation site not unique/found: {name}"
+    mutated = tmp_path / "ionosphere_mut.py"
+    mutated.write_text(src.replace(old, new))
+    env = dict(os.environ, PPMLR_IONO_ORACLE=str(mutated))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "tests/test_oracle_ionosphere.py"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"planted mistake {name} passed every pin:\n{r.stdout[-2000:]}"
