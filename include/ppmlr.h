@@ -218,6 +218,54 @@ ppmlr_status ppmlr_set_riemann_solver(ppmlr_ctx *ctx, int iters);
  * advected contact. */
 ppmlr_status ppmlr_set_steepening(ppmlr_ctx *ctx, int on);
 
+/* Ionosphere shell (Sec. II): a thin conducting sphere at r_iono closes the
+ * field-aligned currents and is tied to the inner boundary by dipole field
+ * lines; its electrostatic potential sets the flow of the inner-sphere cells.
+ * Once per step, before the step's sweeps and from the state at the start of
+ * the step:
+ *   1. J = curl B' at the cell centres (centred differences), sampled with
+ *      B' at the mapping sphere r_fac by trilinear interpolation along the
+ *      dipole field lines of the shell nodes; J_par = J.B/|B|, B = B' + B_d;
+ *   2. down the flux tube J_par scales with |B_d|; the shell takes the radial
+ *      part J_r = J_par(r_iono) B_r/|B| (0 where the line closes below r_fac);
+ *   3. Sigma_P Laplacian Phi = J_r on each polar cap 0 <= theta <= theta_max
+ *      (theta from the cap's own pole, sin^2 theta_max = r_iono / r_inner),
+ *      Phi = 0 at theta_max; cell-centred (n_theta x n_phi) grid, conservative
+ *      five-point spherical Laplacian, solved exactly (Fourier in longitude,
+ *      tridiagonal in colatitude);
+ *   4. Phi carried along the field lines to the neighbours of every inner
+ *      cell (bilinear on the caps, ring mean at the pole, 0 off the caps),
+ *      E = -grad Phi by centred differences, v = E x B_d / |B_d|^2;
+ *   5. every inner cell is reset to (inner rho, rho v, B' = 0,
+ *      p_inner/(gamma-1) + rho v^2/2) instead of the configuration's rest
+ *      state.
+ * The calculation is in FP64 for every precision.  Units: Sigma_P in code
+ * units (mu0 v0 Sigma_SI); radii in R_E. */
+typedef struct {
+    double r_iono;                   /* shell radius, 0 < r_iono < r_inner */
+    double r_fac;                    /* current-mapping radius, r_fac > r_iono */
+    double sigma_p;                  /* Pedersen conductance (code units), > 0 */
+    int n_theta;                     /* colatitude rings per cap, 2..256 */
+    int n_phi;                       /* longitudes, even, 4..1024 */
+} ppmlr_iono;
+/* Turns the shell on (cfg copied) or off (cfg = NULL: the inner cells return
+ * to the configuration's fixed state at the next sweep).  Needs r_inner > 0,
+ * a dipole, and the mapping sphere one cell inside the interior of every axis
+ * (the centres of cells 1 and n-2 bracket [-r_fac, r_fac]).  Allocates
+ * 2 n_theta n_phi x 4 doubles for the caps and 8 doubles per inner cell;
+ * drops the step graphs.  PPMLR_E_INVALID (shell unchanged) otherwise,
+ * PPMLR_E_OOM on allocation failure. */
+ppmlr_status ppmlr_set_ionosphere(ppmlr_ctx *ctx, const ppmlr_iono *cfg);
+/* One ionosphere solve from the current state (what every step does first
+ * while the shell is on), on the context's stream.  PPMLR_E_INVALID when the
+ * shell is off. */
+ppmlr_status ppmlr_ionosphere_solve(ppmlr_ctx *ctx);
+/* Copies the last solve's potential and radial current to host arrays of
+ * 2 * n_theta * n_phi doubles (cap-major: north then south, ring-major,
+ * longitude fastest); either pointer may be NULL.  Synchronises the stream.
+ * PPMLR_E_INVALID when the shell is off. */
+ppmlr_status ppmlr_get_ionosphere(ppmlr_ctx *ctx, double *phi, double *jr);
+
 /* Launch form of each sweep direction (3 entries): 0 = one block per tile
  * reading its input from global memory; 1 = persistent blocks whose input
  * boxes (8 arrays x positions x lanes) are staged into shared memory by the

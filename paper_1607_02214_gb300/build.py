@@ -30,6 +30,7 @@ UNITS = {
     "sweep_fp64_exact.cu": ["-fmad=false"],
     "sweep_mixed.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "cfl_mixed.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
+    "ionosphere.cu": ["-fmad=true"],
 }
 
 

@@ -68,6 +68,17 @@ struct ppmlr_ctx {
     struct Rec { int kind; cudaEvent_t a, b; };
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> pool;
+    // ionosphere shell: the inner cells (ascending linear index, from the
+    // inner mask) and, while the shell is on, its configuration and buffers
+    std::vector<long long> inner_list;
+    struct Iono {
+        bool on;
+        ppmlr_iono cfg;
+        double theta_max, dth, dph;
+        double *buf;                // jr, phi, spec, work, pole
+        long long *cells;           // inner_list on the device
+        double *state;              // 8 x inner_list.size()
+    } iono;
 };
 
 static cudaEvent_t take_event(ppmlr_ctx *c)
@@ -400,8 +411,10 @@ ppmlr_status ppmlr_create(const ppmlr_grid *grid, double gamma, const ppmlr_bc *
         size_t i = 0;
         for (int iz = 0; iz < c->n[2]; iz++)
             for (int iy = 0; iy < c->n[1]; iy++)
-                for (int ix = 0; ix < c->n[0]; ix++, i++)
+                for (int ix = 0; ix < c->n[0]; ix++, i++) {
                     mask[i] = cx[ix] * cx[ix] + cy[iy] * cy[iy] + cz[iz] * cz[iz] < r2 ? 1 : 0;
+                    if (mask[i]) c->inner_list.push_back((long long)i);
+                }
         e = cudaMalloc(&c->inner_mask, mask.size());
         if (e == cudaSuccess) e = cudaMemcpy(c->inner_mask, mask.data(), mask.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
@@ -440,6 +453,9 @@ void ppmlr_destroy(ppmlr_ctx *c)
     if (c->cap) cudaStreamDestroy(c->cap);
     for (auto &r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->pool) cudaEventDestroy(e);
+    cudaFree(c->iono.buf);
+    cudaFree(c->iono.cells);
+    cudaFree(c->iono.state);
     cudaFree(c->bd);
     cudaFree(c->inner_mask);
     cudaFree(c->geof);
@@ -535,6 +551,11 @@ static ppmlr_status launch_one_sweep(ppmlr_ctx *c, int d, double dt, const doubl
     a.bd = c->bd;
     if (c->prec != PPMLR_MIXED) { a.iw = c->iw[d]; a.ih = c->ih[d]; }
     a.inner_mask = c->inner_mask;
+    if (c->iono.on) {
+        a.inner_cells = c->iono.cells;
+        a.inner_state = c->iono.state;
+        a.n_inner = (int)c->inner_list.size();
+    }
     a.flags = c->flags; a.floors = c->floors;
     a.wf = c->wf[d];
     a.cxf = c->cf[0]; a.cyf = c->cf[1]; a.czf = c->cf[2];
@@ -564,8 +585,40 @@ ppmlr_status ppmlr_sweep(ppmlr_ctx *c, int axis, double dt)
     return launch_one_sweep(c, axis, dt, nullptr);
 }
 
+// The ionosphere solve from the current state (five small kernels).
+static ppmlr_status launch_iono(ppmlr_ctx *c)
+{
+    const ppmlr_iono &g = c->iono.cfg;
+    IonoArgs a;
+    memset(&a, 0, sizeof(a));
+    for (int d = 0; d < 3; d++) { a.B[d] = c->U[4 + d]; a.n[d] = c->n[d]; a.c[d] = c->c[d]; }
+    a.M = c->bc.dipole_moment;
+    a.r_iono = g.r_iono; a.r_fac = g.r_fac; a.sigma_p = g.sigma_p;
+    a.theta_max = c->iono.theta_max; a.dth = c->iono.dth; a.dph = c->iono.dph;
+    a.nt = g.n_theta; a.np = g.n_phi;
+    const size_t nodes = 2 * (size_t)g.n_theta * g.n_phi, nm = (size_t)g.n_phi / 2 + 1;
+    a.jr = c->iono.buf;
+    a.phi = a.jr + nodes;
+    a.spec = a.phi + nodes;
+    a.work = a.spec + 2 * (size_t)g.n_theta * nm * 2;
+    a.pole = a.work + 2 * nm * (size_t)g.n_theta;
+    a.inner_cells = c->iono.cells;
+    a.n_inner = (int)c->inner_list.size();
+    a.inner_state = c->iono.state;
+    a.rho_in = c->bc.inner.rho; a.p_in = c->bc.inner.p; a.gamma = c->gamma;
+    int n = 0;
+    cudaError_t e = launch_ionosphere(a, c->stream, &n);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ionosphere launch");
+    c->launches += n;
+    return PPMLR_OK;
+}
+
 static ppmlr_status do_step(ppmlr_ctx *c, double dt, const double *dt_dev)
 {
+    if (c->iono.on) {
+        ppmlr_status s = launch_iono(c);
+        if (s != PPMLR_OK) return s;
+    }
     const int order_even[3] = {0, 1, 2}, order_odd[3] = {2, 1, 0};
     const int *ord = (c->steps & 1) ? order_odd : order_even;
     for (int k = 0; k < 3; k++) {
@@ -784,6 +837,82 @@ ppmlr_status ppmlr_set_riemann_solver(ppmlr_ctx *c, int iters)
     c->riemann_iters = iters;
     drop_graphs(c);
     return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_set_ionosphere(ppmlr_ctx *c, const ppmlr_iono *cfg)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (!cfg) {
+        CK(c, cudaStreamSynchronize(c->stream), "stream sync");
+        cudaFree(c->iono.buf); cudaFree(c->iono.cells); cudaFree(c->iono.state);
+        c->iono = ppmlr_ctx::Iono{};
+        drop_graphs(c);
+        return PPMLR_OK;
+    }
+    const ppmlr_iono g = *cfg;
+    if (!(c->bc.r_inner > 0.0) || c->bc.dipole_moment == 0.0)
+        return fail(c, PPMLR_E_INVALID, "set_ionosphere: needs an inner sphere and a dipole");
+    if (!(g.r_iono > 0.0) || !(g.r_iono < c->bc.r_inner) || !(g.r_fac > g.r_iono) || !isfinite(g.r_fac) ||
+        !(g.sigma_p > 0.0) || !isfinite(g.sigma_p) || g.n_theta < 2 || g.n_theta > 256 || g.n_phi < 4 ||
+        g.n_phi > 1024 || (g.n_phi & 1))
+        return fail(c, PPMLR_E_INVALID, "set_ionosphere: need 0 < r_iono < r_inner < ..., r_fac > r_iono, "
+                                        "sigma_p > 0, 2 <= n_theta <= 256, even 4 <= n_phi <= 1024");
+    for (int d = 0; d < 3; d++) {     // the mapping sphere's curl stencils inside the grid
+        const std::vector<double> &e = c->edges[d];
+        const int n = c->n[d];
+        if (n < 4) return fail(c, PPMLR_E_INVALID, "set_ionosphere: every axis needs at least 4 cells");
+        const double lo = 0.5 * (e[1] + e[2]), hi = 0.5 * (e[n - 2] + e[n - 1]);   // centres 1 and n-2
+        const double rf = g.r_fac * (1.0 + 1e-12);
+        if (!(lo < -rf) || !(rf < hi))
+            return fail(c, PPMLR_E_INVALID, "set_ionosphere: the mapping sphere must lie inside centres 1 .. n-2");
+    }
+    const size_t nodes = 2 * (size_t)g.n_theta * g.n_phi, nm = (size_t)g.n_phi / 2 + 1;
+    const size_t nbuf = 2 * nodes + 2 * (size_t)g.n_theta * nm * 2 + 2 * nm * (size_t)g.n_theta + 2;
+    const size_t ninner = c->inner_list.size();
+    double *buf = nullptr, *state = nullptr;
+    long long *cells = nullptr;
+    cudaError_t e = cudaMalloc(&buf, sizeof(double) * nbuf);
+    if (e == cudaSuccess && ninner) e = cudaMalloc(&cells, sizeof(long long) * ninner);
+    if (e == cudaSuccess && ninner) e = cudaMalloc(&state, sizeof(double) * 8 * ninner);
+    if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0, sizeof(double) * nbuf, c->stream);
+    if (e == cudaSuccess && ninner)
+        e = cudaMemcpyAsync(cells, c->inner_list.data(), sizeof(long long) * ninner, cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaFree(buf); cudaFree(cells); cudaFree(state);
+        return e == cudaErrorMemoryAllocation ? fail(c, PPMLR_E_OOM, "set_ionosphere: out of device memory")
+                                              : cuda_fail(c, e, "set_ionosphere");
+    }
+    cudaFree(c->iono.buf); cudaFree(c->iono.cells); cudaFree(c->iono.state);
+    c->iono.on = true;
+    c->iono.cfg = g;
+    c->iono.theta_max = asin(sqrt(g.r_iono / c->bc.r_inner));
+    c->iono.dth = c->iono.theta_max / g.n_theta;
+    c->iono.dph = 2.0 * M_PI / g.n_phi;
+    c->iono.buf = buf; c->iono.cells = cells; c->iono.state = state;
+    drop_graphs(c);
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_ionosphere_solve(ppmlr_ctx *c)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (!c->iono.on) return fail(c, PPMLR_E_INVALID, "ionosphere_solve: the shell is off");
+    return launch_iono(c);
+}
+
+ppmlr_status ppmlr_get_ionosphere(ppmlr_ctx *c, double *phi, double *jr)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (!c->iono.on) return fail(c, PPMLR_E_INVALID, "get_ionosphere: the shell is off");
+    const size_t nodes = 2 * (size_t)c->iono.cfg.n_theta * c->iono.cfg.n_phi;
+    if (jr) CK(c, cudaMemcpyAsync(jr, c->iono.buf, sizeof(double) * nodes, cudaMemcpyDeviceToHost, c->stream), "copy");
+    if (phi)
+        CK(c, cudaMemcpyAsync(phi, c->iono.buf + nodes, sizeof(double) * nodes, cudaMemcpyDeviceToHost, c->stream),
+           "copy");
+    CK(c, cudaStreamSynchronize(c->stream), "stream sync");
+    return read_flags(c);
 }
 
 ppmlr_status ppmlr_set_steepening(ppmlr_ctx *c, int on)

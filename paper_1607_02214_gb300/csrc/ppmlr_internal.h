@@ -46,6 +46,11 @@ struct SweepArgs {
     const double *bd;          // FP64 forms: dipole table (component k at bd + k * vs + cell) or null
     const double *iw, *ih;     // FP64 forms: 1 / width and 1 / (w_-/2 + w + w_+/2) along the axis, or null
     const unsigned char *inner_mask;   // per cell: 1 inside the inner sphere, or null
+    // ionosphere shell on: sorted linear indices of the inner cells and their
+    // conserved states (array v at inner_state + v * n_inner); null otherwise
+    const long long *inner_cells;
+    const double *inner_state;
+    int n_inner;
     int *flags;
     unsigned long long *floors;
     // float copies for the mixed path (geometry and parameters)
@@ -96,6 +101,26 @@ struct CflArgs {
     const double *iw[3];       // contracted FP64 form: ghost-extended reciprocal widths, or null
     const unsigned char *inner_mask;   // per cell: 1 inside the inner sphere, or null
 };
+
+// One ionosphere solve (ionosphere.cu): state, geometry, cap grid and the
+// device buffers it fills.
+struct IonoArgs {
+    const double *B[3];        // B' of the state (arrays 4..6)
+    int n[3];
+    const double *c[3];        // ghost-extended cell centres of each axis
+    double M, r_iono, r_fac, sigma_p, theta_max, dth, dph;
+    int nt, np;                // rings and longitudes per cap
+    double *jr;                // 2 * nt * np: radial current per cap node
+    double *phi;               // 2 * nt * np: potential
+    double *spec;              // 2 * nt * (np/2 + 1) * 2: Fourier coefficients
+    double *work;              // 2 * (np/2 + 1) * nt: tridiagonal scratch
+    double *pole;              // 2: ring-0 mean per cap
+    const long long *inner_cells;
+    int n_inner;
+    double *inner_state;       // 8 * n_inner
+    double rho_in, p_in, gamma;
+};
+cudaError_t launch_ionosphere(const IonoArgs &a, cudaStream_t s, int *launches);
 
 // Tile shape of one sweep direction.
 struct Tile {

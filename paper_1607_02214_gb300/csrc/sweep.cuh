@@ -1045,6 +1045,18 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
                 inner = x * x + y * y + z * z < a.r_inner * a.r_inner;
             }
         }
+        if (inner && a.inner_cells) {     // the ionosphere's state of this cell
+            int lo = 0, hi = a.n_inner - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (a.inner_cells[mid] < gi) lo = mid + 1; else hi = mid;
+            }
+            if (a.inner_cells[lo] == gi) {
+#pragma unroll
+                for (int v = 0; v < 8; v++) Un[v] = a.inner_state[(long long)v * a.n_inner + lo];
+                inner = false;
+            }
+        }
         if (inner) {
             const auto *q = a.inner;
             double rh = q[0];

@@ -39,6 +39,11 @@ class ppmlr_bc(ctypes.Structure):
                 ("r_inner", c_double), ("inner", ppmlr_prim), ("p_min", c_double), ("powell", c_int)]
 
 
+class ppmlr_iono(ctypes.Structure):
+    _fields_ = [("r_iono", c_double), ("r_fac", c_double), ("sigma_p", c_double), ("n_theta", c_int),
+                ("n_phi", c_int)]
+
+
 DPTR8 = POINTER(c_double) * 8
 
 # (name, restype, argtypes) of every exported function
@@ -68,6 +73,9 @@ SIGNATURES = [
     ("ppmlr_run", c_int, [c_void_p, c_double, c_longlong, c_int]),
     ("ppmlr_set_riemann_solver", c_int, [c_void_p, c_int]),
     ("ppmlr_set_steepening", c_int, [c_void_p, c_int]),
+    ("ppmlr_set_ionosphere", c_int, [c_void_p, POINTER(ppmlr_iono)]),
+    ("ppmlr_ionosphere_solve", c_int, [c_void_p]),
+    ("ppmlr_get_ionosphere", c_int, [c_void_p, POINTER(c_double), POINTER(c_double)]),
     ("ppmlr_ensemble_set_steepening", c_int, [c_void_p, c_int]),
     ("ppmlr_get_time", c_int, [c_void_p, POINTER(c_double)]),
     ("ppmlr_set_time", c_int, [c_void_p, c_double]),
@@ -282,6 +290,29 @@ class Context:
     def set_steepening(self, on):
         """Contact steepening of the remapped densities (default off)."""
         return self._check(load().ppmlr_set_steepening(self._h, int(bool(on))))
+
+    def set_ionosphere(self, r_iono=1.017, r_fac=4.0, sigma_p=0.6283, n_theta=24, n_phi=48, on=True):
+        """Ionosphere shell coupled to the inner boundary (on=False: off).
+        sigma_p in code units (mu0 v0 Sigma_SI: 0.6283 is 5 S)."""
+        if not on:
+            return self._check(load().ppmlr_set_ionosphere(self._h, None))
+        cfg = ppmlr_iono(float(r_iono), float(r_fac), float(sigma_p), int(n_theta), int(n_phi))
+        self._iono = (int(n_theta), int(n_phi))
+        return self._check(load().ppmlr_set_ionosphere(self._h, ctypes.byref(cfg)))
+
+    def ionosphere_solve(self):
+        """One shell solve from the current state (each step does one first)."""
+        return self._check(load().ppmlr_ionosphere_solve(self._h))
+
+    def get_ionosphere(self):
+        """(phi, jr) of the last solve, each (2, n_theta, n_phi): north cap
+        then south, colatitude rings, longitude fastest."""
+        nt, npp = self._iono
+        phi = np.empty((2, nt, npp))
+        jr = np.empty((2, nt, npp))
+        self._check(load().ppmlr_get_ionosphere(self._h, phi.ctypes.data_as(POINTER(c_double)),
+                                                jr.ctypes.data_as(POINTER(c_double))))
+        return phi, jr
 
     def run(self, cfl, nsteps, graph_steps=16):
         """nsteps device-dt steps (as step_cfl), replayed from CUDA graphs of
