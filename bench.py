@@ -200,15 +200,24 @@ def workload(args):
     h0 = 0.4 * 256 / n[0] if args.h0 is None else args.h0
     prob = inputs.magnetosphere(n=n, h0=h0)
     name = f"magnetosphere_{n[0]}x{n[1]}x{n[2]}_h0_{h0:g}_{args.precision}"
+    if getattr(args, "ionosphere", False):
+        name += "_ionosphere"
     return prob, name
 
 
+# the ionosphere shell of --ionosphere and of the bench's shell section
+SHELL = dict(r_iono=1.017, r_fac=4.0, sigma_p=0.6283, n_theta=24, n_phi=48)
+
+
 def config_dict(prob, name, args, world):
-    return {"workload": name, "grid": list(prob.n), "cells": prob.cells, "cfl": prob.cfl,
-            "x_range_re": [-100, 30], "yz_range_re": [-60, 60], "dipole": True, "r_inner_re": 3.0,
-            "inflow": "n=5 cm^-3, vx=-400 km/s, T=1e5 K, Bz=-5 nT", "precision": args.precision,
-            "l2": "state 604 MB per copy > 129 MB L2: inputs larger than L2, no flush",
-            "parallelism": f"replicas x{world}"}
+    d = {"workload": name, "grid": list(prob.n), "cells": prob.cells, "cfl": prob.cfl,
+         "x_range_re": [-100, 30], "yz_range_re": [-60, 60], "dipole": True, "r_inner_re": 3.0,
+         "inflow": "n=5 cm^-3, vx=-400 km/s, T=1e5 K, Bz=-5 nT", "precision": args.precision,
+         "l2": "state 604 MB per copy > 129 MB L2: inputs larger than L2, no flush",
+         "parallelism": f"replicas x{world}"}
+    if getattr(args, "ionosphere", False):
+        d["ionosphere_shell"] = SHELL
+    return d
 
 
 # ------------------------------------------------------------ reference -------
@@ -289,11 +298,13 @@ def run_ours(args, rank, world, dist):
     def max_ranks(x):
         return max_over_ranks(x, dist, "cuda")
 
-    def timed_run(precision, steps, warmup, with_clocks=False, riemann_iters=0, steepen=False):
+    def timed_run(precision, steps, warmup, with_clocks=False, riemann_iters=0, steepen=False, iono=None):
         ctx = ppmlr.Context.from_problem(prob, precision)
         ctx.set_state(U0)
         ctx.set_riemann_solver(riemann_iters)
         ctx.set_steepening(steepen)
+        if iono:
+            ctx.set_ionosphere(**iono)
         if args.launch_config and precision == prec:
             for axis, (C, L, form) in enumerate(args.launch_config):
                 ctx.set_tiles(axis, C, L)
@@ -327,7 +338,8 @@ def run_ours(args, rank, world, dist):
         return ctx, ms, kern, launches, (sampler.summary() if sampler else None)
 
     # ---- main measurement
-    ctx, ms, kern, launches, clocks = timed_run(prec, args.steps, args.warmup, with_clocks=True)
+    ctx, ms, kern, launches, clocks = timed_run(prec, args.steps, args.warmup, with_clocks=True,
+                                                iono=SHELL if args.ionosphere else None)
     ms = max_ranks(ms)
     value = throughput(world * cells, args.steps, ms)
     log(f"[bench] {name}: {ms / args.steps:.3f} ms/step, {value:.4e} cell-updates/s, kernels {kern}")
@@ -428,6 +440,35 @@ def run_ours(args, rank, world, dist):
             st[key] = {"value": world * cells * nsteps / (sms * 1e-3), "ms_per_step": sms / nsteps}
             sctx.close()
         extra["contact_steepening"] = st
+        if prob.bc.r_inner > 0.0 and prob.bc.dipole_moment != 0.0:
+            # the ionosphere shell coupled to the inner boundary: step cost and
+            # the solve alone (CUDA events around repeated solves)
+            from paper_1607_02214_gb300 import inputs
+            cfg = SHELL
+            io = {"config": dict(cfg, sigma_p_siemens=5.0)}
+            for key, p in (("fp64", ppmlr.PPMLR_FP64), ("mixed", ppmlr.PPMLR_MIXED)):
+                nsteps = max(3, args.steps // 4) if key == "fp64" else args.steps
+                ictx, ims, _, ilaunch, _ = timed_run(p, nsteps, args.warmup, iono=cfg)
+                ims = max_ranks(ims)
+                io[key] = {"value": world * cells * nsteps / (ims * 1e-3), "ms_per_step": ims / nsteps,
+                           "gpu_launches_per_step": ilaunch / nsteps}
+                if key == "fp64":
+                    stream = torch.cuda.current_stream()
+                    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    for _ in range(3):
+                        ictx.ionosphere_solve()
+                    reps = 50
+                    a0.record(stream)
+                    for _ in range(reps):
+                        ictx.ionosphere_solve()
+                    a1.record(stream)
+                    a1.synchronize()
+                    io["solve_ms"] = a0.elapsed_time(a1) / reps
+                    phi, jr = ictx.get_ionosphere()
+                    io["cross_cap_potential_kV"] = float((phi[0].max() - phi[0].min()) * inputs.V0 *
+                                                         inputs.B_UNIT_NT * 1e-9 * 6.371e6 * 1e-3)
+                ictx.close()
+            extra["ionosphere_shell"] = io
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -677,6 +718,8 @@ def main():
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-steady", action="store_true", help="skip the long graph-replayed run")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--ionosphere", action="store_true",
+                    help="main measurement with the ionosphere shell coupled to the inner boundary")
     ap.add_argument("--launch-config", type=parse_launch_config, default=None,
                     help="fixed tiles and launch forms of the main precision instead of the autotuner: "
                          "C,L,form for x:y:z, e.g. 256,1,0:64,4,2:64,4,2")

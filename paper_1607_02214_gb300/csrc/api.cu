@@ -8,6 +8,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -61,6 +62,10 @@ struct ppmlr_ctx {
     // parity, input buffer, length and CFL number; dropped when the tiles or
     // launch forms change
     cudaStream_t cap;
+    // with the ionosphere shell on, device-dt steps run the shell's solve on
+    // `side` concurrently with the CFL pass (fork / join events)
+    cudaStream_t side;
+    cudaEvent_t ev_fork, ev_join;
     struct Graph { int parity, buf, ksteps; double cfl; cudaGraphExec_t exec; long long launches; };
     std::vector<Graph> graphs;
     // per-kernel timing records (kind, start, stop) and a pool of spare events
@@ -74,8 +79,9 @@ struct ppmlr_ctx {
     struct Iono {
         bool on;
         ppmlr_iono cfg;
-        double theta_max, dth, dph;
-        double *buf;                // jr, phi, spec, work, pole
+        double *buf;                // jr, phi, spectra, poles, solve tables (IonoLayout)
+        IonoNode *nodes;            // per cap node
+        IonoInner *inner;           // per inner cell
         long long *cells;           // inner_list on the device
         double *state;              // 8 x inner_list.size()
     } iono;
@@ -451,11 +457,13 @@ void ppmlr_destroy(ppmlr_ctx *c)
     cudaStreamSynchronize(c->stream);
     drop_graphs(c);
     if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     for (auto &r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->pool) cudaEventDestroy(e);
-    cudaFree(c->iono.buf);
-    cudaFree(c->iono.cells);
-    cudaFree(c->iono.state);
+    cudaFree(c->iono.buf); cudaFree(c->iono.cells); cudaFree(c->iono.state);
+    cudaFree(c->iono.nodes); cudaFree(c->iono.inner);
     cudaFree(c->bd);
     cudaFree(c->inner_mask);
     cudaFree(c->geof);
@@ -585,38 +593,50 @@ ppmlr_status ppmlr_sweep(ppmlr_ctx *c, int axis, double dt)
     return launch_one_sweep(c, axis, dt, nullptr);
 }
 
-// The ionosphere solve from the current state (five small kernels).
-static ppmlr_status launch_iono(ppmlr_ctx *c)
+// Device buffer of the shell (doubles): jr, phi (2 nt np each), Fourier
+// coefficients (2 nt (np/2+1) x 2), poles (2), then the host tables: twiddles
+// (2 np), colatitude rows (4 nt), mode eigenvalues (np/2+1).
+struct IonoLayout {
+    size_t nodes, nm, jr, phi, spec, pole, tw, rows, lam, total;
+    explicit IonoLayout(const ppmlr_iono &g)
+    {
+        nodes = 2 * (size_t)g.n_theta * g.n_phi;
+        nm = (size_t)g.n_phi / 2 + 1;
+        jr = 0; phi = jr + nodes; spec = phi + nodes; pole = spec + 2 * (size_t)g.n_theta * nm * 2;
+        tw = pole + 2; rows = tw + 2 * (size_t)g.n_phi; lam = rows + 4 * (size_t)g.n_theta; total = lam + nm;
+    }
+};
+
+// The ionosphere solve from the current state (five small kernels) on stream s.
+static ppmlr_status launch_iono(ppmlr_ctx *c, cudaStream_t s)
 {
     const ppmlr_iono &g = c->iono.cfg;
+    const IonoLayout L(g);
     IonoArgs a;
     memset(&a, 0, sizeof(a));
     for (int d = 0; d < 3; d++) { a.B[d] = c->U[4 + d]; a.n[d] = c->n[d]; a.c[d] = c->c[d]; }
-    a.M = c->bc.dipole_moment;
-    a.r_iono = g.r_iono; a.r_fac = g.r_fac; a.sigma_p = g.sigma_p;
-    a.theta_max = c->iono.theta_max; a.dth = c->iono.dth; a.dph = c->iono.dph;
+    a.r_iono = g.r_iono; a.sigma_p = g.sigma_p;
     a.nt = g.n_theta; a.np = g.n_phi;
-    const size_t nodes = 2 * (size_t)g.n_theta * g.n_phi, nm = (size_t)g.n_phi / 2 + 1;
-    a.jr = c->iono.buf;
-    a.phi = a.jr + nodes;
-    a.spec = a.phi + nodes;
-    a.work = a.spec + 2 * (size_t)g.n_theta * nm * 2;
-    a.pole = a.work + 2 * nm * (size_t)g.n_theta;
-    a.inner_cells = c->iono.cells;
+    a.nodes = c->iono.nodes;
+    double *b = c->iono.buf;
+    a.jr = b + L.jr; a.phi = b + L.phi; a.spec = b + L.spec; a.pole = b + L.pole;
+    a.tw = b + L.tw; a.rows = b + L.rows; a.lam = b + L.lam;
+    a.inner = c->iono.inner;
     a.n_inner = (int)c->inner_list.size();
     a.inner_state = c->iono.state;
     a.rho_in = c->bc.inner.rho; a.p_in = c->bc.inner.p; a.gamma = c->gamma;
     int n = 0;
-    cudaError_t e = launch_ionosphere(a, c->stream, &n);
+    cudaError_t e = launch_ionosphere(a, s, &n);
     if (e != cudaSuccess) return cuda_fail(c, e, "ionosphere launch");
     c->launches += n;
     return PPMLR_OK;
 }
 
-static ppmlr_status do_step(ppmlr_ctx *c, double dt, const double *dt_dev)
+// shell_done: the step's ionosphere solve is already on the stream
+static ppmlr_status do_step(ppmlr_ctx *c, double dt, const double *dt_dev, bool shell_done = false)
 {
-    if (c->iono.on) {
-        ppmlr_status s = launch_iono(c);
+    if (c->iono.on && !shell_done) {
+        ppmlr_status s = launch_iono(c, c->stream);
         if (s != PPMLR_OK) return s;
     }
     const int order_even[3] = {0, 1, 2}, order_odd[3] = {2, 1, 0};
@@ -674,12 +694,33 @@ ppmlr_status ppmlr_cfl_dt(ppmlr_ctx *c, double cfl, double *dt_out)
     return read_flags(c);
 }
 
+// One device-dt step: the CFL pass and, with the shell on, the shell's solve
+// on the side stream at the same time (both only read the state), joined
+// before the first sweep; then the three sweeps.
+static ppmlr_status cfl_step(ppmlr_ctx *c, double cfl)
+{
+    if (!c->iono.on) {
+        ppmlr_status s = launch_cfl_kernel(c, cfl, true);
+        return s != PPMLR_OK ? s : do_step(c, 0.0, c->dt_dev);
+    }
+    if (!c->side) CK(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "side stream");
+    if (!c->ev_fork) CK(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "event");
+    if (!c->ev_join) CK(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event");
+    CK(c, cudaEventRecord(c->ev_fork, c->stream), "fork");
+    CK(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork");
+    ppmlr_status s = launch_iono(c, c->side);
+    if (s != PPMLR_OK) return s;
+    CK(c, cudaEventRecord(c->ev_join, c->side), "join");
+    s = launch_cfl_kernel(c, cfl, true);
+    if (s != PPMLR_OK) return s;
+    CK(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0), "join");
+    return do_step(c, 0.0, c->dt_dev, true);
+}
+
 static ppmlr_status step_cfl_direct(ppmlr_ctx *c, double cfl, long long nsteps)
 {
     for (long long k = 0; k < nsteps; k++) {
-        ppmlr_status s = launch_cfl_kernel(c, cfl, true);
-        if (s != PPMLR_OK) return s;
-        s = do_step(c, 0.0, c->dt_dev);
+        ppmlr_status s = cfl_step(c, cfl);
         if (s != PPMLR_OK) return s;
     }
     return PPMLR_OK;
@@ -839,13 +880,73 @@ ppmlr_status ppmlr_set_riemann_solver(ppmlr_ctx *c, int iters)
     return PPMLR_OK;
 }
 
+static void free_iono(ppmlr_ctx *c)
+{
+    cudaFree(c->iono.buf); cudaFree(c->iono.cells); cudaFree(c->iono.state);
+    cudaFree(c->iono.nodes); cudaFree(c->iono.inner);
+    c->iono = ppmlr_ctx::Iono{};
+}
+
+// Earth dipole along -z (host): B = M (3 (m.r) r - m r^2) / r^5, m = -z.
+static void dipole_host(double M, double x, double y, double z, double *B)
+{
+    const double r2 = x * x + y * y + z * z;
+    if (M == 0.0 || r2 == 0.0) { B[0] = B[1] = B[2] = 0.0; return; }
+    const double f = M / (r2 * r2 * sqrt(r2));
+    B[0] = f * (3.0 * -z * x);
+    B[1] = f * (3.0 * -z * y);
+    B[2] = f * (3.0 * -z * z + r2);
+}
+
+// Bilinear stencil of the cap potential at the foot point of the dipole field
+// line through (x, y, z): up to 4 (node, weight) pairs (node -1 - cap: that
+// cap's pole value, the ring-0 mean); none off the caps or where the line
+// closes below the shell.  Returns the number of pairs.
+static int cap_stencil(const ppmlr_iono &g, double theta_max, double dth, double dph, double x, double y, double z,
+                       int *idx, double *w)
+{
+    const double r2 = x * x + y * y + z * z;
+    if (r2 == 0.0) return 0;
+    const double r = sqrt(r2);
+    const double s2i = (g.r_iono / r) * ((x * x + y * y) / r2);
+    if (s2i > 1.0) return 0;
+    const double th = asin(sqrt(s2i));
+    if (!(th < theta_max)) return 0;
+    double ph = atan2(y, x);
+    if (ph < 0.0) ph += 2.0 * M_PI;
+    const int h = z >= 0.0 ? 0 : 1, nt = g.n_theta, np = g.n_phi;
+    const double u = ph / dph, fl = floor(u);
+    const int k0 = ((int)fl % np + np) % np, k1 = (k0 + 1) % np;
+    const double fu = u - fl;
+    int n = 0;
+    auto ring = [&](int j, double wr) {
+        if (j < 0) { idx[n] = -1 - h; w[n++] = wr; return; }
+        if (j >= nt) return;
+        const int base = (h * nt + j) * np;
+        idx[n] = base + k0; w[n++] = wr * (1.0 - fu);
+        idx[n] = base + k1; w[n++] = wr * fu;
+    };
+    const double t = th / dth - 0.5;
+    if (t < 0.0) {
+        const double q = (t + 0.5) / 0.5;
+        ring(-1, 1.0 - q);
+        ring(0, q);
+    } else if (t > nt - 1) {
+        ring(nt - 1, 1.0 - (t - (nt - 1)) / 0.5);
+    } else {
+        const int j = (int)floor(t);
+        ring(j, 1.0 - (t - j));
+        ring(j + 1, t - j);
+    }
+    return n;
+}
+
 ppmlr_status ppmlr_set_ionosphere(ppmlr_ctx *c, const ppmlr_iono *cfg)
 {
     if (!c) return PPMLR_E_INVALID;
     if (!cfg) {
         CK(c, cudaStreamSynchronize(c->stream), "stream sync");
-        cudaFree(c->iono.buf); cudaFree(c->iono.cells); cudaFree(c->iono.state);
-        c->iono = ppmlr_ctx::Iono{};
+        free_iono(c);
         drop_graphs(c);
         return PPMLR_OK;
     }
@@ -853,44 +954,135 @@ ppmlr_status ppmlr_set_ionosphere(ppmlr_ctx *c, const ppmlr_iono *cfg)
     if (!(c->bc.r_inner > 0.0) || c->bc.dipole_moment == 0.0)
         return fail(c, PPMLR_E_INVALID, "set_ionosphere: needs an inner sphere and a dipole");
     if (!(g.r_iono > 0.0) || !(g.r_iono < c->bc.r_inner) || !(g.r_fac > g.r_iono) || !isfinite(g.r_fac) ||
-        !(g.sigma_p > 0.0) || !isfinite(g.sigma_p) || g.n_theta < 2 || g.n_theta > 256 || g.n_phi < 4 ||
+        !(g.sigma_p > 0.0) || !isfinite(g.sigma_p) || g.n_theta < 2 || g.n_theta > IONO_MAX_NT || g.n_phi < 4 ||
         g.n_phi > 1024 || (g.n_phi & 1))
-        return fail(c, PPMLR_E_INVALID, "set_ionosphere: need 0 < r_iono < r_inner < ..., r_fac > r_iono, "
-                                        "sigma_p > 0, 2 <= n_theta <= 256, even 4 <= n_phi <= 1024");
+        return fail(c, PPMLR_E_INVALID, "set_ionosphere: need 0 < r_iono < r_inner, r_fac > r_iono, sigma_p > 0, "
+                                        "2 <= n_theta <= 256, even 4 <= n_phi <= 1024");
+    std::vector<double> ce[3];        // interior centres
     for (int d = 0; d < 3; d++) {     // the mapping sphere's curl stencils inside the grid
         const std::vector<double> &e = c->edges[d];
         const int n = c->n[d];
         if (n < 4) return fail(c, PPMLR_E_INVALID, "set_ionosphere: every axis needs at least 4 cells");
-        const double lo = 0.5 * (e[1] + e[2]), hi = 0.5 * (e[n - 2] + e[n - 1]);   // centres 1 and n-2
+        ce[d].resize(n);
+        for (int i = 0; i < n; i++) ce[d][i] = 0.5 * (e[i] + e[i + 1]);
         const double rf = g.r_fac * (1.0 + 1e-12);
-        if (!(lo < -rf) || !(rf < hi))
+        if (!(ce[d][1] < -rf) || !(rf < ce[d][n - 2]))
             return fail(c, PPMLR_E_INVALID, "set_ionosphere: the mapping sphere must lie inside centres 1 .. n-2");
     }
-    const size_t nodes = 2 * (size_t)g.n_theta * g.n_phi, nm = (size_t)g.n_phi / 2 + 1;
-    const size_t nbuf = 2 * nodes + 2 * (size_t)g.n_theta * nm * 2 + 2 * nm * (size_t)g.n_theta + 2;
+    const IonoLayout L(g);
+    const double M = c->bc.dipole_moment;
+    const double theta_max = asin(sqrt(g.r_iono / c->bc.r_inner));
+    const double dth = theta_max / g.n_theta, dph = 2.0 * M_PI / g.n_phi;
+    // cap solve tables: twiddles, colatitude rows (conservative five-point
+    // form on the unit sphere, no flux through the pole, odd ghost at
+    // theta_max), eigenvalues of the longitude second difference
+    std::vector<double> tab(L.total - L.tw);
+    for (int q = 0; q < g.n_phi; q++) {
+        tab[2 * q] = cos(2.0 * M_PI * q / g.n_phi);
+        tab[2 * q + 1] = sin(2.0 * M_PI * q / g.n_phi);
+    }
+    double *rows = tab.data() + (L.rows - L.tw);
+    for (int j = 0; j < g.n_theta; j++) {
+        const double th = (j + 0.5) * dth, s = sin(th);
+        const double sp = sin(th + 0.5 * dth), sm = j > 0 ? sin(th - 0.5 * dth) : 0.0;
+        rows[4 * j] = sm / (s * dth * dth);
+        rows[4 * j + 1] = j < g.n_theta - 1 ? sp / (s * dth * dth) : 0.0;
+        rows[4 * j + 2] = -(sp + sm) / (s * dth * dth) - (j == g.n_theta - 1 ? sp / (s * dth * dth) : 0.0);
+        rows[4 * j + 3] = 1.0 / (s * s);
+    }
+    double *lam = tab.data() + (L.lam - L.tw);
+    for (size_t m = 0; m < L.nm; m++) {
+        const double sn = sin(M_PI * (double)m / g.n_phi);
+        lam[m] = 4.0 * sn * sn / (dph * dph);
+    }
+    // per node: mapping point along the node's dipole field line at r_fac
+    std::vector<IonoNode> nodes(L.nodes);
+    for (int h = 0; h < 2; h++)
+        for (int j = 0; j < g.n_theta; j++)
+            for (int k = 0; k < g.n_phi; k++) {
+                IonoNode &q = nodes[((size_t)h * g.n_theta + j) * g.n_phi + k];
+                for (int d = 0; d < 3; d++) { q.i0[d] = 1; q.w[d] = 0.0; q.Bd[d] = 0.0; }
+                q.factor = 0.0;
+                const double th = (j + 0.5) * dth, ph = k * dph, st = sin(th), ct = cos(th);
+                const double s2m = (g.r_fac / g.r_iono) * st * st;       // sin^2 at r_fac, same line
+                if (s2m > 1.0) continue;
+                const double zs = h == 0 ? 1.0 : -1.0, sp = sin(ph), cp = cos(ph);
+                const double sm = sqrt(s2m), cm = sqrt(1.0 - s2m);
+                const double p[3] = {g.r_fac * sm * cp, g.r_fac * sm * sp, zs * g.r_fac * cm};
+                for (int d = 0; d < 3; d++) {
+                    const std::vector<double> &cc = ce[d];
+                    int i = (int)(std::upper_bound(cc.begin(), cc.end(), p[d]) - cc.begin()) - 1;
+                    i = i < 1 ? 1 : (i > c->n[d] - 3 ? c->n[d] - 3 : i);
+                    q.i0[d] = i;
+                    q.w[d] = (p[d] - cc[i]) / (cc[i + 1] - cc[i]);
+                }
+                dipole_host(M, p[0], p[1], p[2], q.Bd);
+                const double f[3] = {g.r_iono * st * cp, g.r_iono * st * sp, zs * g.r_iono * ct};
+                double Bf[3];
+                dipole_host(M, f[0], f[1], f[2], Bf);
+                const double br = (Bf[0] * f[0] + Bf[1] * f[1] + Bf[2] * f[2]) / g.r_iono;
+                q.factor = br / sqrt(q.Bd[0] * q.Bd[0] + q.Bd[1] * q.Bd[1] + q.Bd[2] * q.Bd[2]);
+            }
+    // per inner cell: stencils of its six neighbours, E = -grad Phi folded in
     const size_t ninner = c->inner_list.size();
+    std::vector<IonoInner> inner(ninner);
+    for (size_t t = 0; t < ninner; t++) {
+        const long long gi = c->inner_list[t];
+        const int id[3] = {(int)(gi % c->n[0]), (int)((gi / c->n[0]) % c->n[1]),
+                           (int)(gi / ((long long)c->n[0] * c->n[1]))};
+        const double x0[3] = {ce[0][id[0]], ce[1][id[1]], ce[2][id[2]]};
+        IonoInner &q = inner[t];
+        for (int d = 0; d < 3; d++) {
+            for (int s = 0; s < 8; s++) { q.idx[d][s] = 0; q.coef[d][s] = 0.0; }
+            const int lo = id[d] > 0 ? id[d] - 1 : 0, hi = id[d] < c->n[d] - 1 ? id[d] + 1 : c->n[d] - 1;
+            const double span = ce[d][hi] - ce[d][lo];
+            for (int side = 0; side < 2; side++) {
+                double pt[3] = {x0[0], x0[1], x0[2]};
+                pt[d] = ce[d][side == 0 ? hi : lo];
+                int ix[4];
+                double wv[4];
+                const int m = cap_stencil(g, theta_max, dth, dph, pt[0], pt[1], pt[2], ix, wv);
+                for (int s = 0; s < m; s++) {
+                    q.idx[d][4 * side + s] = ix[s];
+                    q.coef[d][4 * side + s] = (side == 0 ? -wv[s] : wv[s]) / span;
+                }
+            }
+        }
+        double B[3];
+        dipole_host(M, x0[0], x0[1], x0[2], B);
+        const double b2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+        for (int d = 0; d < 3; d++) q.bt[d] = b2 > 0.0 ? B[d] / b2 : 0.0;
+    }
     double *buf = nullptr, *state = nullptr;
     long long *cells = nullptr;
-    cudaError_t e = cudaMalloc(&buf, sizeof(double) * nbuf);
+    IonoNode *dnodes = nullptr;
+    IonoInner *dinner = nullptr;
+    cudaError_t e = cudaMalloc(&buf, sizeof(double) * L.total);
+    if (e == cudaSuccess) e = cudaMalloc(&dnodes, sizeof(IonoNode) * nodes.size());
     if (e == cudaSuccess && ninner) e = cudaMalloc(&cells, sizeof(long long) * ninner);
     if (e == cudaSuccess && ninner) e = cudaMalloc(&state, sizeof(double) * 8 * ninner);
-    if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0, sizeof(double) * nbuf, c->stream);
+    if (e == cudaSuccess && ninner) e = cudaMalloc(&dinner, sizeof(IonoInner) * ninner);
+    if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0, sizeof(double) * L.total, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(buf + L.tw, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dnodes, nodes.data(), sizeof(IonoNode) * nodes.size(), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && ninner)
         e = cudaMemcpyAsync(cells, c->inner_list.data(), sizeof(long long) * ninner, cudaMemcpyHostToDevice,
                             c->stream);
+    if (e == cudaSuccess && ninner)
+        e = cudaMemcpyAsync(dinner, inner.data(), sizeof(IonoInner) * ninner, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
-        cudaFree(buf); cudaFree(cells); cudaFree(state);
+        cudaFree(buf); cudaFree(cells); cudaFree(state); cudaFree(dnodes); cudaFree(dinner);
         return e == cudaErrorMemoryAllocation ? fail(c, PPMLR_E_OOM, "set_ionosphere: out of device memory")
                                               : cuda_fail(c, e, "set_ionosphere");
     }
-    cudaFree(c->iono.buf); cudaFree(c->iono.cells); cudaFree(c->iono.state);
+    free_iono(c);
     c->iono.on = true;
     c->iono.cfg = g;
-    c->iono.theta_max = asin(sqrt(g.r_iono / c->bc.r_inner));
-    c->iono.dth = c->iono.theta_max / g.n_theta;
-    c->iono.dph = 2.0 * M_PI / g.n_phi;
     c->iono.buf = buf; c->iono.cells = cells; c->iono.state = state;
+    c->iono.nodes = dnodes; c->iono.inner = dinner;
     drop_graphs(c);
     return PPMLR_OK;
 }
@@ -899,17 +1091,19 @@ ppmlr_status ppmlr_ionosphere_solve(ppmlr_ctx *c)
 {
     if (!c) return PPMLR_E_INVALID;
     if (!c->iono.on) return fail(c, PPMLR_E_INVALID, "ionosphere_solve: the shell is off");
-    return launch_iono(c);
+    return launch_iono(c, c->stream);
 }
 
 ppmlr_status ppmlr_get_ionosphere(ppmlr_ctx *c, double *phi, double *jr)
 {
     if (!c) return PPMLR_E_INVALID;
     if (!c->iono.on) return fail(c, PPMLR_E_INVALID, "get_ionosphere: the shell is off");
-    const size_t nodes = 2 * (size_t)c->iono.cfg.n_theta * c->iono.cfg.n_phi;
-    if (jr) CK(c, cudaMemcpyAsync(jr, c->iono.buf, sizeof(double) * nodes, cudaMemcpyDeviceToHost, c->stream), "copy");
+    const IonoLayout L(c->iono.cfg);
+    if (jr)
+        CK(c, cudaMemcpyAsync(jr, c->iono.buf + L.jr, sizeof(double) * L.nodes, cudaMemcpyDeviceToHost, c->stream),
+           "copy");
     if (phi)
-        CK(c, cudaMemcpyAsync(phi, c->iono.buf + nodes, sizeof(double) * nodes, cudaMemcpyDeviceToHost, c->stream),
+        CK(c, cudaMemcpyAsync(phi, c->iono.buf + L.phi, sizeof(double) * L.nodes, cudaMemcpyDeviceToHost, c->stream),
            "copy");
     CK(c, cudaStreamSynchronize(c->stream), "stream sync");
     return read_flags(c);
@@ -1025,10 +1219,7 @@ static ppmlr_status capture_run_graph(ppmlr_ctx *c, double cfl, int ksteps, ppml
     c->stream = c->cap;
     cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
     ppmlr_status st = e == cudaSuccess ? PPMLR_OK : cuda_fail(c, e, "begin capture");
-    for (int k = 0; st == PPMLR_OK && k < ksteps; k++) {
-        st = launch_cfl_kernel(c, cfl, true);
-        if (st == PPMLR_OK) st = do_step(c, 0.0, c->dt_dev);
-    }
+    for (int k = 0; st == PPMLR_OK && k < ksteps; k++) st = cfl_step(c, cfl);
     cudaGraph_t graph = nullptr;
     if (e == cudaSuccess) {
         cudaError_t e2 = cudaStreamEndCapture(c->cap, &graph);

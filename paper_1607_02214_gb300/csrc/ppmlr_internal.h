@@ -102,20 +102,43 @@ struct CflArgs {
     const unsigned char *inner_mask;   // per cell: 1 inside the inner sphere, or null
 };
 
-// One ionosphere solve (ionosphere.cu): state, geometry, cap grid and the
-// device buffers it fills.
+// Ionosphere shell (ionosphere.cu).  Static per cap node: the trilinear cell
+// i0 (interior indices, 1 .. n-3) and weights of its mapping point at r_fac,
+// B_d there, and factor = |B_d(foot)| / |B_d(point)| x B_r(foot) / |B_d(foot)|
+// (0: the node's field line closes below r_fac).
+struct IonoNode {
+    int i0[3];
+    double w[3];
+    double Bd[3];
+    double factor;
+};
+// Static per inner cell: for each axis d the potential stencils of its two
+// neighbours along d, as 8 (node, coefficient) pairs giving E_d directly
+// (node >= 0: index into the potential; -1 - cap: that cap's pole value;
+// coefficients -w / span for the upper neighbour, +w / span for the lower),
+// and bt = B_d / |B_d|^2 at the cell (v = E x bt).
+struct IonoInner {
+    int idx[3][8];
+    double coef[3][8];
+    double bt[3];
+};
+constexpr int IONO_MAX_NT = 256;      // rings per cap
+// One ionosphere solve: state, geometry, tables and the device buffers it fills.
 struct IonoArgs {
     const double *B[3];        // B' of the state (arrays 4..6)
     int n[3];
     const double *c[3];        // ghost-extended cell centres of each axis
-    double M, r_iono, r_fac, sigma_p, theta_max, dth, dph;
+    double r_iono, sigma_p;
     int nt, np;                // rings and longitudes per cap
+    const IonoNode *nodes;     // 2 * nt * np
     double *jr;                // 2 * nt * np: radial current per cap node
     double *phi;               // 2 * nt * np: potential
     double *spec;              // 2 * nt * (np/2 + 1) * 2: Fourier coefficients
-    double *work;              // 2 * (np/2 + 1) * nt: tridiagonal scratch
     double *pole;              // 2: ring-0 mean per cap
-    const long long *inner_cells;
+    const double *tw;          // np x (cos, sin) of 2 pi q / np
+    const double *rows;        // nt x (lower, upper, diagonal without the longitude term, 1 / sin^2)
+    const double *lam;         // np/2 + 1: (2 - 2 cos(2 pi m / np)) / dphi^2
+    const IonoInner *inner;    // n_inner
     int n_inner;
     double *inner_state;       // 8 * n_inner
     double rho_in, p_in, gamma;
