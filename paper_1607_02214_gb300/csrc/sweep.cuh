@@ -64,11 +64,6 @@ __device__ __forceinline__ bool neg_d(double x)                                 
     return b < 0 && (b << 1) != 0;
 }
 __device__ __forceinline__ long long mag_d(double x) { return __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL; }
-__device__ __forceinline__ long long ord_d(double x)      // monotone map of finite doubles to integers
-{
-    const long long b = __double_as_longlong(x);
-    return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
-}
 // x * y > 0 (both non-zero, same sign; ignores underflow of the product)
 __device__ __forceinline__ bool same_sign_d(double x, double y)
 {
