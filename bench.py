@@ -50,14 +50,14 @@ BYTES_PER_CELL_SWEEP = 128      # read 8 FP64 + write 8 FP64
 # top of the state: traffic above the algorithmic 128 / 64 B by that much; the
 # FP64 y and z sweeps (72-register cap) add ~20 B per cell of spill writes.
 NCU_TRAFFIC = {
-    "fp64:x": {"bytes_per_cell": 150.0, "src": "f65302c2e14c0493"},
-    "fp64:y": {"bytes_per_cell": 171.6, "src": "f65302c2e14c0493"},
-    "fp64:z": {"bytes_per_cell": 168.2, "src": "f65302c2e14c0493"},
-    "fp64:cfl": {"bytes_per_cell": 89.4, "src": "01ec4099a6ebe2a2"},
-    "mixed:x": {"bytes_per_cell": 123.8, "src": "d4e1b2fc03b29060"},
-    "mixed:y": {"bytes_per_cell": 124.9, "src": "d4e1b2fc03b29060"},
-    "mixed:z": {"bytes_per_cell": 125.3, "src": "d4e1b2fc03b29060"},
-    "mixed:cfl": {"bytes_per_cell": 64.3, "src": "6acafd491a781373"},
+    "fp64:x": {"bytes_per_cell": 150.1, "src": "4d17b4cc1c417d54"},
+    "fp64:y": {"bytes_per_cell": 170.6, "src": "4d17b4cc1c417d54"},
+    "fp64:z": {"bytes_per_cell": 168.6, "src": "4d17b4cc1c417d54"},
+    "fp64:cfl": {"bytes_per_cell": 89.4, "src": "b69563e0f0c1e528"},
+    "mixed:x": {"bytes_per_cell": 123.8, "src": "cbd501d8e73fe0aa"},
+    "mixed:y": {"bytes_per_cell": 124.9, "src": "cbd501d8e73fe0aa"},
+    "mixed:z": {"bytes_per_cell": 125.3, "src": "cbd501d8e73fe0aa"},
+    "mixed:cfl": {"bytes_per_cell": 64.4, "src": "7bb02b5f55cf9cf7"},
 }
 
 
