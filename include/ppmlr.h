@@ -363,8 +363,12 @@ ppmlr_status ppmlr_ensemble_autotune(ppmlr_ens *ens, double *best_ms);
  * through per-instance tensor maps (every instance needs nx even and at most
  * 256 positions per tile; along x also C even and ny a multiple of the
  * lanes); budget = positions x lanes per
- * tile (15..448 for the FP64 forms, ..512 for PPMLR_MIXED).  Drops the step
- * graphs.  PPMLR_E_INVALID (launch unchanged) when the form does not fit. */
+ * tile (15..448 for the FP64 forms, ..512 for PPMLR_MIXED).  Tiles: whole
+ * pencils when they fit (else equal chunks), then as many lanes as fit; for
+ * y and z, budget + 10000 selects the other rule: the most lanes (a power of
+ * two up to 16) for which chunks of at least min(n, 48) cells fit.  Drops the
+ * step graphs.  PPMLR_E_INVALID (launch unchanged) when the form does not
+ * fit. */
 ppmlr_status ppmlr_ensemble_set_launch(ppmlr_ens *ens, int axis, int form, int budget);
 /* Riemann solver of every instance's sweeps, as ppmlr_set_riemann_solver
  * (0: two-wave; 1..16: two-shock Newton steps on the fast mode).  Drops the
@@ -373,8 +377,8 @@ ppmlr_status ppmlr_ensemble_set_riemann_solver(ppmlr_ens *ens, int iters);
 /* Contact steepening of every instance's remap, as ppmlr_set_steepening.
  * Drops the captured step graphs. */
 ppmlr_status ppmlr_ensemble_set_steepening(ppmlr_ens *ens, int on);
-/* Launch form and thread budget per direction in use: 1000 * form + budget
- * (3 entries). */
+/* Launch form, tile rule and thread budget per direction in use:
+ * 10000 * lanes_first + 1000 * form + budget (3 entries). */
 ppmlr_status ppmlr_ensemble_get_tiles(ppmlr_ens *ens, int *maxt);
 /* dt of the last step of every instance (count entries; synchronises). */
 ppmlr_status ppmlr_ensemble_get_dt(ppmlr_ens *ens, double *dt_out);

@@ -48,6 +48,7 @@ struct ppmlr_ens {
     int total_tiles[3], threads[3], blocks[3];
     size_t smem[3];
     int maxt[3];                 // tile thread budget chosen per direction
+    int lanes_first[3];          // y/z tile rule: 1 = most lanes, pencils chunked to >= 48 cells
     int mode[3];                 // 0: persistent work queue, 1: one block per tile (table),
                                  // 2: one block per tile (arguments in the kernel parameter),
                                  // 3: one block per tile, input box staged by TMA (y, z)
@@ -85,7 +86,41 @@ static size_t real_size(const ppmlr_ens *e) { return e->prec == PPMLR_MIXED ? si
 
 // Tile shapes of every instance for one direction under a thread budget;
 // false (nothing changed) when `mode` cannot serve every instance.
-static bool plan_direction(ppmlr_ens *e, int d, int maxt, int mode)
+// Tile of one instance along d within `maxt` positions x lanes.  Default
+// rule: whole pencils when they fit (else equal chunks), then as many lanes
+// as fit (y/z: a power of two up to 16, at most 2 nx).  lanes_first (y/z):
+// the most lanes (power of two up to 16) for which chunks of at least
+// min(N, 48) cells fit, then the fewest equal chunks.
+static void pick_tile(const int *n, int d, int maxt, bool lanes_first, int &C, int &L)
+{
+    const int N = n[d];
+    if (lanes_first && d != 0) {
+        const int cmin = N < 48 ? N : 48;
+        L = 1;
+        for (int l = 16; l >= 2; l /= 2) {
+            if (l / 2 >= n[0]) continue;
+            if (maxt / l - 2 * GH >= cmin) { L = l; break; }
+        }
+        const int cmax = maxt / L - 2 * GH;
+        int nchunk = (N + cmax - 1) / cmax;
+        if (nchunk < 1) nchunk = 1;
+        C = (N + nchunk - 1) / nchunk;
+        return;
+    }
+    int nchunk = 1;
+    C = N;
+    while (C + 2 * GH > maxt) { nchunk++; C = (N + nchunk - 1) / nchunk; }
+    L = maxt / (C + 2 * GH);
+    if (L < 1) L = 1;
+    if (d != 0) {
+        int p2 = 1;
+        while (p2 * 2 <= L && p2 * 2 <= 16) p2 *= 2;
+        while (p2 > 1 && p2 / 2 >= n[0]) p2 /= 2;
+        L = p2;
+    }
+}
+
+static bool plan_direction(ppmlr_ens *e, int d, int maxt, int mode, bool lanes_first = false)
 {
     if (mode == 3) {     // TMA staging: every instance's box within the copy engine's rules
         if (!tensor_map_encoder()) return false;
@@ -93,16 +128,8 @@ static bool plan_direction(ppmlr_ens *e, int d, int maxt, int mode)
         int thr = 32;
         for (int i = 0; i < e->count; i++) {
             const int *n = &e->n[3 * i];
-            int nchunk = 1, C = n[d];
-            while (C + 2 * GH > maxt) { nchunk++; C = (n[d] + nchunk - 1) / nchunk; }
-            int L = maxt / (C + 2 * GH);
-            if (L < 1) L = 1;
-            if (d != 0) {
-                int p2 = 1;
-                while (p2 * 2 <= L && p2 * 2 <= 16) p2 *= 2;
-                while (p2 > 1 && p2 / 2 >= n[0]) p2 /= 2;
-                L = p2;
-            }
+            int C, L;
+            pick_tile(n, d, maxt, lanes_first, C, L);
             const Tile t = make_tile(d, n, real_size(e), C, L);
             if (n[0] & 1) return false;
             if (d == 0 && ((t.C & 1) || t.NP + 2 > 256 || n[1] % t.L)) return false;   // x: even origin, one z plane
@@ -114,23 +141,15 @@ static bool plan_direction(ppmlr_ens *e, int d, int maxt, int mode)
     }
     e->maxt[d] = maxt;
     e->mode[d] = mode;
+    e->lanes_first[d] = lanes_first && d != 0 ? 1 : 0;
     e->tiles[d].clear();
     int thr = 32;
     size_t sm = 0;
     int total = 0;
     for (int i = 0; i < e->count; i++) {
         const int *n = &e->n[3 * i];
-        const int N = n[d];
-        int nchunk = 1, C = N;
-        while (C + 2 * GH > maxt) { nchunk++; C = (N + nchunk - 1) / nchunk; }
-        int L = maxt / (C + 2 * GH);
-        if (L < 1) L = 1;
-        if (d != 0) {
-            int p2 = 1;
-            while (p2 * 2 <= L && p2 * 2 <= 16) p2 *= 2;
-            while (p2 > 1 && p2 / 2 >= n[0]) p2 /= 2;
-            L = p2;
-        }
+        int C, L;
+        pick_tile(n, d, maxt, lanes_first, C, L);
         Tile t = make_tile(d, n, real_size(e), C, L);
         e->tiles[d].push_back(t);
         if (t.threads > thr) thr = t.threads;
@@ -585,11 +604,12 @@ ppmlr_status ppmlr_ensemble_autotune(ppmlr_ens *e, double *best_ms)
     }
     for (int d = 0; d < 3; d++) {
         float best = 1e30f;
-        int best_t = e->maxt[d], best_m = e->mode[d];
-        for (int k = 0; k < 4 * nc; k++) {
-            const int mode = k / nc;
+        int best_t = e->maxt[d], best_m = e->mode[d], best_r = e->lanes_first[d];
+        const int rules = d == 0 ? 1 : 2;
+        for (int k = 0; k < 4 * nc * rules; k++) {
+            const int mode = (k / nc) % 4, rule = k / (4 * nc);
             if (mode == 2 && e->count > ENS_PARAM_MAX) continue;
-            if (!plan_direction(e, d, cands[k % nc], mode)) continue;
+            if (!plan_direction(e, d, cands[k % nc], mode, rule == 1)) continue;
             ppmlr_status st = upload_direction(e, d);
             if (st != PPMLR_OK) return st;
             float tot = 0.0f;
@@ -603,9 +623,9 @@ ppmlr_status ppmlr_ensemble_autotune(ppmlr_ens *e, double *best_ms)
                 cudaEventElapsedTime(&ms, t0, t1);
                 if (rep > 0) tot += ms;
             }
-            if (tot < best) { best = tot; best_t = cands[k % nc]; best_m = mode; }
+            if (tot < best) { best = tot; best_t = cands[k % nc]; best_m = mode; best_r = rule; }
         }
-        plan_direction(e, d, best_t, best_m);
+        plan_direction(e, d, best_t, best_m, best_r == 1);
         ppmlr_status st = upload_direction(e, d);
         if (st != PPMLR_OK) return st;
         if (best_ms) best_ms[d] = best / 2.0f;
@@ -673,10 +693,13 @@ ppmlr_status ppmlr_ensemble_set_launch(ppmlr_ens *e, int axis, int form, int bud
 {
     if (!e) return PPMLR_E_INVALID;
     const int maxb = e->prec == PPMLR_MIXED ? MAXT : MAXT_F64;
-    if (axis < 0 || axis > 2 || form < 0 || form > 3 || budget < 2 * GH + 1 || budget > maxb)
+    const bool lanes_first = budget >= 10000;
+    if (lanes_first) budget -= 10000;
+    if (axis < 0 || axis > 2 || form < 0 || form > 3 || budget < 2 * GH + 1 || budget > maxb ||
+        (lanes_first && axis == 0))
         return efail(e, PPMLR_E_INVALID, "set_launch: bad axis, form or budget");
     if (form == 2 && e->count > ENS_PARAM_MAX) return efail(e, PPMLR_E_INVALID, "set_launch: form 2 takes at most 64 instances");
-    if (!plan_direction(e, axis, budget, form))
+    if (!plan_direction(e, axis, budget, form, lanes_first))
         return efail(e, PPMLR_E_INVALID, "set_launch: the TMA form does not fit every instance along this axis");
     ppmlr_status st = upload_direction(e, axis);
     if (st != PPMLR_OK) return st;
@@ -713,7 +736,7 @@ ppmlr_status ppmlr_ensemble_set_riemann_solver(ppmlr_ens *e, int iters)
 ppmlr_status ppmlr_ensemble_get_tiles(ppmlr_ens *e, int *maxt_out)
 {
     if (!e || !maxt_out) return PPMLR_E_INVALID;
-    for (int d = 0; d < 3; d++) maxt_out[d] = 1000 * e->mode[d] + e->maxt[d];
+    for (int d = 0; d < 3; d++) maxt_out[d] = 10000 * e->lanes_first[d] + 1000 * e->mode[d] + e->maxt[d];
     return PPMLR_OK;
 }
 
