@@ -131,3 +131,30 @@ def test_ensemble_tma_form_matches_the_other_forms(precision):
     assert odd.set_launch(1, 3, 256, raise_on_error=False) == ppmlr.PPMLR_E_INVALID  # nx odd
     skew = ppmlr.Ensemble([inputs.magnetosphere(n=(40, 30, 30), h0=1.0)], precision=precision)
     assert skew.set_launch(0, 3, 216, raise_on_error=False) == ppmlr.PPMLR_E_INVALID  # 4 lanes do not divide ny
+
+
+@pytest.mark.parametrize("precision", [ppmlr.PPMLR_FP64_EXACT, ppmlr.PPMLR_MIXED])
+@pytest.mark.parametrize("form", [0, 3])
+def test_ensemble_lanes_first_tiles_match_whole_pencil_tiles(precision, form):
+    """The y/z lanes-first rule (budget + 10000: chunked pencils, more lanes)
+    gives the whole-pencil rule's results (bit for bit on the exact path)."""
+    probs = [inputs.magnetosphere(n=n, h0=1.0, name=f"c{i}")
+             for i, n in enumerate(((40, 64, 60), (36, 70, 52), (44, 50, 66)))]
+    a = ppmlr.Ensemble(probs, precision=precision)
+    b = ppmlr.Ensemble(probs, precision=precision)
+    for axis in (1, 2):
+        a.set_launch(axis, form, 256)                   # whole pencils, 2 lanes
+        b.set_launch(axis, form, 10000 + 256)           # 4 lanes, pencils in chunks of 25..35 cells
+    assert [t // 10000 for t in b.tiles()][1:] == [1, 1] and [t // 10000 for t in a.tiles()][1:] == [0, 0]
+    assert b.set_launch(0, form, 10256, raise_on_error=False) == ppmlr.PPMLR_E_INVALID   # not along x
+    for i, p in enumerate(probs):
+        a.set_state(i, p.U0)
+        b.set_state(i, p.U0)
+    a.step(0.4, 4)
+    b.step(0.4, 4)
+    b.check()
+    for i in range(len(probs)):
+        if precision == ppmlr.PPMLR_FP64_EXACT:
+            assert np.array_equal(a.get_state(i), b.get_state(i)), i
+        else:
+            assert np.max(rel_l1(b.get_state(i), a.get_state(i))) <= 1e-6, i
