@@ -58,6 +58,11 @@ NCU_TRAFFIC = {
     "mixed:y": {"bytes_per_cell": 124.9, "src": "cbd501d8e73fe0aa"},
     "mixed:z": {"bytes_per_cell": 125.3, "src": "cbd501d8e73fe0aa"},
     "mixed:cfl": {"bytes_per_cell": 64.4, "src": "7bb02b5f55cf9cf7"},
+    # ensemble sweeps: captured on the first 8 of the 48 instances (14.9 M
+    # cells; the full ensemble holds ~10 GB), scaled by cells
+    "ensemble:x": {"bytes_per_cell": 125.1, "src": "b9d636627fe33731"},
+    "ensemble:y": {"bytes_per_cell": 126.0, "src": "b9d636627fe33731"},
+    "ensemble:z": {"bytes_per_cell": 126.0, "src": "b9d636627fe33731"},
 }
 
 
@@ -186,6 +191,13 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- workloads ------
+
+def parse_ensemble_launch(text):
+    parts = text.split(":")
+    if len(parts) != 3:
+        raise argparse.ArgumentTypeError("need three form,budget groups separated by ':'")
+    return [tuple(int(v) for v in q.split(",")) for q in parts]
+
 
 def parse_launch_config(text):
     parts = text.split(":")
@@ -583,18 +595,23 @@ def run_ensemble(args, fp64_value, barrier, rank=0, world=1, dist=None):
     import torch
     from paper_1607_02214_gb300 import inputs, ppmlr
     t0 = time.perf_counter()
-    all_probs = inputs.ensemble(48)
+    all_probs = inputs.ensemble(48)[:args.ensemble_count]
     probs = [all_probs[i] for i in shard(len(all_probs), rank, world)]
     log(f"[bench] ensemble inputs built in {time.perf_counter() - t0:.1f} s")
     cells = sum(p.cells for p in probs)
     cells_all = sum(p.cells for p in all_probs)
-    out = {"workload": "ensemble_48_magnetosphere_mixed", "instances": len(all_probs), "cells": cells_all,
+    out = {"workload": f"ensemble_{len(all_probs)}_magnetosphere_mixed", "instances": len(all_probs),
+           "cells": cells_all,
            "grids": sorted({"x".join(map(str, p.n)) for p in all_probs}),
            "scaling": "strong" if world > 1 else None, "instances_per_rank": len(probs)}
     ens = ppmlr.Ensemble(probs, precision=ppmlr.PPMLR_MIXED)
     for i, p in enumerate(probs):
         ens.set_state(i, p.U0)
-    out["tuned_ms"] = ens.autotune()
+    if args.ensemble_launch:
+        for axis, (form, budget) in enumerate(args.ensemble_launch):
+            ens.set_launch(axis, form, budget)
+    else:
+        out["tuned_ms"] = ens.autotune()
     out["tile_thread_budget"] = ens.tiles()
     ens.step(0.4, args.warmup)
     ens.check()
@@ -610,7 +627,7 @@ def run_ensemble(args, fp64_value, barrier, rank=0, world=1, dist=None):
     ens.check()
     out.update({"value": throughput(cells_all, args.steps, ms), "unit": UNIT, "ms_per_step": ms / args.steps,
                 "gpu_launches": ens.launch_count - n0, "graph_replay": True})
-    out["speedup_vs_fp64"] = out["value"] / fp64_value
+    out["speedup_vs_fp64"] = out["value"] / fp64_value if fp64_value and np.isfinite(fp64_value) else None
     if world > 1:        # the per-kernel and comparison runs below are single-GPU diagnostics
         ens.close()
         return out
@@ -724,6 +741,11 @@ def main():
                     help="fixed tiles and launch forms of the main precision instead of the autotuner: "
                          "C,L,form for x:y:z, e.g. 256,1,0:64,4,2:64,4,2")
     ap.add_argument("--ensemble-only", action="store_true", help="only the 48-instance ensemble section")
+    ap.add_argument("--ensemble-count", type=int, default=48,
+                    help="the first N of the 48 seeded ensemble instances (smaller captures)")
+    ap.add_argument("--ensemble-launch", type=parse_ensemble_launch, default=None,
+                    help="fixed ensemble launch form,budget per direction (x:y:z) instead of the autotuner; "
+                         "budget + 10000 = lanes-first tiles (y, z)")
     args = ap.parse_args()
     if args.warmup < 3:
         log("[bench] warm-up raised to 3 steps")
