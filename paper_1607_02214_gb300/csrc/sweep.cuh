@@ -218,10 +218,11 @@ __device__ __forceinline__ void dipole(double M, double x, double y, double z, d
 // extremum.  Contracted forms: c2 and c3 arrive with c1 folded in (c1 is not
 // used), and the two limits as one doubling of the smaller difference.
 template <typename R, bool EX = true>
-__device__ __forceinline__ R limit_slope(R am, R a0, R ap, R c1, R c2, R c3)
+__device__ __forceinline__ R limit_slope(R am, R a0, R ap, R c1, R c2, R c3, R *dp_out = nullptr)
 {
     if constexpr (!EX && std::is_same<R, double>::value) {
         const double dp = ap - a0, dm = a0 - am;
+        if (dp_out) *dp_out = dp;
         if (!same_sign_d(dp, dm)) return 0.0;
         const double da = c2 * dp + c3 * dm;
         const double lim = 2.0 * __longlong_as_double(min(mag_d(dm), mag_d(dp)));
@@ -230,6 +231,7 @@ __device__ __forceinline__ R limit_slope(R am, R a0, R ap, R c1, R c2, R c3)
     }
     if constexpr (!EX && std::is_same<R, float>::value) {   // branch-free: min/max and selects
         const float dp = ap - a0, dm = a0 - am;
+        if (dp_out) *dp_out = dp;
         const float da = c2 * dp + c3 * dm;
         const float m = fminf(fabsf(da), 2.0f * fminf(fabsf(dm), fabsf(dp)));
         return dp * dm > 0.0f ? copysignf(m, da) : 0.0f;
@@ -378,6 +380,12 @@ __device__ __forceinline__ R edge_value(const EdgeCoef<R> &k, R a0, R a1, R dmi,
     const R d = a1 - a0;
     if constexpr (!EX) return a0 + k.k1 * d - k.k4 * dmi1 + k.k5 * dmi;
     return a0 + k.k1 * d + k.k2 * (k.k3 * d - k.k4 * dmi1 + k.k5 * dmi);
+}
+// Contracted forms, with d = a1 - a0 as the slope step computed it.
+template <typename R>
+__device__ __forceinline__ R edge_value_d(const EdgeCoef<R> &k, R a0, R d, R dmi, R dmi1)
+{
+    return a0 + k.k1 * d - k.k4 * dmi1 + k.k5 * dmi;
 }
 
 // Shared-memory array indices.  Phase by phase (barrier between phases):
@@ -635,13 +643,15 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
 
     // ---------------- P2: slopes, flattening indicator, sources ----------------
     R dmv[7];
+    R dpv[7];                  // contracted forms: a_{i+1} - a_i, reused by the interface values (P3)
     R src_m[3] = {0, 0, 0}, src_b[3] = {0, 0, 0}, src_e = 0;
     if (act && p >= 1 && p <= NPe - 2) {
         SlopeCoef<R> k = slope_coef<R, EX>(SM(A_DM, s - PS), dm, SM(A_DM, s + PS));
         const R own[7] = {rho, u, v1, v2, B1, B2, pr};
 #pragma unroll
         for (int v = 0; v < 7; v++) {
-            dmv[v] = limit_slope<R, EX>(SM(A_RHO + v, s - PS), own[v], SM(A_RHO + v, s + PS), k.c1, k.c2, k.c3);
+            dmv[v] = limit_slope<R, EX>(SM(A_RHO + v, s - PS), own[v], SM(A_RHO + v, s + PS), k.c1, k.c2, k.c3,
+                                        EX ? nullptr : &dpv[v]);
             SM(SB0 + v, s) = dmv[v];
         }
         R ft = 0;
@@ -726,7 +736,8 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         const R own[7] = {rho, u, v1, v2, B1, B2, pr};
 #pragma unroll
         for (int v = 0; v < 7; v++) {
-            edg[v] = edge_value<R, EX>(k, own[v], SM(A_RHO + v, s + PS), dmv[v], SM(SB0 + v, s + PS));
+            if constexpr (EX) edg[v] = edge_value<R, EX>(k, own[v], SM(A_RHO + v, s + PS), dmv[v], SM(SB0 + v, s + PS));
+            else edg[v] = edge_value_d<R>(k, own[v], dpv[v], dmv[v], SM(SB0 + v, s + PS));
             SM(SC0 + v, s) = edg[v];
         }
         if (p >= 3 && p <= NPe - 4) {
@@ -898,11 +909,13 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
 
     // ---------------- P7: remap slopes ----------------
     R rmv[7];
+    R rpv[7];                  // contracted forms: q_{i+1} - q_i, reused by the remap interface values (P8)
     if (act && p >= 5 && p <= NPe - 6) {
         SlopeCoef<R> k = slope_coef<R, EX>(SM(SB0 + 7, s - PS), dxL, SM(SB0 + 7, s + PS));
 #pragma unroll
         for (int v = 0; v < 7; v++) {
-            rmv[v] = limit_slope<R, EX>(SM(SB0 + v, s - PS), qL[v], SM(SB0 + v, s + PS), k.c1, k.c2, k.c3);
+            rmv[v] = limit_slope<R, EX>(SM(SB0 + v, s - PS), qL[v], SM(SB0 + v, s + PS), k.c1, k.c2, k.c3,
+                                        EX ? nullptr : &rpv[v]);
             SM(v, s) = rmv[v];
         }
         if (a.steepen) {   // second difference of the Lagrangian density on the Lagrangian widths
@@ -919,7 +932,8 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         EdgeCoef<R> k = edge_coef<R, EX>(SM(SB0 + 7, s - PS), dxL, SM(SB0 + 7, s + PS), SM(SB0 + 7, s + 2 * PS));
 #pragma unroll
         for (int v = 0; v < 7; v++) {
-            red[v] = edge_value<R, EX>(k, qL[v], SM(SB0 + v, s + PS), rmv[v], SM(v, s + PS));
+            if constexpr (EX) red[v] = edge_value<R, EX>(k, qL[v], SM(SB0 + v, s + PS), rmv[v], SM(v, s + PS));
+            else red[v] = edge_value_d<R>(k, qL[v], rpv[v], rmv[v], SM(v, s + PS));
             SM(SC0 + v, s) = red[v];
         }
         if (a.steepen && p >= 6 && !shock_k) {   // contact weight of this zone
