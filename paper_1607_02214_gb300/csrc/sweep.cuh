@@ -71,6 +71,16 @@ __device__ __forceinline__ bool same_sign_d(double x, double y)
     return (a ^ b) >= 0 && (a << 1) != 0 && (b << 1) != 0;
 }
 
+// The remap's donor fraction y (> 0 where it is used) reaches the zone width:
+// y >= 1, on the bit patterns for the fast double form.
+template <typename R, bool EX>
+__device__ __forceinline__ bool sliver_too_wide(R y)
+{
+    if constexpr (!EX && std::is_same<R, double>::value)
+        return __double_as_longlong(y) >= 0x3FF0000000000000LL;       // the bits of 1.0
+    else return !(R(1) - y > R(0));
+}
+
 // x > 0 and x < 0 on the integer pipe for the fast double form, plain
 // comparisons otherwise.
 template <typename R, bool EX>
@@ -972,7 +982,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         if (p <= NPe - 8) {                       // edge p+1/2: donor is this zone when del >= 0
             if (gt0<R, EX>(del_p)) {
                 R y = EX ? del_p / dxL : del_p * idxL_k;
-                if (!gt0<R, EX>(R(1) - y)) atomicOr(a.flags, FLAG_CFL);
+                if (sliver_too_wide<R, EX>(y)) atomicOr(a.flags, FLAG_CFL);
 #pragma unroll
                 for (int v = 0; v < 7; v++) SM(flux_slot(v), s) = del_p * avg_right<R>(pl[v], pr_[v], p6[v], y);
             } else if (!lt0<R, EX>(del_p)) {
@@ -982,7 +992,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         }
         if (p >= 7 && lt0<R, EX>(del_m)) {       // edge p-1/2: donor is this zone when del < 0
             R y = EX ? -del_m / dxL : -del_m * idxL_k;
-            if (!gt0<R, EX>(R(1) - y)) atomicOr(a.flags, FLAG_CFL);
+            if (sliver_too_wide<R, EX>(y)) atomicOr(a.flags, FLAG_CFL);
 #pragma unroll
             for (int v = 0; v < 7; v++) SM(flux_slot(v), s - PS) = del_m * avg_left<R>(pl[v], pr_[v], p6[v], y);
         }
