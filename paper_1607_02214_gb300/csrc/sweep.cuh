@@ -1165,6 +1165,11 @@ __device__ __forceinline__ void tile_box_origin(const SweepArgs &a, int tile, in
 // otherwise roughly doubles the register allocation of the tile body.
 template <typename R, bool PERSIST> struct TmaMinBlocks { static constexpr int value = 1; };
 template <bool PERSIST> struct TmaMinBlocks<float, PERSIST> { static constexpr int value = 2; };
+// The mixed ensemble's one-block-per-tile kernels are held to the same 64
+// registers (two 512-thread blocks per SM): left free, the tile body takes
+// 78-87 and the resident warps halve.
+template <typename R> struct EnsMinBlocks { static constexpr int value = 1; };
+template <> struct EnsMinBlocks<float> { static constexpr int value = 2; };
 
 // Single domain, input staged by TMA (any direction).  PERSIST: each block
 // takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...; while it computes one
@@ -1297,7 +1302,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_kernel(En
 // tile) items in order; the block finds its instance from the first-tile
 // table and copies that instance's arguments to shared memory.
 template <int DIR, typename R, bool EX>
-__global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_grid_kernel(EnsSweepArgs e)
+__global__ void __launch_bounds__(MaxThreads<R>::value, EnsMinBlocks<R>::value) sweep_ensemble_grid_kernel(EnsSweepArgs e)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ SweepArgs args;
@@ -1320,7 +1325,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_grid_kern
 // 1 = its second; the array lives in global memory, written before the
 // launch).  The wait is bounded; a block that gives up raises FLAG_TIMEOUT.
 template <int DIR, typename R, bool EX>
-__global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_tma_kernel(EnsSweepArgs e,
+__global__ void __launch_bounds__(MaxThreads<R>::value, EnsMinBlocks<R>::value) sweep_ensemble_tma_kernel(EnsSweepArgs e,
                                                                                   const CUtensorMap *maps)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -1361,7 +1366,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_tma_kerne
 // parameter (constant bank): the block finds its instance from the first-tile
 // table and reads that instance's fields straight from the parameter space.
 template <int DIR, typename R, bool EX>
-__global__ void __launch_bounds__(MaxThreads<R>::value) sweep_ensemble_param_kernel(const __grid_constant__ EnsSweepParams p)
+__global__ void __launch_bounds__(MaxThreads<R>::value, EnsMinBlocks<R>::value) sweep_ensemble_param_kernel(const __grid_constant__ EnsSweepParams p)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const int t = blockIdx.x;
