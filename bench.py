@@ -48,21 +48,21 @@ BYTES_PER_CELL_SWEEP = 128      # read 8 FP64 + write 8 FP64
 # sha256 prefix of the kernel source they were taken on (null once it changes).
 # The FP64 sweeps and CFL pass also read the dipole table (24 B per cell) on
 # top of the state: traffic above the algorithmic 128 / 64 B by that much; the
-# FP64 y and z sweeps (72-register cap) add ~20 B per cell of spill writes.
+# FP64 y and z sweeps (72-register cap) add ~30 B per cell of spill traffic.
 NCU_TRAFFIC = {
-    "fp64:x": {"bytes_per_cell": 150.1, "src": "4d17b4cc1c417d54"},
-    "fp64:y": {"bytes_per_cell": 170.6, "src": "4d17b4cc1c417d54"},
-    "fp64:z": {"bytes_per_cell": 168.6, "src": "4d17b4cc1c417d54"},
+    "fp64:x": {"bytes_per_cell": 151.4, "src": "69744c4d049bf387"},
+    "fp64:y": {"bytes_per_cell": 181.1, "src": "69744c4d049bf387"},
+    "fp64:z": {"bytes_per_cell": 177.2, "src": "69744c4d049bf387"},
     "fp64:cfl": {"bytes_per_cell": 89.4, "src": "b69563e0f0c1e528"},
-    "mixed:x": {"bytes_per_cell": 123.8, "src": "cbd501d8e73fe0aa"},
-    "mixed:y": {"bytes_per_cell": 124.9, "src": "cbd501d8e73fe0aa"},
-    "mixed:z": {"bytes_per_cell": 125.3, "src": "cbd501d8e73fe0aa"},
-    "mixed:cfl": {"bytes_per_cell": 64.4, "src": "7bb02b5f55cf9cf7"},
+    "mixed:x": {"bytes_per_cell": 123.9, "src": "1260ce696251a8b5"},
+    "mixed:y": {"bytes_per_cell": 124.9, "src": "1260ce696251a8b5"},
+    "mixed:z": {"bytes_per_cell": 125.2, "src": "1260ce696251a8b5"},
+    "mixed:cfl": {"bytes_per_cell": 64.3, "src": "fbbef49639c7f357"},
     # ensemble sweeps: captured on the first 8 of the 48 instances (14.9 M
     # cells; the full ensemble holds ~10 GB), scaled by cells
-    "ensemble:x": {"bytes_per_cell": 125.1, "src": "b9d636627fe33731"},
-    "ensemble:y": {"bytes_per_cell": 126.0, "src": "b9d636627fe33731"},
-    "ensemble:z": {"bytes_per_cell": 126.0, "src": "b9d636627fe33731"},
+    "ensemble:x": {"bytes_per_cell": 125.0, "src": "21fd97639b459256"},
+    "ensemble:y": {"bytes_per_cell": 125.7, "src": "21fd97639b459256"},
+    "ensemble:z": {"bytes_per_cell": 125.9, "src": "21fd97639b459256"},
 }
 
 
