@@ -253,8 +253,11 @@ typedef struct {
  * a dipole, and the mapping sphere one cell inside the interior of every axis
  * (the centres of cells 1 and n-2 bracket [-r_fac, r_fac]).  Allocates
  * 2 n_theta n_phi x 4 doubles for the caps and 8 doubles per inner cell;
- * drops the step graphs.  PPMLR_E_INVALID (shell unchanged) otherwise,
- * PPMLR_E_OOM on allocation failure. */
+ * drops the step graphs.  Until the first solve (a step, or
+ * ppmlr_ionosphere_solve) the inner cells keep the configuration's fixed
+ * state, so a lone ppmlr_sweep resets them as without the shell.
+ * PPMLR_E_INVALID (shell unchanged) otherwise, PPMLR_E_OOM on allocation
+ * failure. */
 ppmlr_status ppmlr_set_ionosphere(ppmlr_ctx *ctx, const ppmlr_iono *cfg);
 /* One ionosphere solve from the current state (what every step does first
  * while the shell is on), on the context's stream.  PPMLR_E_INVALID when the

@@ -1053,6 +1053,16 @@ ppmlr_status ppmlr_set_ionosphere(ppmlr_ctx *c, const ppmlr_iono *cfg)
         const double b2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
         for (int d = 0; d < 3; d++) q.bt[d] = b2 > 0.0 ? B[d] / b2 : 0.0;
     }
+    // until the first solve, every inner cell holds the configuration's fixed
+    // inner state (what the sweeps wrote without the shell)
+    std::vector<double> rest(8 * ninner);
+    {
+        const ppmlr_prim &q = c->bc.inner;
+        const double u[8] = {q.rho, q.rho * q.v[0], q.rho * q.v[1], q.rho * q.v[2], 0.0, 0.0, 0.0,
+                             q.p / (c->gamma - 1.0) + 0.5 * q.rho * (q.v[0] * q.v[0] + q.v[1] * q.v[1] + q.v[2] * q.v[2])};
+        for (int v = 0; v < 8; v++)
+            for (size_t t = 0; t < ninner; t++) rest[(size_t)v * ninner + t] = u[v];
+    }
     double *buf = nullptr, *state = nullptr;
     long long *cells = nullptr;
     IonoNode *dnodes = nullptr;
@@ -1072,6 +1082,8 @@ ppmlr_status ppmlr_set_ionosphere(ppmlr_ctx *c, const ppmlr_iono *cfg)
                             c->stream);
     if (e == cudaSuccess && ninner)
         e = cudaMemcpyAsync(dinner, inner.data(), sizeof(IonoInner) * ninner, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && ninner)
+        e = cudaMemcpyAsync(state, rest.data(), sizeof(double) * rest.size(), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         cudaFree(buf); cudaFree(cells); cudaFree(state); cudaFree(dnodes); cudaFree(dinner);

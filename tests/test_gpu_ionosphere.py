@@ -154,3 +154,18 @@ def test_solve_on_the_full_magnetosphere_grid():
     jr_o = I.radial_current(U, pr.edges, pr.bc.dipole_moment, pr.bc.r_inner, cfg)
     phi_o = I.solve_potential(jr_o, pr.bc.r_inner, cfg)
     assert rel_max(jr_g, jr_o) <= 1e-11 and rel_max(phi_g, phi_o) <= 1e-11
+
+
+def test_before_the_first_solve_the_inner_cells_keep_the_fixed_state():
+    """A lone sweep right after the shell is switched on (no step, no solve)
+    equals the sweep without the shell, bit for bit."""
+    pr = small()
+    U = developed_state(pr, 2)
+    a, b = make_gpu(pr), make_gpu(pr)
+    for c in (a, b):
+        c.set_state(U)
+    a.set_ionosphere(**CFG)
+    for axis in (0, 1, 2):
+        a.sweep(axis, 1e-3)
+        b.sweep(axis, 1e-3)
+    assert np.array_equal(a.get_state(), b.get_state())
