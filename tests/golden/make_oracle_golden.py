@@ -1,8 +1,8 @@
 """Write tests/golden/oracle_regression.json from the oracle alone.
 
-Regression fixture: a few seeded small runs of the oracle, summarised by
-per-variable sums, sums of squares, sampled cells, time steps and floor
-counts.  Regenerate only when the oracle's arithmetic is changed on purpose,
+Regression fixture: a few seeded small runs of the oracle (one with the
+ionosphere shell coupled to the inner boundary), summarised by per-variable
+sums, sums of squares, sampled cells, time steps and floor counts.  Regenerate only when the oracle's arithmetic is changed on purpose,
 and name in the commit message the passage (or reading) that justifies it.
 """
 import json
@@ -15,6 +15,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 import numpy as np  # noqa: E402
 
 import oracle  # noqa: E402
+from oracle import ionosphere  # noqa: E402
 from paper_1607_02214_gb300 import inputs  # noqa: E402
 
 CASES = {
@@ -25,10 +26,13 @@ CASES = {
         "rand", [inputs.random_stretched_edges(k, 40 + d) for d, k in enumerate((10, 9, 8))], 5.0 / 3.0,
         inputs.BoundarySpec(powell=1), inputs.random_smooth_state((10, 9, 8), 41,
         edges=[inputs.random_stretched_edges(k, 40 + d) for d, k in enumerate((10, 9, 8))])), 4),
+    "magnetosphere_28x24x24_h0_1_shell_3steps": lambda: (
+        inputs.magnetosphere(n=(28, 24, 24), h0=1.0, x_ext=(-30.0, 20.0), yz_ext=(-25.0, 25.0)), 3,
+        dict(r_iono=1.017, r_fac=4.0, sigma_p=0.6283, n_theta=8, n_phi=12)),
 }
 
 
-def run_case(prob, nsteps):
+def run_case(prob, nsteps, shell=None):
     bc = prob.bc
     o = oracle.Oracle(prob.edges, prob.gamma, bc.flat_faces(), inflow=bc.inflow, dipole_moment=bc.dipole_moment,
                       r_inner=bc.r_inner, inner=bc.inner, p_min=bc.p_min, powell=bc.powell)
@@ -36,6 +40,10 @@ def run_case(prob, nsteps):
     dts = []
     flags = 0
     for _ in range(nsteps):
+        if shell:
+            v, _, _ = ionosphere.couple(o.get_state(), prob.edges, bc.dipole_moment, bc.r_inner,
+                                        ionosphere.IonoConfig(**shell))
+            o.set_inner_velocity(v)
         dt = o.cfl_dt(prob.cfl)
         dts.append(dt)
         flags |= o.step(dt)
@@ -52,8 +60,7 @@ def run_case(prob, nsteps):
 def main():
     out = {"_about": "Written by make_oracle_golden.py from the oracle only.", "cases": {}}
     for name, fn in CASES.items():
-        prob, nsteps = fn()
-        out["cases"][name] = run_case(prob, nsteps)
+        out["cases"][name] = run_case(*fn())
     with open(os.path.join(HERE, "oracle_regression.json"), "w") as f:
         json.dump(out, f, indent=1)
 

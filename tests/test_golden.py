@@ -51,8 +51,7 @@ def test_oracle_regression_fixture():
     from golden.make_oracle_golden import CASES, run_case
     gold = load("oracle_regression.json")["cases"]
     for name, fn in CASES.items():
-        prob, nsteps = fn()
-        got = run_case(prob, nsteps)
+        got = run_case(*fn())
         ref = gold[name]
         assert got["flags"] == ref["flags"] and got["floors"] == ref["floors"]
         np.testing.assert_allclose(got["dt"], ref["dt"], rtol=1e-13)
