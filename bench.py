@@ -40,9 +40,10 @@ HBM_FALLBACK_GBS = 6800.0
 FP64_PEAK_GFLOPS = 1006.0
 FP64_NOMINAL_GFLOPS = 1250.0
 # Algorithmic FP64 flops (+, -, x, /, sqrt) per interior cell of one sweep on
-# the magnetosphere workload (PPM coefficients counted once per zone), counted
-# by an instrumented build of the reference; and per cell of the CFL pass.
-FLOPS_PER_CELL = {"x": 1189.1, "y": 1241.9, "z": 1243.7, "cfl": 208.0}
+# the magnetosphere workload (PPM coefficients counted once per zone) and per
+# cell of the CFL pass, counted by the op-counting build of the oracle
+# (oracle/opcount/count_flops.py, 256 x 192 x 192).
+FLOPS_PER_CELL = {"x": 1189.1, "y": 1241.9, "z": 1243.7, "cfl": 207.0}
 BYTES_PER_CELL_SWEEP = 128      # read 8 FP64 + write 8 FP64
 # DRAM bytes per cell of one launch measured by ncu for each kernel, with the
 # sha256 prefix of the kernel source they were taken on (null once it changes).
