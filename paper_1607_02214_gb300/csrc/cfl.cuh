@@ -136,8 +136,11 @@ __device__ __forceinline__ void cfl_body(const CflArgs &a, const int bid, const 
                 double c2 = 0.5 * (s2 + sqrt_fast(q2));
                 double cf = sqrt_fast(__double_as_longlong(c1) > __double_as_longlong(c2) ? c1 : c2);
                 if (a.iw[0]) {
+                    // a NaN rate (bit patterns above +inf) is skipped, as the
+                    // quotient form's comparison skips a NaN bound
                     const double r = (fabs(U[1 + d] * ir) + cf) * a.iw[d][idx[d] + GH];
-                    if (__double_as_longlong(r) > __double_as_longlong(rate)) rate = r;
+                    const long long rb = __double_as_longlong(r);
+                    if (rb > __double_as_longlong(rate) && rb <= 0x7FF0000000000000LL) rate = r;
                 } else {
                     double s = a.w[d][idx[d] + GH] / (fabs(U[1 + d] * ir) + cf);
                     if (s < best) best = s;

@@ -44,3 +44,19 @@ def test_invalid_arguments():
         g.sweep(3, 1e-3)
     with pytest.raises(ppmlr.PPMLRError):
         g.step_cfl(-0.4, 1)
+
+
+@pytest.mark.parametrize("precision", [ppmlr.PPMLR_FP64, ppmlr.PPMLR_FP64_EXACT])
+def test_cfl_skips_a_nonfinite_cell_like_the_oracle(precision):
+    """The CFL reduction ignores a cell whose state is NaN (the oracle's
+    comparison does); the flag for the NaN comes from the sweep that made it."""
+    from gpu_util import make_oracle
+    pr = inputs.brio_wu_3d((16, 8, 8))
+    U = pr.U0.copy()
+    U[7, 3, 4, 5] = np.nan
+    o = make_oracle(pr)
+    o.set_state(U)
+    g = ppmlr.Context.from_problem(pr, precision)
+    g.set_state(U)
+    dt_o, dt_g = o.cfl_dt(0.4), g.cfl_dt(0.4)
+    assert np.isfinite(dt_g) and abs(dt_g - dt_o) <= 1e-14 * dt_o
