@@ -218,6 +218,14 @@ ppmlr_status ppmlr_set_riemann_solver(ppmlr_ctx *ctx, int iters);
  * advected contact. */
 ppmlr_status ppmlr_set_steepening(ppmlr_ctx *ctx, int on);
 
+/* Failure-path self-test of the kernels' bounded waits: launches one block
+ * that waits, with the wait helper of the TMA-staged sweeps (here bounded at
+ * 4096 polls), on an mbarrier that nothing completes; the wait gives up, the
+ * block raises the timeout flag and returns.  The next synchronising call
+ * (ppmlr_check, ppmlr_get_state, ppmlr_cfl_dt) returns PPMLR_E_TIMEOUT once;
+ * the context stays usable.  No paper counterpart. */
+ppmlr_status ppmlr_selftest_wait_timeout(ppmlr_ctx *ctx);
+
 /* Ionosphere shell (Sec. II): a thin conducting sphere at r_iono closes the
  * field-aligned currents and is tied to the inner boundary by dipole field
  * lines; its electrostatic potential sets the flow of the inner-sphere cells.

@@ -31,6 +31,7 @@ UNITS = {
     "sweep_mixed.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "cfl_mixed.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "ionosphere.cu": ["-fmad=true"],
+    "selftest.cu": ["-fmad=true"],
 }
 
 

@@ -1121,6 +1121,15 @@ ppmlr_status ppmlr_get_ionosphere(ppmlr_ctx *c, double *phi, double *jr)
     return read_flags(c);
 }
 
+ppmlr_status ppmlr_selftest_wait_timeout(ppmlr_ctx *c)
+{
+    if (!c) return PPMLR_E_INVALID;
+    cudaError_t e = launch_wait_selftest(c->flags, 1 << 12, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "selftest launch");
+    c->launches++;
+    return PPMLR_OK;
+}
+
 ppmlr_status ppmlr_set_steepening(ppmlr_ctx *c, int on)
 {
     if (!c) return PPMLR_E_INVALID;

@@ -144,6 +144,9 @@ struct IonoArgs {
     double rho_in, p_in, gamma;
 };
 cudaError_t launch_ionosphere(const IonoArgs &a, cudaStream_t s, int *launches);
+// selftest.cu: one block waits, with at most `polls` polls, on an mbarrier that
+// nothing completes, then raises FLAG_TIMEOUT in *flags
+cudaError_t launch_wait_selftest(int *flags, int polls, cudaStream_t s);
 
 // Tile shape of one sweep direction.
 struct Tile {

@@ -1110,10 +1110,11 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
-// Bounded wait on the mbarrier phase; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+// Bounded wait on the mbarrier phase (at most `polls` try_wait polls); false
+// if it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int polls = 1 << 22)
 {
-    for (int it = 0; it < (1 << 22); it++) {
+    for (int it = 0; it < polls; it++) {
         unsigned done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"

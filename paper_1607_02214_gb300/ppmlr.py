@@ -73,6 +73,7 @@ SIGNATURES = [
     ("ppmlr_run", c_int, [c_void_p, c_double, c_longlong, c_int]),
     ("ppmlr_set_riemann_solver", c_int, [c_void_p, c_int]),
     ("ppmlr_set_steepening", c_int, [c_void_p, c_int]),
+    ("ppmlr_selftest_wait_timeout", c_int, [c_void_p]),
     ("ppmlr_set_ionosphere", c_int, [c_void_p, POINTER(ppmlr_iono)]),
     ("ppmlr_ionosphere_solve", c_int, [c_void_p]),
     ("ppmlr_get_ionosphere", c_int, [c_void_p, POINTER(c_double), POINTER(c_double)]),
@@ -299,6 +300,10 @@ class Context:
         cfg = ppmlr_iono(float(r_iono), float(r_fac), float(sigma_p), int(n_theta), int(n_phi))
         self._iono = (int(n_theta), int(n_phi))
         return self._check(load().ppmlr_set_ionosphere(self._h, ctypes.byref(cfg)))
+
+    def selftest_wait_timeout(self):
+        """Launch the bounded-wait self-test (the next check reports PPMLR_E_TIMEOUT)."""
+        return self._check(load().ppmlr_selftest_wait_timeout(self._h))
 
     def ionosphere_solve(self):
         """One shell solve from the current state (each step does one first)."""

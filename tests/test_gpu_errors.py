@@ -60,3 +60,17 @@ def test_cfl_skips_a_nonfinite_cell_like_the_oracle(precision):
     g.set_state(U)
     dt_o, dt_g = o.cfl_dt(0.4), g.cfl_dt(0.4)
     assert np.isfinite(dt_g) and abs(dt_g - dt_o) <= 1e-14 * dt_o
+
+
+def test_bounded_wait_gives_up_and_reports_timeout():
+    """A device wait that nothing completes gives up after its bound: the
+    timeout status is reported once and the context keeps working."""
+    pr = inputs.brio_wu_3d((16, 8, 8))
+    g, ref = make_gpu(pr), make_gpu(pr)
+    g.selftest_wait_timeout()
+    assert g.check(raise_on_error=False) == ppmlr.PPMLR_E_TIMEOUT
+    assert g.check(raise_on_error=False) == ppmlr.PPMLR_OK
+    for c in (g, ref):
+        c.step_cfl(0.4, 3)
+        c.check()
+    assert np.array_equal(g.get_state(), ref.get_state())
