@@ -235,19 +235,36 @@ def config_dict(prob, name, args, world):
 
 # ------------------------------------------------------------ reference -------
 
-def oracle_sample(prob, steps, threads=0):
-    """Time the oracle on the host cores: `steps` steps of prob with its CFL dt."""
+def oracle_sample(prob, steps, threads=0, keep=False):
+    """Time the oracle on the host cores: `steps` steps of prob with its CFL dt.
+    keep: also return the time steps and the final state."""
     import oracle
     cores = oracle.set_threads(threads)
     bc = prob.bc
     o = oracle.Oracle(prob.edges, prob.gamma, bc.flat_faces(), inflow=bc.inflow, dipole_moment=bc.dipole_moment,
                       r_inner=bc.r_inner, inner=bc.inner, p_min=bc.p_min, powell=bc.powell)
     o.set_state(prob.U0)
+    dts = []
     t0 = time.perf_counter()
     for _ in range(steps):
-        o.step(o.cfl_dt(prob.cfl))
+        dt = o.cfl_dt(prob.cfl)
+        dts.append(dt)
+        o.step(dt)
     t = time.perf_counter() - t0
+    if keep:
+        return prob.cells * steps / t, t, cores, dts, o.get_state()
     return prob.cells * steps / t, t, cores
+
+
+def errors_vs(U, ref):
+    """Per-variable relative L1 (each variable's group scale: rho; momentum; B'; E)
+    and Linf of U against ref, both (8, nz, ny, nx)."""
+    diff = np.abs(U - ref).reshape(8, -1)
+    a = np.abs(ref).reshape(8, -1).sum(axis=1)
+    grp = np.array([a[0], *[a[1:4].sum()] * 3, *[a[4:7].sum()] * 3, a[7]])
+    names = ["rho", "mx", "my", "mz", "Bx", "By", "Bz", "E"]
+    return {"rel_l1": dict(zip(names, (diff.sum(axis=1) / grp).tolist())),
+            "linf": dict(zip(names, diff.max(axis=1).tolist()))}
 
 
 def run_reference(args, rank, world):
@@ -527,9 +544,22 @@ def run_ours(args, rank, world, dist):
         small = inputs.magnetosphere(n=(64, 48, 48), h0=1.6)
         r_small, _, _ = oracle_sample(small, 1)
         steps = max(1, min(3, int(20.0 * r_small / cells)))
-        rate, t, cores = oracle_sample(prob, steps)
+        rate, t, cores, dts, Uo = oracle_sample(prob, steps, keep=True)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{steps} full step(s) of {name}, OpenMP over pencils, {t:.1f} s"}
+        # the GPU paths replayed with the oracle's time steps: their error
+        # against the oracle on the full workload
+        acc = {"steps": steps}
+        for key, p in (("fp64", ppmlr.PPMLR_FP64), ("mixed", ppmlr.PPMLR_MIXED)):
+            c = ppmlr.Context.from_problem(prob, p)
+            c.set_state(U0)
+            for dt in dts:
+                c.step(dt)
+            c.check()
+            acc[key] = errors_vs(c.get_state(), Uo)
+            c.close()
+        extra["error_vs_oracle"] = acc
+        del Uo
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
