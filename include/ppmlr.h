@@ -259,9 +259,12 @@ typedef struct {
 /* Turns the shell on (cfg copied) or off (cfg = NULL: the inner cells return
  * to the configuration's fixed state at the next sweep).  Needs r_inner > 0,
  * a dipole, and the mapping sphere one cell inside the interior of every axis
- * (the centres of cells 1 and n-2 bracket [-r_fac, r_fac]).  Allocates
- * 2 n_theta n_phi x 4 doubles for the caps and 8 doubles per inner cell;
- * drops the step graphs.  Until the first solve (a step, or
+ * (the centres of cells 1 and n-2 bracket [-r_fac, r_fac]).  Allocates per
+ * cap node about 4 doubles (current, potential, Fourier coefficients) and a
+ * 72-byte table entry, per inner cell 8 doubles and a 312-byte stencil entry,
+ * plus the solve tables (2 n_phi + 4 n_theta + n_phi/2 + 1 doubles); drops
+ * the step graphs.  Device-dt steps run the solve beside the CFL reduction
+ * on a second stream.  Until the first solve (a step, or
  * ppmlr_ionosphere_solve) the inner cells keep the configuration's fixed
  * state, so a lone ppmlr_sweep resets them as without the shell.
  * PPMLR_E_INVALID (shell unchanged) otherwise, PPMLR_E_OOM on allocation
