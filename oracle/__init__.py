@@ -67,6 +67,7 @@ def lib():
         L.orc_set_riemann.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_set_steepening.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_set_inner_velocity.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_flatten.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp]
         _lib = L
     return _lib
 
@@ -211,6 +212,20 @@ def ppm_parabola(ai, aL, aR, f=0.0):
     out = np.zeros(3)
     lib().orc_ppm_parabola(float(ai), float(aL), float(aR), float(f), _ptr(out))
     return out
+
+
+def flatten(Pt, u):
+    """Flattening of a pencil from its total pressure and normal velocity
+    (Colella & Woodward 1984, App. A): returns (ft, f); ft is the shock
+    indicator of every zone (0 outside 2..n-3), f the coefficient of zones
+    3..n-4 (0 elsewhere)."""
+    Pt = np.ascontiguousarray(Pt, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    assert Pt.shape == u.shape and Pt.ndim == 1
+    ft = np.zeros_like(Pt)
+    f = np.zeros_like(Pt)
+    lib().orc_flatten(len(Pt), _ptr(Pt), _ptr(u), _ptr(ft), _ptr(f))
+    return ft, f
 
 
 def avg_right(aL, aR, a6, y):

@@ -32,7 +32,9 @@
  * Parity pins: every routine here is pinned by the CPU tests (cubic exactness
  * of the interface formula, parabola averages, Riemann-invariant and symmetry
  * checks, exact Sod solution, Brio-Wu self-convergence, Alfven-wave order,
- * conservation, equilibria, split symmetry).
+ * conservation, equilibria, split symmetry, flattening values worked out by
+ * hand, the CFL step against hand-computed states and the eigenvalues of the
+ * MHD Jacobian, boundary ghosts against their definitions).
  */
 #include <math.h>
 #include <stdint.h>
@@ -367,6 +369,41 @@ int orc_set_threads(int t)
 }
 
 /* Conserved state of a primitive state (rho, v, B', p): closure of Sec. II. */
+/* Flattening coefficient of Colella & Woodward (1984), Appendix A, on a
+ * pencil of NP zones, with the total pressure Pt = p + |B'|^2/2 in place of
+ * the gas pressure [R: MHD] and the normal velocity u.
+ *   Shock indicator of zone p (2 <= p <= NP-3): the zone is in a shock when
+ *   the pressure jump across it exceeds FLAT_EPS of the smaller neighbour,
+ *   |Pt[p+1] - Pt[p-1]| > FLAT_EPS min(Pt[p+1], Pt[p-1]), and the flow is
+ *   compressive there, u[p-1] > u[p+1].  Then
+ *   ft = clamp((steep - FLAT_W1) FLAT_W2, 0, 1) with the steepness
+ *   steep = (Pt[p+1] - Pt[p-1]) / (Pt[p+2] - Pt[p-2]) (1 where the wide
+ *   difference vanishes); elsewhere ft = 0.
+ *   Coefficient of zone p (3 <= p <= NP-4): f = max(ft[p], ft[p - s]),
+ *   s = sign(Pt[p+1] - Pt[p-1]) -- the neighbour on the low-pressure side
+ *   (s = 0 is taken as +1 [R]).
+ * ft is written for every zone (0 outside 2..NP-3); f only for 3..NP-4. */
+void orc_flatten(int NP, const double *Pt, const double *u, double *ft, double *f)
+{
+    for (int p = 0; p < NP; p++) ft[p] = 0.0;
+    for (int p = 2; p <= NP - 3; p++) {
+        double dP = Pt[p + 1] - Pt[p - 1];
+        double pmin = Pt[p + 1] < Pt[p - 1] ? Pt[p + 1] : Pt[p - 1];
+        if (fabs(dP) > FLAT_EPS * pmin && u[p - 1] - u[p + 1] > 0.0) {
+            double den = Pt[p + 2] - Pt[p - 2];
+            double steep = den != 0.0 ? dP / den : 1.0;
+            double fz = (steep - FLAT_W1) * FLAT_W2;
+            if (fz < 0.0) fz = 0.0;
+            if (fz > 1.0) fz = 1.0;
+            ft[p] = fz;
+        }
+    }
+    for (int p = 3; p <= NP - 4; p++) {
+        double up = Pt[p + 1] - Pt[p - 1] < 0.0 ? ft[p + 1] : ft[p - 1];
+        f[p] = ft[p] > up ? ft[p] : up;
+    }
+}
+
 static void prim_to_cons(double rho, const double *v, const double *Bp, double p, double gamma, double *U)
 {
     U[0] = rho;
@@ -522,23 +559,7 @@ static void sweep_pencil(orc_ctx *c, int d, int j, int k, double dt, pencil_buf 
     const double *dm = b->tmp;
 
     /* 3. flattening coefficient (CW84 App. A) on total pressure and u [R] */
-    for (int p = 0; p < NP; p++) b->ft[p] = 0.0;
-    for (int p = 2; p <= NP - 3; p++) {
-        double dP = b->Pt[p + 1] - b->Pt[p - 1];
-        double pmin = b->Pt[p + 1] < b->Pt[p - 1] ? b->Pt[p + 1] : b->Pt[p - 1];
-        if (fabs(dP) > FLAT_EPS * pmin && b->q[1][p - 1] - b->q[1][p + 1] > 0.0) {
-            double den = b->Pt[p + 2] - b->Pt[p - 2];
-            double steep = den != 0.0 ? dP / den : 1.0;
-            double f = (steep - FLAT_W1) * FLAT_W2;
-            if (f < 0.0) f = 0.0;
-            if (f > 1.0) f = 1.0;
-            b->ft[p] = f;
-        }
-    }
-    for (int p = 3; p <= NP - 4; p++) {
-        double up = b->Pt[p + 1] - b->Pt[p - 1] < 0.0 ? b->ft[p + 1] : b->ft[p - 1];
-        b->f[p] = b->ft[p] > up ? b->ft[p] : up;
-    }
+    orc_flatten(NP, b->Pt, b->q[1], b->ft, b->f);
 
     /* 4. Lagrangian PPM of the 7 primitives on the mass coordinate, then the
      *    domain-of-dependence averages (CW84 eq. 1.12), each over the mass its
