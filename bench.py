@@ -32,13 +32,20 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s per full xyz step"
 UNIT = "cell-updates/s"
 HBM_FALLBACK_GBS = 6800.0
-# FP64 peak of a GB300 in flop/s: bench_fp64_rate.cu measures 503 G FP64
-# fused multiply-adds per second over all 152 SMs (1.60 per SM per clock at
-# 2070 MHz; DADD and DMUL run at the same instruction rate, DDIV at 88.6 G/s,
-# DSQRT at 58.4 G/s), i.e. 1006 GFLOP/s with an FMA counted as two flops.
-# The nominal dense FP64 rate of the part is 1.25 TFLOP/s.
-FP64_PEAK_GFLOPS = 1006.0
+# The FP64 peak of the "alu" roofline is measured in each run on the GPU in
+# use (ppmlr_measure_pipe_rates: FP64 fused multiply-adds per second x 2
+# flops; 503 G FMA/s = 1006 GFLOP/s on a GB300 at 2070 MHz).  The nominal
+# dense FP64 rate of the part is 1.25 TFLOP/s.
 FP64_NOMINAL_GFLOPS = 1250.0
+
+
+def hbm_peak():
+    """Measured HBM copy bandwidth of this machine's GPUs (GB/s) and its source."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
 # Algorithmic FP64 flops (+, -, x, /, sqrt) per interior cell of one sweep on
 # the magnetosphere workload (PPM coefficients counted once per zone) and per
 # cell of the CFL pass, counted by the op-counting build of the oracle
@@ -347,7 +354,6 @@ def run_ours(args, rank, world, dist):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         n0 = ctx.launch_count
-        ctx.enable_timing(True)
         sampler = ClockSampler(local) if with_clocks else None
         if sampler:
             sampler.__enter__()
@@ -361,11 +367,21 @@ def run_ours(args, rank, world, dist):
         if sampler:
             sampler.__exit__(None, None, None)
         ms = e0.elapsed_time(e1)
-        kern = ctx.read_timing()
         launches = ctx.launch_count - n0
+        ctx.check()
+        # per-kernel times in a separate pass (events between the kernels stay
+        # out of the timed region above)
+        ctx.enable_timing(True)
+        ctx.step_cfl(prob.cfl, max(3, min(steps, 10)))
+        kern = ctx.read_timing()
         ctx.enable_timing(False)
         ctx.check()
         return ctx, ms, kern, launches, (sampler.summary() if sampler else None)
+
+    # ---- FP64 and FP32 pipe rates of this GPU (the FP64 roofline's peak)
+    rates = ppmlr.measure_pipe_rates(torch.cuda.current_stream().cuda_stream)
+    fp64_peak = 2.0 * rates["dfma_per_s"] * 1e-9
+    hbm, hbm_src = hbm_peak()
 
     # ---- main measurement
     ctx, ms, kern, launches, clocks = timed_run(prec, args.steps, args.warmup, with_clocks=True,
@@ -381,23 +397,22 @@ def run_ours(args, rank, world, dist):
     traffic = ncu_traffic(f"{args.precision}:{dom}", cells)
     if args.precision == "fp64":
         ach = FLOPS_PER_CELL[dom] * cells / (avg_ms * 1e-3) / 1e9
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": ach / FP64_PEAK_GFLOPS, "traffic": traffic, "kernel": f"sweep_{dom}" if dom != "cfl" else "cfl",
+        roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "GFLOP/s",
+                "frac": ach / fp64_peak, "traffic": traffic, "kernel": f"sweep_{dom}" if dom != "cfl" else "cfl",
                 "avg_launch_ms": avg_ms,
-                "peak_source": "measured FP64 FMA rate x 2 flops (bench_fp64_rate.cu, 152 SMs)",
+                "peak_source": "measured in this run: FP64 FMA rate x 2 flops (ppmlr_measure_pipe_rates)",
+                "pipe_rates": rates,
                 "peak_nominal": FP64_NOMINAL_GFLOPS, "frac_of_nominal": ach / FP64_NOMINAL_GFLOPS}
     else:
-        try:
-            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-                hbm, src = float(json.load(f)["hbm_gbs"]), "measured"
-        except Exception:
-            hbm, src = HBM_FALLBACK_GBS, "fallback"
         ach = BYTES_PER_CELL_SWEEP * cells / (avg_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": traffic, "kernel": f"sweep_{dom}", "avg_launch_ms": avg_ms, "peak_source": src}
+                "traffic": traffic, "kernel": f"sweep_{dom}", "avg_launch_ms": avg_ms, "peak_source": hbm_src}
     per_kernel = {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1],
-                      "hbm_frac_of_measured": BYTES_PER_CELL_SWEEP * cells / (v[0] / max(v[1], 1) * 1e-3) / 1e9 / 6787.2
+                      "hbm_frac_of_measured": BYTES_PER_CELL_SWEEP * cells / (v[0] / max(v[1], 1) * 1e-3) / 1e9 / hbm
                       if k != "cfl" else None} for k, v in kern.items()}
+    if args.precision == "fp64":
+        for k, v in per_kernel.items():
+            v["fp64_frac_of_measured"] = FLOPS_PER_CELL[k] * cells / (v["avg_ms"] * 1e-3) / 1e9 / fp64_peak
 
     # ---- the other precision, and its error against the FP64 path
     extra = {}
@@ -430,10 +445,10 @@ def run_ours(args, rank, world, dist):
         oavg = okern[odom][0] / max(okern[odom][1], 1)
         obytes = (128 if odom != "cfl" else 64) * cells
         oach = obytes / (oavg * 1e-3) / 1e9
-        oroof = {"bound": "hbm", "achieved": oach, "peak": 6787.2, "unit": "GB/s", "frac": oach / 6787.2,
+        oroof = {"bound": "hbm", "achieved": oach, "peak": hbm, "unit": "GB/s", "frac": oach / hbm,
                  "traffic": ncu_traffic(f"{key}:{odom}", cells),
                  "kernel": f"sweep_{odom}" if odom != "cfl" else "cfl", "avg_launch_ms": oavg,
-                 "peak_source": "measured"}
+                 "peak_source": hbm_src}
         extra[key] = {"value": ovalue, "ms_per_step": oms / args.steps, "roofline": oroof,
                       "tiles": {"C_L": octx.tiles(), "forms": octx.sweep_forms()},
                       "speedup_vs_fp64": (ovalue / value) if key == "mixed" else (value / ovalue),
@@ -535,7 +550,7 @@ def run_ours(args, rank, world, dist):
 
     # ---- large single domain 512x384x384 (finest 0.2 R_E), both precisions
     if not args.quick and not args.no_large and world == 1:
-        extra["large"] = run_large(args, barrier)
+        extra["large"] = run_large(args, barrier, fp64_peak)
 
     # ---- CPU baseline: the oracle on this host's cores, bounded sample
     cpu = None
@@ -666,9 +681,10 @@ def run_ensemble(args, fp64_value, barrier, rank=0, world=1, dist=None):
     out["kernels_avg_ms"] = kern
     dom = max(("x", "y", "z"), key=lambda k: kern[k])
     ach = BYTES_PER_CELL_SWEEP * cells / (kern[dom] * 1e-3) / 1e9
-    out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": 6787.2, "unit": "GB/s", "frac": ach / 6787.2,
+    hbm, hbm_src = hbm_peak()
+    out["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                        "traffic": ncu_traffic(f"ensemble:{dom}", cells),
-                       "kernel": f"sweep_ensemble_{dom}", "avg_launch_ms": kern[dom], "peak_source": "measured"}
+                       "kernel": f"sweep_ensemble_{dom}", "avg_launch_ms": kern[dom], "peak_source": hbm_src}
     # the same instances advanced one context at a time (no batching)
     ctxs = [ppmlr.Context.from_problem(p, ppmlr.PPMLR_MIXED) for p in probs]
     for c, p in zip(ctxs, probs):
@@ -708,7 +724,7 @@ def run_ensemble(args, fp64_value, barrier, rank=0, world=1, dist=None):
     return out
 
 
-def run_large(args, barrier):
+def run_large(args, barrier, fp64_peak):
     """512x384x384 stretched grid (finest 0.2 R_E), same extent and boundaries."""
     import torch
     from paper_1607_02214_gb300 import inputs, ppmlr
@@ -725,23 +741,26 @@ def run_large(args, barrier):
         stream = torch.cuda.current_stream()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
-        ctx.enable_timing(True)
         e0.record(stream)
         ctx.step_cfl(prob.cfl, steps)
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1)
+        ctx.check()
+        ctx.enable_timing(True)                 # per-kernel times: a separate pass
+        ctx.step_cfl(prob.cfl, max(3, min(steps, 6)))
         kern = ctx.read_timing()
         ctx.enable_timing(False)
         ctx.check()
+        hbm, _ = hbm_peak()
         per = {}
         for k, (tot, n) in kern.items():
             avg = tot / max(n, 1)
             byts = (BYTES_PER_CELL_SWEEP if k != "cfl" else 64) * cells
-            per[k] = {"avg_ms": avg, "hbm_frac_of_measured": byts / (avg * 1e-3) / 1e9 / 6787.2}
+            per[k] = {"avg_ms": avg, "hbm_frac_of_measured": byts / (avg * 1e-3) / 1e9 / hbm}
             if name == "fp64":
                 per[k]["fp64_gflops"] = FLOPS_PER_CELL[k] * cells / (avg * 1e-3) / 1e9
-                per[k]["fp64_frac_of_measured"] = per[k]["fp64_gflops"] / FP64_PEAK_GFLOPS
+                per[k]["fp64_frac_of_measured"] = per[k]["fp64_gflops"] / fp64_peak
         out[name] = {"value": cells * steps / (ms * 1e-3), "ms_per_step": ms / steps, "steps": steps,
                      "kernels": per, "tiles": ctx.tiles(), "forms": ctx.sweep_forms()}
         ctx.close()

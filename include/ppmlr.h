@@ -326,10 +326,12 @@ ppmlr_status ppmlr_set_time(ppmlr_ctx *ctx, double t);
  * ppmlr_checkpoint_save synchronises, writes `path`.part and renames it to
  * `path` (PPMLR_E_INVALID if the file cannot be written); it then reports
  * pending device flags.  ppmlr_checkpoint_load verifies the whole file
- * (magic, version, checksum, grid size and edges bit for bit against the
- * context's) before it replaces the state, step counter and simulated time;
- * otherwise PPMLR_E_INVALID with the state unchanged.  A checkpoint of any
- * precision loads into a context of any precision (the state is FP64).
+ * (magic, version, checksum, grid size, edges bit for bit and gamma against
+ * the context's) before it replaces the state, step counter and simulated
+ * time; otherwise PPMLR_E_INVALID with the state unchanged.  A checkpoint of
+ * any precision loads into a context of any precision (the state is FP64 in
+ * every form; ppmlr_checkpoint_info reports the writer's precision).  If a
+ * device copy fails while saving, no file (and no `path`.part) is left.
  * Loading a checkpoint of step k and continuing reproduces an uninterrupted
  * run bit for bit (state and time). */
 ppmlr_status ppmlr_checkpoint_save(ppmlr_ctx *ctx, const char *path);
@@ -402,6 +404,17 @@ const char *ppmlr_ensemble_last_error(const ppmlr_ens *ens);
 long long ppmlr_ensemble_launch_count(const ppmlr_ens *ens);
 void ppmlr_ensemble_destroy(ppmlr_ens *ens);
 
+/* Arithmetic-pipe rates of the current GPU (measurement support, no paper
+ * counterpart): instructions per second of FP64 fused multiply-add
+ * (rates[0]), FP64 add (rates[1]) and FP32 fused multiply-add (rates[2]),
+ * each from eight independent dependency chains per thread, 8 blocks of 256
+ * threads per SM, timed with CUDA events on `cuda_stream` (NULL = default)
+ * after a warm-up launch.  Allocates and frees a small output buffer;
+ * synchronises the stream.  The FP64 rate x 2 flops is the peak of the FP64
+ * sweeps' roofline.  Errors: PPMLR_E_INVALID (rates NULL), PPMLR_E_OOM,
+ * PPMLR_E_CUDA. */
+ppmlr_status ppmlr_measure_pipe_rates(void *cuda_stream, double rates[3]);
+
 /* Allocation-free CFL time step.  The paper has no counterpart: this entry
  * point exists for callers that must not allocate device memory -- a host
  * solver whose device memory belongs to another allocator that forbids raw
@@ -415,15 +428,19 @@ void ppmlr_ensemble_destroy(ppmlr_ens *ens);
  *   ppmlr_bc; cfl > 0; blocks: reduction blocks, 0 = automatic, at most 1024
  *   (the size of the static scratch; larger values return PPMLR_E_INVALID);
  *   dt_out: device pointer that receives dt; cuda_stream: stream (NULL =
- *   default).  Asynchronous.  Same formula and same double arithmetic as
- *   ppmlr_cfl_dt, so both give the same dt for the same state.
+ *   default).  Asynchronous.  The formula of ppmlr_cfl_dt in the exact double
+ *   arithmetic of the CPU reference: the dt equals that of a
+ *   PPMLR_FP64_EXACT context bit for bit, and that of a PPMLR_FP64 context
+ *   (contracted arithmetic) to roundoff.
  * Scratch: a static device array of 1056 doubles (8.4 KB) that every GPU that
  * loads the library holds until the process exits.  All calls on a device
  * share it and it keeps the last call's contents (its ticket counter is
  * cleared at the start of each call); calls whose kernels overlap on the GPU
  * race on it and must be serialised by the caller.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress) and
- * caches it; make that first call before capturing any stream work.
+ * caches it with the unique ID of the current CUDA context; a call under a
+ * different context of the device (after cudaDeviceReset, say) looks it up
+ * again.  Make the first call on a device before capturing any stream work.
  * Errors: PPMLR_E_INVALID (NULL pointer, n < 1, too many cells or blocks,
  * gamma <= 1, cfl <= 0), PPMLR_E_CUDA. */
 ppmlr_status ppmlr_cfl_dt_noalloc(const double *const U[8], const int n[3], const double *const width[3],

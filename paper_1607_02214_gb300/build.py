@@ -32,6 +32,7 @@ UNITS = {
     "cfl_mixed.cu": ["-fmad=true", "-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "ionosphere.cu": ["-fmad=true"],
     "selftest.cu": ["-fmad=true"],
+    "pipe_rate.cu": ["-fmad=true"],
 }
 
 

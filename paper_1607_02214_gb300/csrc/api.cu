@@ -1391,9 +1391,15 @@ ppmlr_status ppmlr_checkpoint_save(ppmlr_ctx *c, const char *path)
     }
     std::vector<double> buf((size_t)c->ncell);
     for (int v = 0; v < 8 && ok; v++) {
-        CK(c, cudaMemcpyAsync(buf.data(), c->U[v], sizeof(double) * buf.size(), cudaMemcpyDeviceToHost, c->stream),
-           "checkpoint copy");
-        CK(c, cudaStreamSynchronize(c->stream), "stream sync");
+        cudaError_t e = cudaMemcpyAsync(buf.data(), c->U[v], sizeof(double) * buf.size(), cudaMemcpyDeviceToHost,
+                                        c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {            // no partial file left behind
+            fclose(out.f);
+            out.f = nullptr;
+            remove(tmp.c_str());
+            return cuda_fail(c, e, "checkpoint copy");
+        }
         ok = fwrite(buf.data(), sizeof(double), buf.size(), out.f) == buf.size();
         hash.add(buf.data(), sizeof(double) * buf.size());
     }
@@ -1424,6 +1430,7 @@ ppmlr_status ppmlr_checkpoint_load(ppmlr_ctx *c, const char *path)
             for (int d = 0; d < 3; d++)
                 if (memcmp(edges[d].data(), c->edges[d].data(), sizeof(double) * edges[d].size()) != 0)
                     return "checkpoint: grid edges differ from the context's";
+            if (!(h.gamma == c->gamma)) return "checkpoint: gamma differs from the context's";
         }
         ce = cudaMemcpy(c->Un[v], data, sizeof(double) * (size_t)c->ncell, cudaMemcpyHostToDevice);
         return ce == cudaSuccess ? nullptr : "checkpoint: device copy failed";

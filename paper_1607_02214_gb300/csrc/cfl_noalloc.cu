@@ -18,11 +18,18 @@
 //
 // Set-up: the first call on each device looks up the device address of the
 // static array with cudaGetSymbolAddress (the host-side name of a __device__
-// array is only a stand-in, not a device address) and caches it per device.
-// Make that first call on a device before capturing any stream work.
+// array is only a stand-in, not a device address) and caches it per device
+// together with the unique ID of the CUDA context that was current then.  A
+// later call under another context of that device (after cudaDeviceReset, or
+// a context created and destroyed through the driver API) repeats the lookup,
+// since the module and its array may then sit at another address.  Make the
+// first call on a device before capturing any stream work.
 //
-// The arithmetic is the same IEEE double sequence as ppmlr_cfl_dt (compiled
-// without contraction), so both return the same dt for the same state.
+// The arithmetic is the IEEE double sequence of the exact-form CFL kernel
+// (compiled without contraction), which is the CPU reference's sequence: the
+// dt equals ppmlr_cfl_dt of a PPMLR_FP64_EXACT context bit for bit, and that
+// of the default PPMLR_FP64 context (contracted rate form) to roundoff.
+#include <cuda.h>
 #include <math.h>
 #include <mutex>
 
@@ -147,19 +154,54 @@ __global__ void __launch_bounds__(NA_THREADS) cfl_noalloc_kernel(NaArgs a)
     }
 }
 
-// Per-device cache of the scratch array's device address.
+// Per-device cache of the scratch array's device address, keyed by the unique
+// ID of the context it was looked up under.
 constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_na_mutex;
 double *g_na_ptr[NA_MAX_DEVICES] = {nullptr};
+unsigned long long g_na_ctx[NA_MAX_DEVICES] = {0};
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Unique ID of the current context (0: none current, or the driver offers no
+// context IDs -- then every call looks the address up again).
+unsigned long long current_context_id()
+{
+    static const CtxGetCurrentFn get_current = []() -> CtxGetCurrentFn {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        return cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+                       q == cudaDriverEntryPointSuccess
+                   ? (CtxGetCurrentFn)p
+                   : nullptr;
+    }();
+    static const CtxGetIdFn get_id = []() -> CtxGetIdFn {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        return cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+                       q == cudaDriverEntryPointSuccess
+                   ? (CtxGetIdFn)p
+                   : nullptr;
+    }();
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 cudaError_t scratch_address(int device, double **out)
 {
     std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[device]) {
+    const unsigned long long id = current_context_id();
+    if (!g_na_ptr[device] || id == 0 || id != g_na_ctx[device]) {
         double *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress((void **)&ptr, g_cfl_scratch);
+        cudaError_t e = cudaGetSymbolAddress((void **)&ptr, g_cfl_scratch);   // makes the context current if none was
         if (e != cudaSuccess) return e;
         g_na_ptr[device] = ptr;
+        g_na_ctx[device] = id != 0 ? id : current_context_id();
     }
     *out = g_na_ptr[device];
     return cudaSuccess;

@@ -1127,6 +1127,16 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
     }
     return false;
 }
+// After a bounded wait gave up: one more bounded wait on each buffer that still
+// has a box copy in flight, so that the block, when it returns, does not
+// leave the copy engine writing into shared memory it no longer owns.  If a
+// copy still has not landed after this second wait the block returns anyway
+// (FLAG_TIMEOUT is already raised and the status reports it).
+__device__ __forceinline__ void mbar_drain(unsigned long long *bar, unsigned parity)
+{
+    (void)mbar_wait(bar, parity);
+}
+
 // One 4D box (x, y, z, variable) of the state into shared memory.
 __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
                                             unsigned long long *bar)
@@ -1208,6 +1218,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value, TmaMinBlocks<R, PERSIST>
     if constexpr (!PERSIST) {                            // one tile per block, no loop
         if (!mbar_wait(&bar[0], 0u)) {
             if (threadIdx.x == 0) atomicOr(a.flags, FLAG_TIMEOUT);
+            mbar_drain(&bar[0], 0u);
             return;
         }
         sweep_tile<DIR, R, EX, const SweepArgs>(a, t, work, 0, stage0);
@@ -1228,6 +1239,10 @@ __global__ void __launch_bounds__(MaxThreads<R>::value, TmaMinBlocks<R, PERSIST>
         }
         if (!mbar_wait(&bar[b], phase[b])) {
             if (threadIdx.x == 0) atomicOr(a.flags, FLAG_TIMEOUT);
+            // no further prefetch; drain this tile's copy and the next tile's,
+            // issued above into the other buffer
+            mbar_drain(&bar[b], phase[b]);
+            if (tn < ntiles) mbar_drain(&bar[b ^ 1], phase[b ^ 1]);
             return;
         }
         phase[b] ^= 1u;
@@ -1358,6 +1373,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value, EnsMinBlocks<R>::value) 
     }
     if (!mbar_wait(&bar, 0u)) {
         if (threadIdx.x == 0) atomicOr(args.flags, FLAG_TIMEOUT);
+        mbar_drain(&bar, 0u);
         return;
     }
     sweep_tile<DIR, R, EX, const SweepArgs>(args, tile, smem_raw + stage_pad, e.flip, stage);

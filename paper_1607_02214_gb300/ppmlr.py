@@ -104,6 +104,7 @@ SIGNATURES = [
     ("ppmlr_cfl_dt_noalloc", c_int, [DPTR8, POINTER(c_int), POINTER(c_double) * 3, POINTER(c_double) * 3,
                                      c_double, c_double, c_double, c_double, c_double, c_int, POINTER(c_double),
                                      c_void_p]),
+    ("ppmlr_measure_pipe_rates", c_int, [c_void_p, POINTER(c_double)]),
 ]
 
 _lib = None
@@ -128,6 +129,16 @@ def __getattr__(name):          # module-level access to the raw ABI functions
     if name.startswith("ppmlr_"):
         return getattr(load(), name)
     raise AttributeError(name)
+
+
+def measure_pipe_rates(stream=None):
+    """Instructions per second of FP64 FMA, FP64 add and FP32 FMA on the
+    current GPU (ppmlr_measure_pipe_rates)."""
+    out = (c_double * 3)()
+    st = load().ppmlr_measure_pipe_rates(c_void_p(stream), out)
+    if st != PPMLR_OK:
+        raise PPMLRError(st, "ppmlr_measure_pipe_rates failed")
+    return {"dfma_per_s": out[0], "dadd_per_s": out[1], "ffma_per_s": out[2]}
 
 
 class PPMLRError(RuntimeError):

@@ -100,6 +100,13 @@ def test_damaged_or_foreign_checkpoint_is_refused(tmp_path):
     stretched = make_gpu(inputs.magnetosphere(n=(40, 34, 30), h0=0.9))   # same size, other edges
     with pytest.raises(ppmlr.PPMLRError):
         stretched.checkpoint_load(path)
+    pr_gamma = small_magnetosphere()                                       # same grid, other gamma
+    pr_gamma.gamma = 1.4
+    other_gamma = make_gpu(pr_gamma)
+    before = other_gamma.get_state()
+    with pytest.raises(ppmlr.PPMLRError):
+        other_gamma.checkpoint_load(path)
+    assert np.array_equal(other_gamma.get_state(), before)
 
 
 def test_long_exact_run_is_bit_identical_to_the_oracle():
