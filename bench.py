@@ -344,7 +344,10 @@ def run_ours(args, rank, world, dist):
             ctx.set_ionosphere(**iono)
         if args.launch_config and precision == prec:
             for axis, (C, L, form) in enumerate(args.launch_config):
-                ctx.set_tiles(axis, C, L)
+                if form == 3:                    # marching form: C is its chunk length
+                    ctx.set_march_chunk(axis, C)
+                else:
+                    ctx.set_tiles(axis, C, L)
                 ctx.set_sweep_form(axis, form)
         elif not args.no_autotune:
             ctx.autotune()

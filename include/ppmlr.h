@@ -183,8 +183,15 @@ ppmlr_status ppmlr_read_timing(ppmlr_ctx *ctx, double *total_ms, long long *laun
 ppmlr_status ppmlr_autotune(ppmlr_ctx *ctx, double *best_ms);
 
 /* Tile shape in use per direction: C (cells per chunk) and L (lanes);
- * C and L point to 3 entries each. */
+ * C and L point to 3 entries each.  A direction in the marching form (3)
+ * reports its chunk length and L = 32 (pencils per warp). */
 ppmlr_status ppmlr_get_tiles(ppmlr_ctx *ctx, int *C, int *L);
+
+/* Chunk length of the marching form along one axis (1 <= C <= n[axis];
+ * default n[axis], whole pencils): each warp walks C output cells of 32
+ * pencils and reads C + 14 input cells.  Results do not depend on it.
+ * PPMLR_E_INVALID (state unchanged) outside those bounds. */
+ppmlr_status ppmlr_set_march_chunk(ppmlr_ctx *ctx, int axis, int C);
 
 /* Force the tile shape of one direction (axis 0, 1, 2): C cells per chunk
  * (1 <= C <= n[axis]) and L lanes (L >= 1) with (C + 14) * L within the
@@ -287,8 +294,13 @@ ppmlr_status ppmlr_get_ionosphere(ppmlr_ctx *ctx, double *phi, double *jr);
  * the current tile's arithmetic; 2 = one block per tile with its input box
  * staged by the tensor memory accelerator.  Forms 1 and 2 apply to the y and
  * z sweeps with an even number of lanes, nx even and at most 256 positions
- * per tile.  The autotuner chooses the form with the tile shape; results do
- * not depend on it beyond roundoff on the contracted paths. */
+ * per tile; 3 = the marching form of PPMLR_MIXED: one thread per pencil
+ * walking it cell by cell, every stage of the scheme on the newest zone whose
+ * inputs are complete, neighbour values in register windows (no
+ * shared-memory exchange, no barriers), 32 pencils per warp; a context with
+ * contact steepening on runs the tile form 0 in its place.  The autotuner
+ * chooses the form with the tile shape; results do not depend on it beyond
+ * roundoff on the contracted paths. */
 ppmlr_status ppmlr_get_sweep_forms(ppmlr_ctx *ctx, int *form);
 /* Select a launch form for one axis (PPMLR_E_INVALID if not available). */
 ppmlr_status ppmlr_set_sweep_form(ppmlr_ctx *ctx, int axis, int form);

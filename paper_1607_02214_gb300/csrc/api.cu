@@ -44,7 +44,9 @@ struct ppmlr_ctx {
     int cfl_blocks;
     Tile tile[3];
     int mode[3];                 // 0: one block per tile; 1: persistent, TMA-staged input (y, z);
-                                 // 2: one block per tile, TMA-staged input (y, z)
+                                 // 2: one block per tile, TMA-staged input (y, z);
+                                 // 3: marching form (one thread per pencil; mixed path)
+    int march_C[3];              // marching form: output cells per chunk along each axis
     CUtensorMap tmap[3][2];      // per direction, per state buffer (input = buffer 0 or 1)
     int tma_blocks[3];
     size_t tma_smem[3];
@@ -405,7 +407,7 @@ ppmlr_status ppmlr_create(const ppmlr_grid *grid, double gamma, const ppmlr_bc *
         if (e != cudaSuccess) { cudaFree(c->geof); cudaFree(c->geo); cudaFree(c->state); delete c; return PPMLR_E_CUDA; }
     }
     size_t rs = prec == PPMLR_MIXED ? sizeof(float) : sizeof(double);
-    for (int d = 0; d < 3; d++) { c->tile[d] = choose_tile(d, c->n, rs); c->mode[d] = 0; }
+    for (int d = 0; d < 3; d++) { c->tile[d] = choose_tile(d, c->n, rs); c->mode[d] = 0; c->march_C[d] = c->n[d]; }
     c->sms = dev_sms;
     c->bd = nullptr;
     c->inner_mask = nullptr;
@@ -571,7 +573,14 @@ static ppmlr_status launch_one_sweep(ppmlr_ctx *c, int d, double dt, const doubl
     for (int k = 0; k < 8; k++) a.inflowf[k] = (float)a.inflow[k];
     int rec = timing_begin(c, d);
     cudaError_t e;
-    if (c->mode[d] != 0) {
+    if (c->mode[d] == 3 && !c->steepen) {          // marching form (no contact steepening)
+        a.C = c->march_C[d];
+        a.nchunk = (a.N + a.C - 1) / a.C;
+        a.L = 32;
+        a.NP = a.C + 2 * GH;
+        a.ngx = d == 0 ? (int)(((long long)c->n[1] * c->n[2] + 31) / 32) : (c->n[0] + 31) / 32;
+        e = sweep_launchers(c->prec).march(d, a, c->stream);
+    } else if (c->mode[d] == 1 || c->mode[d] == 2) {
         const int b = c->U[0] == c->state ? 0 : 1;     // buffer holding the input state
         e = sweep_launchers(c->prec).tma(d, c->mode[d] == 1, a, c->tmap[d][b], c->tma_blocks[d], t.threads,
                                          c->tma_smem[d], c->stream);
@@ -754,7 +763,10 @@ ppmlr_status ppmlr_get_diagnostics(ppmlr_ctx *c, long long *step, long long *flo
     return PPMLR_OK;
 }
 
-// Per-process cache of tuned tile shapes: (dir, nx, ny, nz, prec) -> (C, L).
+// The marching form serves the mixed path without contact steepening.
+static bool march_eligible(const ppmlr_ctx *c) { return c->prec == PPMLR_MIXED && !c->steepen; }
+
+// Per-process cache of tuned tile shapes: (dir, nx, ny, nz, prec) -> (C, L, form).
 static std::mutex g_tune_mutex;
 static std::map<std::tuple<int, int, int, int, int>, std::tuple<int, int, int>> g_tune_cache;
 
@@ -782,9 +794,14 @@ ppmlr_status ppmlr_autotune(ppmlr_ctx *c, double *best_ms)
             std::lock_guard<std::mutex> lk(g_tune_mutex);
             auto it = g_tune_cache.find(key);
             if (it != g_tune_cache.end()) {
-                c->tile[d] = make_tile(d, c->n, rs, std::get<0>(it->second), std::get<1>(it->second));
                 const int f = std::get<2>(it->second);
-                c->mode[d] = f != 0 && setup_tma(c, d, f) ? f : 0;
+                if (f == 3) {
+                    c->march_C[d] = std::get<0>(it->second);
+                    c->mode[d] = 3;
+                } else {
+                    c->tile[d] = make_tile(d, c->n, rs, std::get<0>(it->second), std::get<1>(it->second));
+                    c->mode[d] = f != 0 && setup_tma(c, d, f) ? f : 0;
+                }
                 continue;
             }
         }
@@ -812,16 +829,31 @@ ppmlr_status ppmlr_autotune(ppmlr_ctx *c, double *best_ms)
                 if (tma_eligible(c, d, make_tile(d, c->n, rs, cl.first, cl.second), f))
                     trials.push_back({cl.first, cl.second, f});
         }
+        const int keep_march = c->march_C[d];
+        if (march_eligible(c))            // marching form: whole pencils or 2..4 equal chunks
+            for (int k = 1; k <= 4; k++) {
+                const int C = (N + k - 1) / k;
+                if (k > 1 && C < 32) break;
+                trials.push_back({C, 32, 3});
+            }
         for (auto &tr : trials) {
-            c->tile[d] = make_tile(d, c->n, rs, std::get<0>(tr), std::get<1>(tr));
             const int f = std::get<2>(tr);
-            c->mode[d] = f != 0 && setup_tma(c, d, f) ? f : 0;
-            if (c->mode[d] != f) continue;
+            if (f == 3) {
+                c->march_C[d] = std::get<0>(tr);
+                c->mode[d] = 3;
+            } else {
+                c->tile[d] = make_tile(d, c->n, rs, std::get<0>(tr), std::get<1>(tr));
+                c->mode[d] = f != 0 && setup_tma(c, d, f) ? f : 0;
+                if (c->mode[d] != f) continue;
+            }
             float tot = 0.0f;
             for (int rep = 0; rep < 3; rep++) {
                 CK(c, cudaEventRecord(t0, c->stream), "event");
                 st = launch_one_sweep(c, d, 0.0, c->dt_dev);
-                if (st != PPMLR_OK) { c->tile[d] = keep; c->mode[d] = keep_mode; return st; }
+                if (st != PPMLR_OK) {
+                    c->tile[d] = keep; c->mode[d] = keep_mode; c->march_C[d] = keep_march;
+                    return st;
+                }
                 CK(c, cudaEventRecord(t1, c->stream), "event");
                 CK(c, cudaEventSynchronize(t1), "event sync");
                 // undo the buffer swap of launch_one_sweep: the state stays in place
@@ -832,9 +864,16 @@ ppmlr_status ppmlr_autotune(ppmlr_ctx *c, double *best_ms)
             }
             if (tot < best) { best = tot; pick = tr; }
         }
-        c->tile[d] = make_tile(d, c->n, rs, std::get<0>(pick), std::get<1>(pick));
         const int fp = std::get<2>(pick);
-        c->mode[d] = fp != 0 && setup_tma(c, d, fp) ? fp : 0;
+        if (fp == 3) {
+            c->tile[d] = keep;
+            c->march_C[d] = std::get<0>(pick);
+            c->mode[d] = 3;
+        } else {
+            c->tile[d] = make_tile(d, c->n, rs, std::get<0>(pick), std::get<1>(pick));
+            c->march_C[d] = keep_march;
+            c->mode[d] = fp != 0 && setup_tma(c, d, fp) ? fp : 0;
+        }
         if (best_ms) best_ms[d] = best / 2.0f;
         std::lock_guard<std::mutex> lk(g_tune_mutex);
         g_tune_cache[key] = pick;
@@ -852,7 +891,21 @@ ppmlr_status ppmlr_autotune(ppmlr_ctx *c, double *best_ms)
 ppmlr_status ppmlr_get_tiles(ppmlr_ctx *c, int *C, int *L)
 {
     if (!c || !C || !L) return PPMLR_E_INVALID;
-    for (int d = 0; d < 3; d++) { C[d] = c->tile[d].C; L[d] = c->tile[d].L; }
+    for (int d = 0; d < 3; d++) {
+        const bool m = c->mode[d] == 3 && !c->steepen;
+        C[d] = m ? c->march_C[d] : c->tile[d].C;
+        L[d] = m ? 32 : c->tile[d].L;
+    }
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_set_march_chunk(ppmlr_ctx *c, int axis, int C)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (axis < 0 || axis > 2) return fail(c, PPMLR_E_INVALID, "set_march_chunk: bad axis");
+    if (C < 1 || C > c->n[axis]) return fail(c, PPMLR_E_INVALID, "set_march_chunk: need 1 <= C <= n[axis]");
+    c->march_C[axis] = C;
+    drop_graphs(c);
     return PPMLR_OK;
 }
 
@@ -1148,9 +1201,14 @@ ppmlr_status ppmlr_get_sweep_forms(ppmlr_ctx *c, int *form)
 ppmlr_status ppmlr_set_sweep_form(ppmlr_ctx *c, int axis, int form)
 {
     if (!c) return PPMLR_E_INVALID;
-    if (axis < 0 || axis > 2 || form < 0 || form > 2) return fail(c, PPMLR_E_INVALID, "set_sweep_form: bad axis or form");
+    if (axis < 0 || axis > 2 || form < 0 || form > 3) return fail(c, PPMLR_E_INVALID, "set_sweep_form: bad axis or form");
     drop_graphs(c);
     if (form == 0) { c->mode[axis] = 0; return PPMLR_OK; }
+    if (form == 3) {
+        if (c->prec != PPMLR_MIXED) return fail(c, PPMLR_E_INVALID, "the marching form (3) is a PPMLR_MIXED form");
+        c->mode[axis] = 3;
+        return PPMLR_OK;
+    }
     if (const char *why = setup_tma_why(c, axis, form)) return fail(c, PPMLR_E_INVALID, why);
     c->mode[axis] = form;
     return PPMLR_OK;

@@ -2,6 +2,7 @@
 // kernel translation unit instantiates one variant with its own compiler
 // flags and exports a SweepLaunchers table.
 #pragma once
+#include "march.cuh"
 #include "sweep.cuh"
 
 namespace ppmlr {
@@ -156,6 +157,21 @@ struct SweepVariant {
             return cudaErrorNotSupported;
         }
     }
+    template <int DIR>
+    static cudaError_t march_dir(const SweepArgs &a, cudaStream_t s)
+    {
+        const int warps = march_warps(a, DIR);
+        const int blocks = (warps + MARCH_WARPS - 1) / MARCH_WARPS;
+        sweep_march_kernel<DIR><<<blocks, 32 * MARCH_WARPS, march_smem_bytes(), s>>>(a);
+        return cudaGetLastError();
+    }
+    static cudaError_t march(int dir, const SweepArgs &a, cudaStream_t s)
+    {
+        if constexpr (std::is_same<R, float>::value && !EX)
+            return dir == 0 ? march_dir<0>(a, s) : dir == 1 ? march_dir<1>(a, s) : march_dir<2>(a, s);
+        else
+            return cudaErrorNotSupported;
+    }
     static int tma_per_sm(int dir, int persist, int threads, size_t smem)
     {
         if (persist)
@@ -187,7 +203,7 @@ struct SweepVariant {
     static constexpr SweepLaunchers table()
     {
         return {single, ens, param, per_sm, tma, tma_per_sm,
-                std::is_same<R, double>::value ? &dipole_table : nullptr, ens_tma, ens_tma_per_sm};
+                std::is_same<R, double>::value ? &dipole_table : nullptr, ens_tma, ens_tma_per_sm, march};
     }
 };
 

@@ -178,6 +178,9 @@ struct SweepLaunchers {
     cudaError_t (*ens_tma)(int dir, const EnsSweepArgs &e, const CUtensorMap *maps, int blocks, int threads,
                            size_t smem, cudaStream_t s);
     int (*ens_tma_per_sm)(int dir, int threads, size_t smem);
+    // marching form (one thread per pencil; PPMLR_MIXED only, else cudaErrorNotSupported):
+    // `a` carries the chunk length C, nchunk and the lane groups ngx (of 32)
+    cudaError_t (*march)(int dir, const SweepArgs &a, cudaStream_t s);
 };
 
 // cuTensorMapEncodeTiled from the driver (null if unavailable)

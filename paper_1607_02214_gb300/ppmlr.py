@@ -105,6 +105,7 @@ SIGNATURES = [
                                      c_double, c_double, c_double, c_double, c_double, c_int, POINTER(c_double),
                                      c_void_p]),
     ("ppmlr_measure_pipe_rates", c_int, [c_void_p, POINTER(c_double)]),
+    ("ppmlr_set_march_chunk", c_int, [c_void_p, c_int, c_int]),
 ]
 
 _lib = None
@@ -381,6 +382,10 @@ class Context:
 
     def set_tiles(self, axis, C, L):
         return self._check(load().ppmlr_set_tiles(self._h, int(axis), int(C), int(L)))
+
+    def set_march_chunk(self, axis, C):
+        """Chunk length of the marching form (3) along one axis."""
+        return self._check(load().ppmlr_set_march_chunk(self._h, int(axis), int(C)))
 
     def sweep_forms(self):
         f = (c_int * 3)()
