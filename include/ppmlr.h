@@ -381,7 +381,10 @@ ppmlr_status ppmlr_ensemble_time_kernels(ppmlr_ens *ens, double cfl, int nsteps,
  * tiles from a work counter; 1: one block per tile, arguments from a device
  * table; 2: one block per tile, arguments of all instances in the kernel
  * parameter, up to 64 instances; 3: one block per tile with the input box
- * staged by TMA), timed out of place; best_ms: 3 entries or NULL. */
+ * staged by TMA; 4: persistent blocks taking tiles from a work counter,
+ * arguments of all instances in the kernel parameter, up to 64 instances),
+ * timed out of place; a persistent form (0 or 4) is kept when it is within
+ * 2 % of the fastest; best_ms: 3 entries or NULL. */
 ppmlr_status ppmlr_ensemble_autotune(ppmlr_ens *ens, double *best_ms);
 /* Fix the launch of one sweep direction instead of autotuning it: form 0 =
  * persistent blocks taking tiles from a work counter, 1 = one block per tile
@@ -390,7 +393,9 @@ ppmlr_status ppmlr_ensemble_autotune(ppmlr_ens *ens, double *best_ms);
  * tile with the tile's input box staged by the tensor memory accelerator
  * through per-instance tensor maps (every instance needs nx even and at most
  * 256 positions per tile; along x also C even and ny a multiple of the
- * lanes); budget = positions x lanes per
+ * lanes), 4 = persistent blocks taking tiles from a work counter with the
+ * arguments of all instances in the kernel parameter (at most 64
+ * instances); budget = positions x lanes per
  * tile (15..448 for the FP64 forms, ..512 for PPMLR_MIXED).  Tiles: whole
  * pencils when they fit (else equal chunks), then as many lanes as fit; for
  * y and z, budget + 10000 selects the other rule: the most lanes (a power of

@@ -571,6 +571,7 @@ static ppmlr_status launch_one_sweep(ppmlr_ctx *c, int d, double dt, const doubl
     a.cxf = c->cf[0]; a.cyf = c->cf[1]; a.czf = c->cf[2];
     a.gammaf = (float)a.gamma; a.p_minf = (float)a.p_min; a.Mf = (float)a.M; a.r_innerf = (float)a.r_inner;
     for (int k = 0; k < 8; k++) a.inflowf[k] = (float)a.inflow[k];
+    a.p_reff = c->prec == PPMLR_MIXED ? mixed_pressure_reference(c->bc) : 0.0f;
     int rec = timing_begin(c, d);
     cudaError_t e;
     if (c->mode[d] == 3 && !c->steepen) {          // marching form (no contact steepening)

@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "ppmlr_internal.h"
@@ -51,7 +52,8 @@ struct ppmlr_ens {
     int lanes_first[3];          // y/z tile rule: 1 = most lanes, pencils chunked to >= 48 cells
     int mode[3];                 // 0: persistent work queue, 1: one block per tile (table),
                                  // 2: one block per tile (arguments in the kernel parameter),
-                                 // 3: one block per tile, input box staged by TMA (y, z)
+                                 // 3: one block per tile, input box staged by TMA (y, z),
+                                 // 4: persistent work queue, arguments in the kernel parameter
     CUtensorMap *d_maps[3];      // mode 3: per instance the maps of its two state sets
     std::vector<SweepArgs> host_args[3];
     std::vector<Tile> tiles[3];
@@ -160,10 +162,13 @@ static bool plan_direction(ppmlr_ens *e, int d, int maxt, int mode, bool lanes_f
     e->threads[d] = thr;
     e->smem[d] = sm;
     e->total_tiles[d] = total;
-    int per_sm = sweep_launchers(e->prec).per_sm(d, thr, sm);
+    if (mode == 4 && e->count > ENS_PARAM_MAX) return false;
+    const bool persist = mode == 0 || mode == 4;
+    int per_sm = mode == 4 ? sweep_launchers(e->prec).param_persist_per_sm(d, thr, sm)
+                           : sweep_launchers(e->prec).per_sm(d, thr, sm);
     int b = per_sm * e->sms;
-    e->blocks[d] = (mode != 0 || b > total) ? total : b;
-    if (mode == 0 && e->blocks[d] == total && total > 1) e->blocks[d] = total - 1;   // keep it persistent
+    e->blocks[d] = (!persist || b > total) ? total : b;
+    if (persist && e->blocks[d] == total && total > 1) e->blocks[d] = total - 1;   // keep it persistent
     return true;
 }
 
@@ -236,6 +241,7 @@ static ppmlr_status upload_direction(ppmlr_ens *e, int d)
         a.flags = e->flags; a.floors = e->floors;
         a.gammaf = (float)a.gamma; a.p_minf = (float)a.p_min; a.Mf = (float)a.M; a.r_innerf = (float)a.r_inner;
         for (int k = 0; k < 8; k++) a.inflowf[k] = (float)a.inflow[k];
+        a.p_reff = e->prec == PPMLR_MIXED ? mixed_pressure_reference(b) : 0.0f;
         args[i] = a;
         first[i] = acc;
         acc += t.ntiles;
@@ -257,7 +263,7 @@ static ppmlr_status upload_direction(ppmlr_ens *e, int d)
 static cudaError_t launch_dir(ppmlr_ens *e, int d, int flip, unsigned int *queue, cudaStream_t s)
 {
     const SweepLaunchers &L = sweep_launchers(e->prec);
-    if (e->mode[d] == 2) {
+    if (e->mode[d] == 2 || e->mode[d] == 4) {
         EnsSweepParams p;
         memset(&p, 0, sizeof(p));
         for (int i = 0; i < e->count; i++) p.args[i] = e->host_args[d][i];
@@ -265,6 +271,8 @@ static cudaError_t launch_dir(ppmlr_ens *e, int d, int flip, unsigned int *queue
         for (int i = 0; i < e->count; i++) { p.first_tile[i] = acc; acc += e->tiles[d][i].ntiles; }
         p.count = e->count;
         p.flip = flip;
+        p.total_tiles = acc;
+        if (e->mode[d] == 4) return L.param_persist(d, p, queue, e->blocks[d], e->threads[d], e->smem[d], s);
         return L.param(d, p, e->blocks[d], e->threads[d], e->smem[d], s);
     }
     EnsSweepArgs ea{e->d_args[d], e->d_first_tile[d], e->count, e->total_tiles[d], flip, queue};
@@ -606,9 +614,11 @@ ppmlr_status ppmlr_ensemble_autotune(ppmlr_ens *e, double *best_ms)
         float best = 1e30f;
         int best_t = e->maxt[d], best_m = e->mode[d], best_r = e->lanes_first[d];
         const int rules = d == 0 ? 1 : 2;
-        for (int k = 0; k < 4 * nc * rules; k++) {
-            const int mode = (k / nc) % 4, rule = k / (4 * nc);
-            if (mode == 2 && e->count > ENS_PARAM_MAX) continue;
+        // per candidate (budget, form, tile rule) the time of two sweeps
+        std::vector<std::tuple<float, int, int, int>> timed;
+        for (int k = 0; k < 5 * nc * rules; k++) {
+            const int mode = (k / nc) % 5, rule = k / (5 * nc);
+            if ((mode == 2 || mode == 4) && e->count > ENS_PARAM_MAX) continue;
             if (!plan_direction(e, d, cands[k % nc], mode, rule == 1)) continue;
             ppmlr_status st = upload_direction(e, d);
             if (st != PPMLR_OK) return st;
@@ -623,7 +633,21 @@ ppmlr_status ppmlr_ensemble_autotune(ppmlr_ens *e, double *best_ms)
                 cudaEventElapsedTime(&ms, t0, t1);
                 if (rep > 0) tot += ms;
             }
+            timed.push_back({tot, cands[k % nc], mode, rule});
             if (tot < best) { best = tot; best_t = cands[k % nc]; best_m = mode; best_r = rule; }
+        }
+        // a persistent form (one launch of resident blocks taking tiles from
+        // the work counter) is kept when it is within 2 % of the fastest
+        if (best_m != 0 && best_m != 4) {
+            float pbest = 1e30f;
+            for (auto &tc : timed)
+                if ((std::get<2>(tc) == 0 || std::get<2>(tc) == 4) && std::get<0>(tc) < pbest) {
+                    pbest = std::get<0>(tc);
+                    if (pbest <= 1.02f * best) {
+                        best_t = std::get<1>(tc); best_m = std::get<2>(tc); best_r = std::get<3>(tc);
+                    }
+                }
+            if (pbest <= 1.02f * best) best = pbest;
         }
         plan_direction(e, d, best_t, best_m, best_r == 1);
         ppmlr_status st = upload_direction(e, d);
@@ -695,10 +719,11 @@ ppmlr_status ppmlr_ensemble_set_launch(ppmlr_ens *e, int axis, int form, int bud
     const int maxb = e->prec == PPMLR_MIXED ? MAXT : MAXT_F64;
     const bool lanes_first = budget >= 10000;
     if (lanes_first) budget -= 10000;
-    if (axis < 0 || axis > 2 || form < 0 || form > 3 || budget < 2 * GH + 1 || budget > maxb ||
+    if (axis < 0 || axis > 2 || form < 0 || form > 4 || budget < 2 * GH + 1 || budget > maxb ||
         (lanes_first && axis == 0))
         return efail(e, PPMLR_E_INVALID, "set_launch: bad axis, form or budget");
-    if (form == 2 && e->count > ENS_PARAM_MAX) return efail(e, PPMLR_E_INVALID, "set_launch: form 2 takes at most 64 instances");
+    if ((form == 2 || form == 4) && e->count > ENS_PARAM_MAX)
+        return efail(e, PPMLR_E_INVALID, "set_launch: forms 2 and 4 take at most 64 instances");
     if (!plan_direction(e, axis, budget, form, lanes_first))
         return efail(e, PPMLR_E_INVALID, "set_launch: the TMA form does not fit every instance along this axis");
     ppmlr_status st = upload_direction(e, axis);

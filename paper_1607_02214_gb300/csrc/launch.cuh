@@ -47,6 +47,43 @@ struct SweepVariant {
         return cudaGetLastError();
     }
     template <int DIR>
+    static cudaError_t param_persist_dir(const EnsSweepParams &p, unsigned int *queue, int blocks, int threads,
+                                         size_t smem, cudaStream_t s)
+    {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t r = cudaFuncSetAttribute(sweep_ensemble_param_persist_kernel<DIR, R, EX>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            if (r != cudaSuccess) return r;
+            attr = true;
+        }
+        sweep_ensemble_param_persist_kernel<DIR, R, EX><<<blocks, threads, smem, s>>>(p, queue);
+        return cudaGetLastError();
+    }
+    template <int DIR>
+    static int param_persist_per_sm_dir(int threads, size_t smem)
+    {
+        cudaFuncSetAttribute(sweep_ensemble_param_persist_kernel<DIR, R, EX>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_ensemble_param_persist_kernel<DIR, R, EX>,
+                                                          threads, smem) != cudaSuccess)
+            return 1;
+        return n > 0 ? n : 1;
+    }
+    static cudaError_t param_persist(int dir, const EnsSweepParams &p, unsigned int *queue, int blocks, int threads,
+                                     size_t smem, cudaStream_t s)
+    {
+        return dir == 0 ? param_persist_dir<0>(p, queue, blocks, threads, smem, s)
+               : dir == 1 ? param_persist_dir<1>(p, queue, blocks, threads, smem, s)
+                          : param_persist_dir<2>(p, queue, blocks, threads, smem, s);
+    }
+    static int param_persist_per_sm(int dir, int threads, size_t smem)
+    {
+        return dir == 0 ? param_persist_per_sm_dir<0>(threads, smem)
+               : dir == 1 ? param_persist_per_sm_dir<1>(threads, smem) : param_persist_per_sm_dir<2>(threads, smem);
+    }
+    template <int DIR>
     static int per_sm_dir(int threads, size_t smem)
     {
         cudaFuncSetAttribute(sweep_ensemble_kernel<DIR, R, EX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -203,7 +240,8 @@ struct SweepVariant {
     static constexpr SweepLaunchers table()
     {
         return {single, ens, param, per_sm, tma, tma_per_sm,
-                std::is_same<R, double>::value ? &dipole_table : nullptr, ens_tma, ens_tma_per_sm, march};
+                std::is_same<R, double>::value ? &dipole_table : nullptr, ens_tma, ens_tma_per_sm,
+                param_persist, param_persist_per_sm, march};
     }
 };
 

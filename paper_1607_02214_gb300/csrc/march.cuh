@@ -169,30 +169,38 @@ __global__ void __launch_bounds__(32 * MARCH_WARPS, 1) sweep_march_kernel(const 
             dipole_f(a.Mf, DIR == 0 ? pa : pxl, DIR == 1 ? pa : pyl, DIR == 2 ? pa : pzl, B);
             Bd0f = B[DIR]; Bd1f = B[T1]; Bd2f = B[T2];
             const bool out_cell = g >= g0 && g < g0 + Ce;
+            float pabs;                                 // p; the windows hold p - p_reff
             if (source_cell(g) < 0) {
                 const float *f = a.inflowf;
                 rho0 = f[0];
                 u0 = f[1 + DIR]; v1_0 = f[1 + T1]; v2_0 = f[1 + T2];
                 Bn0 = f[4 + DIR] - Bd0f; B1_0 = f[4 + T1] - Bd1f; B2_0 = f[4 + T2] - Bd2f;
-                p0 = f[7];
-                e0 = p0 / (gm1 * rho0) + 0.5f * (u0 * u0 + v1_0 * v1_0 + v2_0 * v2_0) +
+                pabs = f[7];
+                p0 = f[7] - a.p_reff;
+                e0 = pabs / (gm1 * rho0) + 0.5f * (u0 * u0 + v1_0 * v1_0 + v2_0 * v2_0) +
                      0.5f * (Bn0 * Bn0 + B1_0 * B1_0 + B2_0 * B2_0) / rho0;
             } else {
                 df q[8];
 #pragma unroll
                 for (int v = 0; v < 8; v++) q[v] = split_double(cur[v]);
-                p0 = pressure_df(q[0], q[1 + DIR], q[1 + T1], q[1 + T2], q[4 + DIR], q[4 + T1], q[4 + T2], q[7],
-                                 gm1);
+                const df pp = pressure_df_pair(q[0], q[1 + DIR], q[1 + T1], q[1 + T2], q[4 + DIR], q[4 + T1],
+                                               q[4 + T2], q[7], gm1);
+                pabs = pp.h + pp.l;
+                p0 = (pp.h - a.p_reff) + pp.l;
                 rho0 = q[0].h;
                 const float ir = 1.0f / rho0;
                 u0 = q[1 + DIR].h * ir; v1_0 = q[1 + T1].h * ir; v2_0 = q[1 + T2].h * ir;
                 Bn0 = q[4 + DIR].h; B1_0 = q[4 + T1].h; B2_0 = q[4 + T2].h;
                 e0 = q[7].h * ir;
             }
-            if (p0 < a.p_minf) { p0 = a.p_minf; floors += (out_cell && lane_ok) ? 1u : 0u; }
+            if (pabs < a.p_minf) {
+                pabs = a.p_minf;
+                p0 = a.p_minf - a.p_reff;
+                floors += (out_cell && lane_ok) ? 1u : 0u;
+            }
             dm0 = rho0 * wf[g];
-            Pt0 = p0 + 0.5f * (Bn0 * Bn0 + B1_0 * B1_0 + B2_0 * B2_0);
-            W0 = rho0 * fsqrt<float, false>(fast2<float, false>(rho0, p0, Bn0, B1_0, B2_0, gam));
+            Pt0 = pabs + 0.5f * (Bn0 * Bn0 + B1_0 * B1_0 + B2_0 * B2_0);
+            W0 = rho0 * fsqrt<float, false>(fast2<float, false>(rho0, pabs, Bn0, B1_0, B2_0, gam));
             AY0 = v2_0 * Bd0f - u0 * Bd2f;
             AZ0 = u0 * Bd1f - v1_0 * Bd0f;
         }
@@ -286,10 +294,14 @@ __global__ void __launch_bounds__(32 * MARCH_WARPS, 1) sweep_march_kernel(const 
             const float Bnf = 0.5f * (Bn4 + Bn3);
             const float PL = slP[6] + 0.5f * (slP[4] * slP[4] + slP[5] * slP[5]);
             const float PR = sr[6] + 0.5f * (sr[4] * sr[4] + sr[5] * sr[5]);
-            float WL = slP[0] * sqrtf(fast2<float, false>(slP[0], slP[6], Bnf, slP[4], slP[5], gam));
-            float WR = sr[0] * sqrtf(fast2<float, false>(sr[0], sr[6], Bnf, sr[4], sr[5], gam));
-            if (a.riemann_iters > 0 && PL > 0.0f && PR > 0.0f)
-                two_shock<float, false>(a.riemann_iters, slP[1], sr[1], PL, PR, gam, WL, WR);
+            // (PL, PR, P* and S* relative to p_reff; absolute pressures for the
+            // impedances, the nonlinear solver and the energy flux)
+            const float pref = a.p_reff;
+            float WL = slP[0] * sqrtf(fast2<float, false>(slP[0], slP[6] + pref, Bnf, slP[4], slP[5], gam));
+            float WR = sr[0] * sqrtf(fast2<float, false>(sr[0], sr[6] + pref, Bnf, sr[4], sr[5], gam));
+            const float PLa = PL + pref, PRa = PR + pref;
+            if (a.riemann_iters > 0 && PLa > 0.0f && PRa > 0.0f)
+                two_shock<float, false>(a.riemann_iters, slP[1], sr[1], PLa, PRa, gam, WL, WR);
             const float iW = 1.0f / (WL + WR);
             const float us = (WL * slP[1] + WR * sr[1] + PL - PR) * iW;
             const float Ps = (WR * PL + WL * PR + WL * WR * (slP[1] - sr[1])) * iW;
@@ -314,7 +326,7 @@ __global__ void __launch_bounds__(32 * MARCH_WARPS, 1) sweep_march_kernel(const 
             }
             rs[0] = us; rs[1] = Ss; rs[2] = sst[0]; rs[3] = sst[1];
             rs[4] = Bnf * vst[0]; rs[5] = Bnf * vst[1];
-            rs[6] = Ss * us - sst[0] * vst[0] - sst[1] * vst[1];
+            rs[6] = (Ss + pref) * us - sst[0] * vst[0] - sst[1] * vst[1];
         }
 
         // ---------------- S6: Lagrangian update of zone g-4 (edges g-9/2 | g-7/2)

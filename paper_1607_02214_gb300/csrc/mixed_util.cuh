@@ -105,6 +105,22 @@ __device__ __forceinline__ float pressure_df(df rho, df m0, df m1, df m2, df b0,
     return gm1 * (q.h + q.l);
 }
 
+// The same pressure as a float pair h + l (about 44-48 significant bits):
+// gm1 times the double-float difference, the product split by the FMA
+// two-product.  The mixed sweeps form p - p_ref from it without first
+// rounding p to a float.
+__device__ __forceinline__ df pressure_df_pair(df rho, df m0, df m1, df m2, df b0, df b1, df b2, df E, float gm1)
+{
+    const df mm = df_add(df_add(df_sqr(m0), df_sqr(m1)), df_sqr(m2));
+    const df bb = df_add(df_add(df_sqr(b0), df_sqr(b1)), df_sqr(b2));
+    df t = df_add(df_div(mm, rho), bb);
+    t.h *= 0.5f;
+    t.l *= 0.5f;
+    const df q = df_add(E, df_neg(t));
+    const float ph = gm1 * q.h;
+    return {ph, fmaf(gm1, q.h, -ph) + gm1 * q.l};
+}
+
 // Earth dipole in float (moment along -z).
 __device__ __forceinline__ void dipole_f(float M, float x, float y, float z, float *B)
 {

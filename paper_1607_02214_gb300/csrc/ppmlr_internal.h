@@ -58,7 +58,23 @@ struct SweepArgs {
     const float *cxf, *cyf, *czf;
     float gammaf, p_minf, Mf, r_innerf;
     float inflowf[8];
+    // mixed path: the sweeps reconstruct and trace p - p_reff and form the
+    // Riemann problem's total pressures relative to it (the scheme is
+    // invariant under a constant pressure offset; float differences of
+    // pressures near p_reff keep their digits).  0 for the FP64 forms.
+    float p_reff;
 };
+
+// Pressure offset p_reff of the mixed sweeps: the inflow pressure when any
+// face is an inflow face (the solar wind fills most of a magnetosphere
+// domain), else 0 (the plain arithmetic).
+inline float mixed_pressure_reference(const ppmlr_bc &bc)
+{
+    for (int d = 0; d < 3; d++)
+        for (int s = 0; s < 2; s++)
+            if (bc.face[d][s] == PPMLR_BC_INFLOW) return (float)bc.inflow.p;
+    return 0.0f;
+}
 
 // Persistent ensemble sweep: per-instance arguments (input state = U, output
 // = Un; flip = 1 swaps them), the first global tile of every instance and a
@@ -80,6 +96,7 @@ struct EnsSweepParams {
     int first_tile[ENS_PARAM_MAX];
     int count;
     int flip;
+    int total_tiles;           // persistent parameter form: tiles of all instances
 };
 
 struct CflArgs {
@@ -178,6 +195,11 @@ struct SweepLaunchers {
     cudaError_t (*ens_tma)(int dir, const EnsSweepArgs &e, const CUtensorMap *maps, int blocks, int threads,
                            size_t smem, cudaStream_t s);
     int (*ens_tma_per_sm)(int dir, int threads, size_t smem);
+    // ensemble, persistent blocks taking tiles from a work counter (zero at
+    // launch), all instances' arguments in the kernel parameter
+    cudaError_t (*param_persist)(int dir, const EnsSweepParams &p, unsigned int *queue, int blocks, int threads,
+                                 size_t smem, cudaStream_t s);
+    int (*param_persist_per_sm)(int dir, int threads, size_t smem);
     // marching form (one thread per pencil; PPMLR_MIXED only, else cudaErrorNotSupported):
     // `a` carries the chunk length C, nchunk and the lane groups ngx (of 32)
     cudaError_t (*march)(int dir, const SweepArgs &a, cudaStream_t s);

@@ -510,6 +510,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     // ---------------- P1: load, ghosts, primitives ----------------
     double dx = 0.0, pos[3] = {0.0, 0.0, 0.0}, Bdg[3] = {0.0, 0.0, 0.0};
     R rho = 0, u = 0, v1 = 0, v2 = 0, Bn = 0, B1 = 0, B2 = 0, pr = 0, W = 0, dm = 0, e = 0;
+    R pdel = 0;                // reconstructed pressure: p - p_reff (mixed path), p (FP64 forms)
     R Bd0 = 0, Bd1 = 0, Bd2 = 0;
     R dtm_k = 0;               // contracted forms: dt / dm (P1 or P4 -> P6)
     bool floored = false;
@@ -608,6 +609,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             u = f[1 + DIR]; v1 = f[1 + T1]; v2 = f[1 + T2];
             Bn = f[4 + DIR] - Bd0; B1 = f[4 + T1] - Bd1; B2 = f[4 + T2] - Bd2;
             pr = f[7];
+            pdel = f[7] - a.p_reff;
             e = pr / (gm1 * rho) + 0.5f * (u * u + v1 * v1 + v2 * v2) + 0.5f * (Bn * Bn + B1 * B1 + B2 * B2) / rho;
         } else {
             df q[8];
@@ -621,24 +623,26 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
 #pragma unroll
                 for (int v = 0; v < 8; v++) q[v] = split_double(__ldg(Uin + v * vs + CHK(gi, NCELL)));
             }
-            float prf = pressure_df(q[0], q[1 + DIR], q[1 + T1], q[1 + T2], q[4 + DIR], q[4 + T1], q[4 + T2],
-                                    q[7], gm1);
+            const df pp = pressure_df_pair(q[0], q[1 + DIR], q[1 + T1], q[1 + T2], q[4 + DIR], q[4 + T1],
+                                           q[4 + T2], q[7], gm1);
             rho = q[0].h;
             const float ir = 1.0f / rho;
             u = q[1 + DIR].h * ir; v1 = q[1 + T1].h * ir; v2 = q[1 + T2].h * ir;
             Bn = q[4 + DIR].h; B1 = q[4 + T1].h; B2 = q[4 + T2].h;
             e = q[7].h * ir;
-            pr = prf;
+            pr = pp.h + pp.l;
+            pdel = (pp.h - a.p_reff) + pp.l;
         }
-        if (pr < a.p_minf) { pr = a.p_minf; floored = out_cell; }
+        if (pr < a.p_minf) { pr = a.p_minf; pdel = a.p_minf - a.p_reff; floored = out_cell; }
         dm = rho * dxf;
     }
+    if constexpr (F64) pdel = pr;
     if (act) {
         R Pt = pr + R(0.5) * (Bn * Bn + B1 * B1 + B2 * B2);
         if constexpr (F64 && !EX) W = fast_impedance<R>(rho, pr, Bn, B1, B2, gam);
         else W = rho * fsqrt<R, EX>(fast2<R, EX>(rho, pr, Bn, B1, B2, gam));
         SM(A_RHO, s) = rho; SM(A_U, s) = u; SM(A_V1, s) = v1; SM(A_V2, s) = v2;
-        SM(A_B1, s) = B1; SM(A_B2, s) = B2; SM(A_P, s) = pr; SM(A_DM, s) = dm;
+        SM(A_B1, s) = B1; SM(A_B2, s) = B2; SM(A_P, s) = pdel; SM(A_DM, s) = dm;
         SM(A_PT, s) = Pt; SM(A_BN, s) = Bn;
         if (a.do_src) {   // v x B_d in the local frame
             SM(A_AX, s) = v1 * Bd2 - v2 * Bd1;
@@ -657,7 +661,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     R src_m[3] = {0, 0, 0}, src_b[3] = {0, 0, 0}, src_e = 0;
     if (act && p >= 1 && p <= NPe - 2) {
         SlopeCoef<R> k = slope_coef<R, EX>(SM(A_DM, s - PS), dm, SM(A_DM, s + PS));
-        const R own[7] = {rho, u, v1, v2, B1, B2, pr};
+        const R own[7] = {rho, u, v1, v2, B1, B2, pdel};
 #pragma unroll
         for (int v = 0; v < 7; v++) {
             dmv[v] = limit_slope<R, EX>(SM(A_RHO + v, s - PS), own[v], SM(A_RHO + v, s + PS), k.c1, k.c2, k.c3,
@@ -743,7 +747,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     bool shock_k = false;      // contact steepening: this zone sits in a shock
     if (act && p >= 1 && p <= NPe - 3) {
         EdgeCoef<R> k = edge_coef<R, EX>(SM(A_DM, s - PS), dm, SM(A_DM, s + PS), SM(A_DM, s + 2 * PS));
-        const R own[7] = {rho, u, v1, v2, B1, B2, pr};
+        const R own[7] = {rho, u, v1, v2, B1, B2, pdel};
 #pragma unroll
         for (int v = 0; v < 7; v++) {
             if constexpr (EX) edg[v] = edge_value<R, EX>(k, own[v], SM(A_RHO + v, s + PS), dmv[v], SM(SB0 + v, s + PS));
@@ -784,7 +788,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             yf = W * dtm;
             ya = fsqrt<R, EX>(rho) * K<R>::ab(Bn) * dtm;
         }
-        const R own[7] = {rho, u, v1, v2, B1, B2, pr};
+        const R own[7] = {rho, u, v1, v2, B1, B2, pdel};
         R srv[9];
         // contracted forms: no blend where the zone is not flattened (flat is +0;
         // the double test on its bit pattern)
@@ -819,18 +823,32 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
 #pragma unroll
         for (int v = 0; v < 9; v++) Rs[v] = SM(v, s + PS);
         R Bnf = R(0.5) * (Bn + SM(A_BN, s + PS));
+        // total pressures relative to p_reff (mixed path; 0 for the FP64
+        // forms): u*, P* - p_reff and the Lagrangian momentum update need only
+        // their differences and weighted means
         R PL = sl[6] + R(0.5) * (sl[4] * sl[4] + sl[5] * sl[5]);
         R PR = Rs[6] + R(0.5) * (Rs[4] * Rs[4] + Rs[5] * Rs[5]);
+        R pref = R(0);
+        if constexpr (!F64) pref = a.p_reff;
         R WL, WR;
-        if constexpr (EX || !F64) {
+        if constexpr (!F64) {
+            WL = sl[0] * K<R>::sq(fast2<R, EX>(sl[0], sl[6] + pref, Bnf, sl[4], sl[5], gam));
+            WR = Rs[0] * K<R>::sq(fast2<R, EX>(Rs[0], Rs[6] + pref, Bnf, Rs[4], Rs[5], gam));
+        } else if constexpr (EX) {
             WL = sl[0] * K<R>::sq(fast2<R, EX>(sl[0], sl[6], Bnf, sl[4], sl[5], gam));
             WR = Rs[0] * K<R>::sq(fast2<R, EX>(Rs[0], Rs[6], Bnf, Rs[4], Rs[5], gam));
         } else {            // contracted FP64 form: no reciprocal of the traced densities
             WL = fast_impedance<R>(sl[0], sl[6], Bnf, sl[4], sl[5], gam);
             WR = fast_impedance<R>(Rs[0], Rs[6], Bnf, Rs[4], Rs[5], gam);
         }
-        if (a.riemann_iters > 0 && PL > R(0) && PR > R(0))
-            two_shock<R, EX>(a.riemann_iters, sl[1], Rs[1], PL, PR, gam, WL, WR);
+        if constexpr (!F64) {
+            const R PLa = PL + pref, PRa = PR + pref;          // the nonlinear solver takes absolute pressures
+            if (a.riemann_iters > 0 && PLa > R(0) && PRa > R(0))
+                two_shock<R, EX>(a.riemann_iters, sl[1], Rs[1], PLa, PRa, gam, WL, WR);
+        } else {
+            if (a.riemann_iters > 0 && PL > R(0) && PR > R(0))
+                two_shock<R, EX>(a.riemann_iters, sl[1], Rs[1], PL, PR, gam, WL, WR);
+        }
         R us, Ps;
         if constexpr (EX) {
             us = (WL * sl[1] + WR * Rs[1] + PL - PR) / (WL + WR);
@@ -864,7 +882,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         }
         rs_u = us; rs_S = Ss; rs_s1 = ss[0]; rs_s2 = ss[1];
         rs_b1 = Bnf * vs[0]; rs_b2 = Bnf * vs[1];
-        rs_fe = Ss * us - ss[0] * vs[0] - ss[1] * vs[1];
+        rs_fe = (Ss + pref) * us - ss[0] * vs[0] - ss[1] * vs[1];     // absolute S* in the energy flux
         SM(SC0 + 0, s) = rs_u; SM(SC0 + 1, s) = rs_S; SM(SC0 + 2, s) = rs_s1; SM(SC0 + 3, s) = rs_s2;
         SM(SC0 + 4, s) = rs_b1; SM(SC0 + 5, s) = rs_b2; SM(SC0 + 6, s) = rs_fe;
     }
@@ -1393,6 +1411,34 @@ __global__ void __launch_bounds__(MaxThreads<R>::value, EnsMinBlocks<R>::value) 
         if (p.first_tile[mid] <= t) lo = mid; else hi = mid - 1;
     }
     sweep_tile<DIR, R, EX, const SweepArgs>(p.args[lo], t - p.first_tile[lo], smem_raw, p.flip);
+}
+
+// Ensemble, persistent blocks with all instances' arguments in the kernel
+// parameter: each block repeatedly takes the next tile from the work counter
+// (one atomic per tile, no waiting), finds its instance from the first-tile
+// table and runs the tile with that instance's fields read straight from the
+// parameter space (no per-block copy of the arguments, so the tile body keeps
+// the one-block-per-tile form's register budget).
+template <int DIR, typename R, bool EX>
+__global__ void __launch_bounds__(MaxThreads<R>::value, EnsMinBlocks<R>::value)
+    sweep_ensemble_param_persist_kernel(const __grid_constant__ EnsSweepParams p, unsigned int *queue)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ int next;
+    for (;;) {
+        if (threadIdx.x == 0) next = (int)atomicAdd(queue, 1u);
+        __syncthreads();
+        const int t = next;
+        __syncthreads();                       // every thread has read `next` before it is rewritten
+        if (t >= p.total_tiles) break;
+        int lo = 0, hi = p.count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p.first_tile[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        sweep_tile<DIR, R, EX, const SweepArgs>(p.args[lo], t - p.first_tile[lo], smem_raw, p.flip);
+        __syncthreads();                       // the tile's shared memory is free again
+    }
 }
 
 // Dipole table of a single domain (FP64 forms): B_d at every cell centre,

@@ -498,7 +498,7 @@ class Ensemble:
         return self._check(load().ppmlr_ensemble_set_steepening(self._h, int(bool(on))))
 
     def set_launch(self, axis, form, budget, raise_on_error=True):
-        """Fix one direction's launch form (0..3) and tile budget (positions x
+        """Fix one direction's launch form (0..4) and tile budget (positions x
         lanes; + 10000 for y/z: the lanes-first tile rule)."""
         st = load().ppmlr_ensemble_set_launch(self._h, int(axis), int(form), int(budget))
         return self._check(st) if raise_on_error else st

@@ -133,8 +133,38 @@ def test_ensemble_tma_form_matches_the_other_forms(precision):
     assert skew.set_launch(0, 3, 216, raise_on_error=False) == ppmlr.PPMLR_E_INVALID  # 4 lanes do not divide ny
 
 
+@pytest.mark.parametrize("precision", [ppmlr.PPMLR_FP64_EXACT, ppmlr.PPMLR_FP64, ppmlr.PPMLR_MIXED])
+def test_ensemble_persistent_parameter_form_matches_the_other_forms(precision):
+    """Form 4: persistent blocks taking tiles from the work counter, every
+    instance's arguments in the kernel parameter."""
+    probs = small_ensemble(9)
+    a = ppmlr.Ensemble(probs, precision=precision)
+    b = ppmlr.Ensemble(probs, precision=precision)
+    for axis in range(3):
+        a.set_launch(axis, 1, 256)
+        b.set_launch(axis, 4, 256)
+    assert [t // 1000 for t in b.tiles()] == [4, 4, 4]
+    for i, p in enumerate(probs):
+        a.set_state(i, p.U0)
+        b.set_state(i, p.U0)
+    a.step(0.4, 4)
+    b.step(0.4, 4)
+    b.check()
+    for i in range(len(probs)):
+        if precision == ppmlr.PPMLR_FP64_EXACT:
+            assert np.array_equal(a.get_state(i), b.get_state(i)), i
+        else:
+            tol = 1e-12 if precision == ppmlr.PPMLR_FP64 else 1e-6
+            assert np.max(rel_l1(b.get_state(i), a.get_state(i))) <= tol, i
+    assert a.diagnostics()["floor_hits"] == b.diagnostics()["floor_hits"]
+    many = ppmlr.Ensemble([inputs.magnetosphere(n=(24, 20, 20), h0=2.0, x_ext=(-30, 20), yz_ext=(-25, 25),
+                                                name=f"t{i}") for i in range(65)], precision=precision)
+    for form in (2, 4):                              # the kernel parameter holds at most 64 instances
+        assert many.set_launch(1, form, 256, raise_on_error=False) == ppmlr.PPMLR_E_INVALID
+
+
 @pytest.mark.parametrize("precision", [ppmlr.PPMLR_FP64_EXACT, ppmlr.PPMLR_MIXED])
-@pytest.mark.parametrize("form", [0, 3])
+@pytest.mark.parametrize("form", [0, 3, 4])
 def test_ensemble_lanes_first_tiles_match_whole_pencil_tiles(precision, form):
     """The y/z lanes-first rule (budget + 10000: chunked pencils, more lanes)
     gives the whole-pencil rule's results (bit for bit on the exact path)."""

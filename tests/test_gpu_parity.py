@@ -6,7 +6,7 @@ so the observed difference is expected to be 0).  Mixed path: relative L1
 import numpy as np
 import pytest
 
-from gpu_util import linf, make_gpu, make_oracle, rel_l1, run_pair
+from gpu_util import assert_parity, linf, make_gpu, make_oracle, rel_l1, run_pair
 from paper_1607_02214_gb300 import inputs, ppmlr
 
 pytestmark = pytest.mark.gpu
@@ -182,7 +182,8 @@ def test_high_mach_translation_fp64_exact_mixed_bounded():
     o, g, dts = run_pair(pr, 5, precision=ppmlr.PPMLR_FP64_EXACT)
     assert np.array_equal(g.get_state(), o.get_state())
     _, gf, _ = run_pair(pr, 5, dts=dts)
-    assert np.max(rel_l1(gf.get_state(), o.get_state())) <= FP64_TOL
+    # (m_z, generated only by the field perturbations, is a weak component here)
+    assert_parity(gf.get_state(), o.get_state(), FP64_TOL, 1e-9)
     _, gm, _ = run_pair(pr, 5, precision=ppmlr.PPMLR_MIXED, dts=dts)
     pa, pb = pressure(gm.get_state()), pressure(o.get_state())
     assert np.all(pb > 0.5)
