@@ -117,6 +117,19 @@ ppmlr_status ppmlr_set_state(ppmlr_ctx *ctx, const double *const U[8], int on_de
  * copy has completed. */
 ppmlr_status ppmlr_get_state(ppmlr_ctx *ctx, double *const U[8], int on_device);
 
+/* Layers k0 .. k0+nk-1 along z (the slowest axis) of the state: copied out of
+ * (get) or into (set) the context; U: 8 arrays of nk * n[1] * n[0] doubles
+ * (x fastest), host or device memory (on_device), caller-owned.  For a
+ * domain split along z across ranks (block decomposition, the paper's own
+ * scaling axis, Secs. III-A and III-B): each rank's context holds its slab
+ * plus 7 halo layers (the stencil radius of one sweep) toward each
+ * neighbour, and the halos are refreshed from the neighbours' owned layers
+ * after every z sweep.  Stream-ordered on the context's stream; host copies
+ * synchronise it.  PPMLR_E_INVALID for k0 < 0, nk < 0, k0 + nk > n[2] or a
+ * NULL array. */
+ppmlr_status ppmlr_get_layers(ppmlr_ctx *ctx, int k0, int nk, double *const U[8], int on_device);
+ppmlr_status ppmlr_set_layers(ppmlr_ctx *ctx, int k0, int nk, const double *const U[8], int on_device);
+
 /* CFL time step (reading of the paper, which states none):
  *   dt = cfl * min over non-inner interior cells and axes d of
  *        dx_d / (|v_d| + max(c_f,d(B'), c_f,d(B' + B_d))).

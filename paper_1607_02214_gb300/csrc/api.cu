@@ -514,6 +514,46 @@ static ppmlr_status read_flags(ppmlr_ctx *c)
     return PPMLR_OK;
 }
 
+// z-layer ranges of the state (z is the slowest axis: layers k0 .. k0+nk-1
+// of array v are one contiguous block), for the halo exchange of a domain
+// split along z.
+static const char *layer_range_error(const ppmlr_ctx *c, int k0, int nk, const void *const *U)
+{
+    if (!U) return "layers: null array list";
+    for (int v = 0; v < 8; v++)
+        if (!U[v]) return "layers: null array";
+    if (k0 < 0 || nk < 0 || k0 + nk > c->n[2]) return "layers: need 0 <= k0 and k0 + nk <= n[2]";
+    return nullptr;
+}
+
+ppmlr_status ppmlr_get_layers(ppmlr_ctx *c, int k0, int nk, double *const U[8], int on_device)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (const char *why = layer_range_error(c, k0, nk, (const void *const *)U)) return fail(c, PPMLR_E_INVALID, why);
+    const size_t plane = (size_t)c->n[0] * c->n[1];
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    for (int v = 0; v < 8; v++)
+        if (nk > 0)
+            CK(c, cudaMemcpyAsync(U[v], c->U[v] + (size_t)k0 * plane, sizeof(double) * plane * nk, kind, c->stream),
+               "get_layers copy");
+    if (!on_device) CK(c, cudaStreamSynchronize(c->stream), "get_layers sync");
+    return PPMLR_OK;
+}
+
+ppmlr_status ppmlr_set_layers(ppmlr_ctx *c, int k0, int nk, const double *const U[8], int on_device)
+{
+    if (!c) return PPMLR_E_INVALID;
+    if (const char *why = layer_range_error(c, k0, nk, (const void *const *)U)) return fail(c, PPMLR_E_INVALID, why);
+    const size_t plane = (size_t)c->n[0] * c->n[1];
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int v = 0; v < 8; v++)
+        if (nk > 0)
+            CK(c, cudaMemcpyAsync(c->U[v] + (size_t)k0 * plane, U[v], sizeof(double) * plane * nk, kind, c->stream),
+               "set_layers copy");
+    if (!on_device) CK(c, cudaStreamSynchronize(c->stream), "set_layers sync");
+    return PPMLR_OK;
+}
+
 ppmlr_status ppmlr_check(ppmlr_ctx *c)
 {
     if (!c) return PPMLR_E_INVALID;

@@ -52,6 +52,8 @@ SIGNATURES = [
     ("ppmlr_set_stream", c_int, [c_void_p, c_void_p]),
     ("ppmlr_set_state", c_int, [c_void_p, DPTR8, c_int]),
     ("ppmlr_get_state", c_int, [c_void_p, DPTR8, c_int]),
+    ("ppmlr_get_layers", c_int, [c_void_p, c_int, c_int, DPTR8, c_int]),
+    ("ppmlr_set_layers", c_int, [c_void_p, c_int, c_int, DPTR8, c_int]),
     ("ppmlr_cfl_dt", c_int, [c_void_p, c_double, POINTER(c_double)]),
     ("ppmlr_step", c_int, [c_void_p, c_double]),
     ("ppmlr_step_cfl", c_int, [c_void_p, c_double, c_int]),
@@ -262,6 +264,25 @@ class Context:
             self._check(st)
             return out
         return out, st
+
+    def get_layers(self, k0, nk, out=None):
+        """z layers k0 .. k0+nk-1 of the state, (8, nk, ny, nx): into `out`
+        (a contiguous float64 numpy array or device tensor) or a new numpy
+        array."""
+        if out is None:
+            out = np.empty((8, nk, self.shape[2], self.shape[3]), dtype=np.float64)
+        assert tuple(out.shape) == (8, nk, self.shape[2], self.shape[3])
+        p, dev = self._ptrs(out)
+        self._check(load().ppmlr_get_layers(self._h, int(k0), int(nk), p, dev))
+        return out
+
+    def set_layers(self, k0, U):
+        """Overwrite z layers k0 .. k0+len-1 with U, (8, nk, ny, nx)."""
+        if not hasattr(U, "data_ptr"):
+            U = np.ascontiguousarray(U, dtype=np.float64)
+        assert tuple(U.shape)[0] == 8 and tuple(U.shape)[2:] == self.shape[2:]
+        p, dev = self._ptrs(U)
+        return self._check(load().ppmlr_set_layers(self._h, int(k0), int(U.shape[1]), p, dev))
 
     def cfl_dt(self, cfl):
         dt = c_double()
