@@ -58,25 +58,25 @@ BYTES_PER_CELL_SWEEP = 128      # read 8 FP64 + write 8 FP64
 # top of the state: traffic above the algorithmic 128 / 64 B by that much; the
 # FP64 y and z sweeps (72-register cap) add ~30 B per cell of spill traffic.
 NCU_TRAFFIC = {
-    "fp64:x": {"bytes_per_cell": 151.4, "src": "fe3bbfb1879de707"},
-    "fp64:y": {"bytes_per_cell": 181.1, "src": "fe3bbfb1879de707"},
-    "fp64:z": {"bytes_per_cell": 177.2, "src": "fe3bbfb1879de707"},
-    "fp64:cfl": {"bytes_per_cell": 89.4, "src": "b69563e0f0c1e528"},
-    "mixed:x": {"bytes_per_cell": 123.9, "src": "47f41a220077743d"},
-    "mixed:y": {"bytes_per_cell": 124.9, "src": "47f41a220077743d"},
-    "mixed:z": {"bytes_per_cell": 125.2, "src": "47f41a220077743d"},
-    "mixed:cfl": {"bytes_per_cell": 64.3, "src": "11b7132d0b34f725"},
+    "fp64:x": {"bytes_per_cell": 151.2, "src": "4cffd53096c27579"},
+    "fp64:y": {"bytes_per_cell": 181.1, "src": "4cffd53096c27579"},
+    "fp64:z": {"bytes_per_cell": 177.0, "src": "4cffd53096c27579"},
+    "fp64:cfl": {"bytes_per_cell": 89.3, "src": "dd8ed0d0de48614f"},
+    "mixed:x": {"bytes_per_cell": 123.5, "src": "e74a977a95a7eb8e"},
+    "mixed:y": {"bytes_per_cell": 124.5, "src": "e74a977a95a7eb8e"},
+    "mixed:z": {"bytes_per_cell": 124.9, "src": "e74a977a95a7eb8e"},
+    "mixed:cfl": {"bytes_per_cell": 64.3, "src": "e75f597d7ca449b3"},
     # ensemble sweeps: captured on the first 8 of the 48 instances (14.9 M
     # cells; the full ensemble holds ~10 GB), scaled by cells
-    "ensemble:x": {"bytes_per_cell": 125.0, "src": "9677c2199a15c2c3"},
-    "ensemble:y": {"bytes_per_cell": 125.7, "src": "9677c2199a15c2c3"},
-    "ensemble:z": {"bytes_per_cell": 125.9, "src": "9677c2199a15c2c3"},
+    "ensemble:x": {"bytes_per_cell": 125.1, "src": "85d78e838d4282d2"},
+    "ensemble:y": {"bytes_per_cell": 125.5, "src": "85d78e838d4282d2"},
+    "ensemble:z": {"bytes_per_cell": 125.6, "src": "85d78e838d4282d2"},
 }
 
 
 # Sources of each (precision, kernel) entry of NCU_TRAFFIC; the hash of the
 # files at capture time is stored with the entry.
-_SWEEP = ("sweep.cuh", "launch.cuh", "mixed_util.cuh", "ppmlr_internal.h")
+_SWEEP = ("sweep.cuh", "launch.cuh", "march.cuh", "mixed_util.cuh", "ppmlr_internal.h")
 KERNEL_SOURCES = {
     "fp64:sweep": _SWEEP + ("sweep_fp64.cu",),
     "mixed:sweep": _SWEEP + ("sweep_mixed.cu",),
