@@ -42,7 +42,7 @@ __device__ __forceinline__ float cell_bound(const CflArgs &a, const long long i,
     const float gm1 = a.gammaf - 1.0f;
     df q[8];
 #pragma unroll
-    for (int v = 0; v < 8; v++) q[v] = split_double(u[v]);
+    for (int v = 0; v < 8; v++) q[v] = split_double_fast(u[v]);
     float pr = pressure_df(q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7], gm1);
     if (pr < a.p_minf) pr = a.p_minf;
     float Bd[3];

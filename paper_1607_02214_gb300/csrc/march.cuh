@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(32 * MARCH_WARPS, 1) sweep_march_kernel(const 
             } else {
                 df q[8];
 #pragma unroll
-                for (int v = 0; v < 8; v++) q[v] = split_double(cur[v]);
+                for (int v = 0; v < 8; v++) q[v] = split_double_fast(cur[v]);
                 const df pp = pressure_df_pair(q[0], q[1 + DIR], q[1 + T1], q[1 + T2], q[4 + DIR], q[4 + T1],
                                                q[4 + T2], q[7], gm1);
                 pabs = pp.h + pp.l;

@@ -8,8 +8,9 @@
 // FP32 pipe (error-free transformations: Knuth's two-sum and the FMA-based
 // two-product, about 44-48 significant bits -- enough to keep the cancellation
 // of E against the kinetic and magnetic energies harmless), and (3) widens the
-// FP32 increment back to double with integer operations, so that the only
-// FP64 instruction left per conserved variable is the final accumulate.
+// FP32 increment back to double with one conversion, so that the FP64 pipe
+// sees two instructions per conserved variable (conversion, accumulate) --
+// about a third of its capacity at the sweeps' rate.
 #pragma once
 #include <math.h>
 
@@ -48,15 +49,30 @@ __device__ __forceinline__ df split_double(double x)
     return r;
 }
 
-// Exact float -> double (denormal floats are zero under flush-to-zero).
-__device__ __forceinline__ double widen(float f)
+// Fast split for doubles in the normal float range (the common case: one
+// funnel shift and two logic operations for h, h's bits being those of the
+// truncated double): the double's exponent e in [897, 1150] maps to the
+// float exponent e - 896 = (e mod 256) with its top bit flipped; the rest
+// (zero, tiny, huge, non-finite) takes split_double.
+__device__ __forceinline__ df split_double_fast(double x)
 {
-    const unsigned b = __float_as_uint(f);
-    const unsigned sgn = b & 0x80000000u, ef = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
-    if (ef == 0u) return __hiloint2double((int)sgn, 0);
-    const unsigned ed = ef == 0xFFu ? 0x7FFu : ef + 896u;
-    return __hiloint2double((int)(sgn | (ed << 20) | (m >> 3)), (int)(m << 29));
+    const long long b = __double_as_longlong(x);
+    const unsigned hi = (unsigned)((unsigned long long)b >> 32), lo = (unsigned)b;
+    const unsigned e = (hi >> 20) & 0x7FFu;
+    if (e - 897u >= 254u) return split_double(x);
+    const unsigned t = __funnelshift_l(lo, hi, 3);       // hi << 3 | lo >> 29: exponent bits 8..0, mantissa 23
+    const unsigned sgn = hi & 0x80000000u;
+    df r;
+    r.h = __uint_as_float(sgn | ((t ^ 0x40000000u) & 0x7FFFFFFFu));
+    const unsigned rem = lo & 0x1FFFFFFFu;               // value rem * 2^(e-1075)
+    const float scale = e >= 949u ? __uint_as_float((e - 948u) << 23) : 0.0f;
+    r.l = __uint_as_float(__float_as_uint(__uint2float_rn(rem) * scale) ^ sgn);
+    return r;
 }
+
+// Exact float -> double (one conversion; denormal floats are zero under
+// flush-to-zero).
+__device__ __forceinline__ double widen(float f) { return (double)f; }
 
 // Error-free transformations (no multiply appears, so contraction cannot fuse them).
 __device__ __forceinline__ df two_sum(float a, float b)

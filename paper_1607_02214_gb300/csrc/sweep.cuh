@@ -289,17 +289,21 @@ __device__ __forceinline__ R monotone(R ai, R &l, R &r)
         }
         return 3.0 * (dl - dr);
     }
-    if constexpr (!EX && std::is_same<R, float>::value) {   // branch-free: selects only
-        const float da = r - l;
-        const float m6 = 6.0f * (ai - 0.5f * (l + r));
-        const float dm6 = da * m6, dd = da * da;
-        const bool ext = (r - ai) * (ai - l) <= 0.0f;
-        const bool lo = dm6 > dd, hi = !lo && -dd > dm6;
-        const float nl = lo ? 3.0f * ai - 2.0f * r : l;
-        const float nr = hi ? 3.0f * ai - 2.0f * l : r;
-        l = ext ? ai : nl;
-        r = ext ? ai : nr;
-        return 6.0f * (ai - 0.5f * (l + r));
+    if constexpr (!EX && std::is_same<R, float>::value) {
+        // branch-free, on the one-sided differences as in the fast double
+        // form: extremum when dl, dr differ in sign; otherwise the overshoot
+        // tests |dl| > 2 |dr| (l = ai - 2 dr) and |dr| > 2 |dl| (r = ai + 2 dl),
+        // and a6 = 3 (dl - dr) of the adjusted ends
+        const float dl = ai - l, dr = r - ai;
+        const bool ext = dl * dr <= 0.0f;
+        const float adl = fabsf(dl), adr = fabsf(dr);
+        float dl2 = adl > adr + adr ? dr + dr : dl;
+        float dr2 = adr > adl + adl ? dl + dl : dr;
+        dl2 = ext ? 0.0f : dl2;
+        dr2 = ext ? 0.0f : dr2;
+        l = ai - dl2;
+        r = ai + dr2;
+        return 3.0f * (dl2 - dr2);
     }
     if ((r - ai) * (ai - l) <= R(0)) {
         l = ai; r = ai;
@@ -617,11 +621,11 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             if (stage && ps >= 0 && ps < NP) {
                 const int slot = stage_index<DIR>(l, ps, NP, L), sv = stage_array_stride<DIR>(NP, L);
 #pragma unroll
-                for (int v = 0; v < 8; v++) q[v] = split_double(stage[CHK(v * sv + slot, 8 * sv)]);
+                for (int v = 0; v < 8; v++) q[v] = split_double_fast(stage[CHK(v * sv + slot, 8 * sv)]);
             } else {
                 const long long gi = base + (long long)src * stride;
 #pragma unroll
-                for (int v = 0; v < 8; v++) q[v] = split_double(__ldg(Uin + v * vs + CHK(gi, NCELL)));
+                for (int v = 0; v < 8; v++) q[v] = split_double_fast(__ldg(Uin + v * vs + CHK(gi, NCELL)));
             }
             const df pp = pressure_df_pair(q[0], q[1 + DIR], q[1 + T1], q[1 + T2], q[4 + DIR], q[4 + T1],
                                            q[4 + T2], q[7], gm1);
