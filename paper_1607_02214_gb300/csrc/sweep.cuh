@@ -71,6 +71,15 @@ __device__ __forceinline__ bool same_sign_d(double x, double y)
     return (a ^ b) >= 0 && (a << 1) != 0 && (b << 1) != 0;
 }
 
+// x * 2^k for a finite double whose result stays a normal number, on the
+// integer pipe (the exponent field moved; zero stays zero): the same value as
+// the multiplication, without an instruction on the GB300's FP64 pipe.
+__device__ __forceinline__ double pow2_scale(double x, int k)
+{
+    const long long b = __double_as_longlong(x);
+    return (b << 1) == 0 ? x : __longlong_as_double(b + ((long long)k << 52));
+}
+
 // The remap's donor fraction y (> 0 where it is used) reaches the zone width:
 // y >= 1, on the bit patterns for the fast double form.
 template <typename R, bool EX>
@@ -193,10 +202,11 @@ __device__ __forceinline__ void two_shock(const int iters, const R uL, const R u
 template <typename R>
 __device__ __forceinline__ R fast_impedance(R rho, R p, R Bn, R B1, R B2, R gam)
 {
+    // (the factors 4 and 1/2 as exponent moves on the integer pipe)
     const R gp = gam * p;
     const R S = gp + (Bn * Bn + B1 * B1 + B2 * B2);
-    const R D = S * S - R(4) * gp * (Bn * Bn);          // fsqrt gives 0 for D <= 0
-    return fsqrt<R, false>(rho * (R(0.5) * (S + fsqrt<R, false>(D))));
+    const R D = S * S - pow2_scale(gp, 2) * (Bn * Bn);  // fsqrt gives 0 for D <= 0
+    return fsqrt<R, false>(rho * pow2_scale(S + fsqrt<R, false>(D), -1));
 }
 
 // Earth dipole along -z: B_d = M [3 (m.r) r - m r^2] / r^5, m = -z.
@@ -235,7 +245,8 @@ __device__ __forceinline__ R limit_slope(R am, R a0, R ap, R c1, R c2, R c3, R *
         if (dp_out) *dp_out = dp;
         if (!same_sign_d(dp, dm)) return 0.0;
         const double da = c2 * dp + c3 * dm;
-        const double lim = 2.0 * __longlong_as_double(min(mag_d(dm), mag_d(dp)));
+        // twice the smaller difference (both non-zero here): the exponent field + 1
+        const double lim = __longlong_as_double(min(mag_d(dm), mag_d(dp)) + (1LL << 52));
         const double m = mag_d(lim) < mag_d(da) ? lim : fabs(da);
         return pos_d(da) ? m : (neg_d(da) ? -m : 0.0);
     }
@@ -576,7 +587,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             e = R(E / rd);
         } else {
             const double ir = 1.0 / rd;
-            prd = (a.gamma - 1.0) * (E - 0.5 * (mn * mn + m1 * m1 + m2 * m2) * ir
+            prd = (a.gamma - 1.0) * (E - pow2_scale(mn * mn + m1 * m1 + m2 * m2, -1) * ir
                                      - 0.5 * (bn * bn + b1 * b1 + b2 * b2));
             rho = R(rd); u = R(mn * ir); v1 = R(m1 * ir); v2 = R(m2 * ir);
             e = R(E * ir);
@@ -826,7 +837,9 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         R Rs[9];
 #pragma unroll
         for (int v = 0; v < 9; v++) Rs[v] = SM(v, s + PS);
-        R Bnf = R(0.5) * (Bn + SM(A_BN, s + PS));
+        R Bnf;
+        if constexpr (F64 && !EX) Bnf = pow2_scale(Bn + SM(A_BN, s + PS), -1);
+        else Bnf = R(0.5) * (Bn + SM(A_BN, s + PS));
         // total pressures relative to p_reff (mixed path; 0 for the FP64
         // forms): u*, P* - p_reff and the Lagrangian momentum update need only
         // their differences and weighted means
@@ -862,7 +875,9 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             us = (WL * sl[1] + WR * Rs[1] + PL - PR) * iW;
             Ps = (WR * PL + WL * PR + WL * WR * (sl[1] - Rs[1])) * iW;
         }
-        R Ss = Ps - R(0.5) * Bnf * Bnf;
+        R Ss;
+        if constexpr (F64 && !EX) Ss = Ps - pow2_scale(Bnf, -1) * Bnf;
+        else Ss = Ps - R(0.5) * Bnf * Bnf;
         R ZL = fsqrt<R, EX>(sl[0]) * K<R>::ab(Bnf);
         R ZR = fsqrt<R, EX>(Rs[0]) * K<R>::ab(Bnf);
         R vs[2], ss[2];
