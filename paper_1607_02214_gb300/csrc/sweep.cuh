@@ -80,6 +80,25 @@ __device__ __forceinline__ double pow2_scale(double x, int k)
     return (b << 1) == 0 ? x : __longlong_as_double(b + ((long long)k << 52));
 }
 
+// 1/x in the contracted double form: the hardware's approximate reciprocal
+// refined by one cubically convergent Newton-Raphson step,
+// r (1 + e + e^2) with e = 1 - x r (three fused multiply-adds: from a seed
+// good to ~2^-22 the error falls to ~2^-66, i.e. the result is within an
+// ulp of 1/x, not necessarily the correctly rounded quotient); other forms
+// divide.  x finite and non-zero where it is used.
+template <typename R, bool EX>
+__device__ __forceinline__ R recip(R x)
+{
+    if constexpr (!EX && std::is_same<R, double>::value) {
+        double r;
+        asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+        const double e = fma(-x, r, 1.0);
+        return fma(r, fma(e, e, e), r);
+    } else {
+        return R(1) / x;
+    }
+}
+
 // The remap's donor fraction y (> 0 where it is used) reaches the zone width:
 // y >= 1, on the bit patterns for the fast double form.
 template <typename R, bool EX>
@@ -127,7 +146,7 @@ template <typename R, bool EX = true>
 __device__ __forceinline__ R fast2(R rho, R p, R Bn, R B1, R B2, R gam)
 {
     if constexpr (!EX) {
-        const R ir = R(1) / rho;
+        const R ir = recip<R, EX>(rho);
         const R a2 = gam * p * ir;
         const R b2 = (Bn * Bn + B1 * B1 + B2 * B2) * ir;
         const R bn2 = Bn * Bn * ir;
@@ -351,7 +370,7 @@ __device__ __forceinline__ SlopeCoef<R> slope_coef(R xm, R x0, R xp)
 {
     if constexpr (!EX) {
         const R d1 = xm + x0 + xp, d2 = xp + x0, d3 = xm + x0;
-        const R q = x0 * (R(1) / (d1 * (d2 * d3)));
+        const R q = x0 * recip<R, EX>(d1 * (d2 * d3));
         SlopeCoef<R> k;
         k.c1 = R(1);
         k.c2 = (R(2) * xm + x0) * d3 * q;
@@ -375,7 +394,7 @@ __device__ __forceinline__ EdgeCoef<R> edge_coef(R x0, R x1, R x2, R x3)
     if constexpr (!EX) {
         const R d1 = R(2) * x1 + x2, d2 = R(2) * x2 + x1, d3 = x1 + x2, d4 = x0 + x1 + x2 + x3;
         const R d12 = d1 * d2, d34 = d3 * d4;
-        const R inv = R(1) / (d12 * d34);
+        const R inv = recip<R, EX>(d12 * d34);
         const R r1 = d2 * d34 * inv, r2 = d1 * d34 * inv, r3 = d12 * d4 * inv, r4 = d12 * d3 * inv;
         const R z1 = (x0 + x1) * r1, z2 = (x3 + x2) * r2;
         EdgeCoef<R> k;
@@ -586,7 +605,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             rho = R(rd); u = R(mn / rd); v1 = R(m1 / rd); v2 = R(m2 / rd);
             e = R(E / rd);
         } else {
-            const double ir = 1.0 / rd;
+            const double ir = recip<double, EX>(rd);
             prd = (a.gamma - 1.0) * (E - pow2_scale(mn * mn + m1 * m1 + m2 * m2, -1) * ir
                                      - 0.5 * (bn * bn + b1 * b1 + b2 * b2));
             rho = R(rd); u = R(mn * ir); v1 = R(m1 * ir); v2 = R(m2 * ir);
@@ -871,7 +890,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             us = (WL * sl[1] + WR * Rs[1] + PL - PR) / (WL + WR);
             Ps = (WR * PL + WL * PR + WL * WR * (sl[1] - Rs[1])) / (WL + WR);
         } else {
-            const R iW = R(1) / (WL + WR);
+            const R iW = recip<R, EX>(WL + WR);
             us = (WL * sl[1] + WR * Rs[1] + PL - PR) * iW;
             Ps = (WR * PL + WL * PR + WL * WR * (sl[1] - Rs[1])) * iW;
         }
@@ -883,7 +902,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         R vs[2], ss[2];
         const R zsum = ZL + ZR;
         const bool zero_z = (EX || !F64) ? zsum == R(0) : !pos_d(zsum);   // Z >= 0: zero or not
-        const R iZ = (EX || zero_z) ? R(0) : R(1) / zsum;
+        const R iZ = (EX || zero_z) ? R(0) : recip<R, EX>(zsum);
 #pragma unroll
         for (int t = 0; t < 2; t++) {
             R vL = sl[2 + t], vR = Rs[2 + t];
@@ -930,7 +949,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             qL[0] = rhoL; qL[1] = rhoL * uL; qL[2] = rhoL * v1L; qL[3] = rhoL * v2L;
             qL[4] = B1dx / dxL; qL[5] = B2dx / dxL; qL[6] = rhoL * eL;
         } else {
-            const R dtm = dtm_k, idxL = R(1) / dxL;     // dt / dm from P1 or P4
+            const R dtm = dtm_k, idxL = recip<R, EX>(dxL);     // dt / dm from P1 or P4
             idxL_k = idxL;
             R uL = u - (rs_S - lS) * dtm;
             R v1L = v1 + (rs_s1 - ls1) * dtm;
