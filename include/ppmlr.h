@@ -208,7 +208,8 @@ ppmlr_status ppmlr_set_march_chunk(ppmlr_ctx *ctx, int axis, int C);
 
 /* Force the tile shape of one direction (axis 0, 1, 2): C cells per chunk
  * (1 <= C <= n[axis]) and L lanes (L >= 1) with (C + 14) * L within the
- * thread budget (448 for the FP64 forms, 512 for PPMLR_MIXED).  Resets that
+ * thread budget (512 for PPMLR_MIXED; 448 for the FP64 forms, except 576
+ * for the x sweep of PPMLR_FP64).  Resets that
  * direction's launch form to 0.  Results do not depend on the shape.  Returns
  * PPMLR_E_INVALID (state unchanged) for shapes outside those bounds. */
 ppmlr_status ppmlr_set_tiles(ppmlr_ctx *ctx, int axis, int C, int L);
@@ -444,6 +445,16 @@ void ppmlr_ensemble_destroy(ppmlr_ens *ens);
  * sweeps' roofline.  Errors: PPMLR_E_INVALID (rates NULL), PPMLR_E_OOM,
  * PPMLR_E_CUDA. */
 ppmlr_status ppmlr_measure_pipe_rates(void *cuda_stream, double rates[3]);
+
+/* Self-test of the PPMLR_FP64 form's own square root and reciprocal (a
+ * hardware approximation refined by one third-order step; no paper
+ * counterpart): over n >= 1 arguments (1 + f) 2^e, e cycling over
+ * -1000..1000, the largest error in ulps of the correctly rounded result:
+ * max_ulp[0] square root, max_ulp[1] reciprocal (both at most 1 for the
+ * form's accuracy claim).  Runs on `cuda_stream` (NULL = default), allocates
+ * and frees 16 bytes, synchronises the stream.  Errors: PPMLR_E_INVALID
+ * (max_ulp NULL or n < 1), PPMLR_E_OOM, PPMLR_E_CUDA. */
+ppmlr_status ppmlr_selftest_fp64_arith(void *cuda_stream, long long n, double max_ulp[2]);
 
 /* Allocation-free CFL time step.  The paper has no counterpart: this entry
  * point exists for callers that must not allocate device memory -- a host

@@ -259,6 +259,8 @@ static const char *tma_ineligible(const ppmlr_ctx *c, int d, const Tile &t, int 
 {
     if (!encode_fn()) return "cuTensorMapEncodeTiled is not available from the driver";
     if (c->n[0] & 1) return "the TMA form needs nx even (16-byte aligned rows)";
+    if (t.threads > (c->prec == PPMLR_MIXED ? MAXT : MAXT_F64))
+        return "the TMA kernels take at most 512 (mixed) or 448 (FP64) threads per tile";
     if (d == 0) {
         if (form != 2) return "the x sweep has only the one-tile TMA form (2)";
         if (t.C & 1) return "the x-sweep TMA form needs an even chunk length C";
@@ -815,7 +817,6 @@ ppmlr_status ppmlr_autotune(ppmlr_ctx *c, double *best_ms)
 {
     if (!c) return PPMLR_E_INVALID;
     const size_t rs = c->prec == PPMLR_MIXED ? sizeof(float) : sizeof(double);
-    const int maxt = c->prec == PPMLR_MIXED ? MAXT : MAXT_F64;
     unsigned long long floors_before = 0;
     CK(c, cudaMemcpyAsync(&floors_before, c->floors, sizeof(floors_before), cudaMemcpyDeviceToHost, c->stream),
        "floors copy");
@@ -847,6 +848,7 @@ ppmlr_status ppmlr_autotune(ppmlr_ctx *c, double *best_ms)
             }
         }
         const int N = c->n[d];
+        const int maxt = tile_budget(c->prec, d);
         std::vector<std::pair<int, int>> cands;
         for (int nchunk = 1; nchunk <= 4; nchunk++) {
             const int C = (N + nchunk - 1) / nchunk;
@@ -957,7 +959,7 @@ ppmlr_status ppmlr_set_tiles(ppmlr_ctx *c, int axis, int C, int L)
     const int N = c->n[axis];
     if (C < 1 || C > N || L < 1) return fail(c, PPMLR_E_INVALID, "set_tiles: need 1 <= C <= n[axis] and L >= 1");
     const size_t rs = c->prec == PPMLR_MIXED ? sizeof(float) : sizeof(double);
-    const int maxt = c->prec == PPMLR_MIXED ? MAXT : MAXT_F64;
+    const int maxt = tile_budget(c->prec, axis);
     if ((long long)(C + 2 * GH) * L > maxt) return fail(c, PPMLR_E_INVALID, "set_tiles: (C + 14) * L exceeds the thread budget");
     c->tile[axis] = make_tile(axis, c->n, rs, C, L);
     c->mode[axis] = 0;

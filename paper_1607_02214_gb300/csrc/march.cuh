@@ -270,6 +270,7 @@ __global__ void __launch_bounds__(32 * MARCH_WARPS, 1) sweep_march_kernel(const 
             const float ya = fsqrt<float, false>(rho3) * fabsf(Bn3) * dtm;
             const float own[7] = {rho3, u3, v1_3, v2_3, B1_3, B2_3, p3};
             const bool blend = flat != 0.0f;
+            const AvgCoef<float> kf = avg_coef<float>(yf), ka = avg_coef<float>(ya);
 #pragma unroll
             for (int v = 0; v < 7; v++) {
                 float lft = eA[v], rgt = eB[v];
@@ -277,13 +278,14 @@ __global__ void __launch_bounds__(32 * MARCH_WARPS, 1) sweep_march_kernel(const 
                     lft = flat * own[v] + (1.0f - flat) * lft;
                     rgt = flat * own[v] + (1.0f - flat) * rgt;
                 }
-                const float a6 = monotone<float, false>(own[v], lft, rgt);
-                const float y = (v == 2 || v == 3) ? ya : yf;
-                sl[v] = avg_right<float>(lft, rgt, a6, y);
-                sr[v] = avg_left<float>(lft, rgt, a6, y);
+                float dl2, dr2;
+                monotone_d(own[v], lft, rgt, dl2, dr2);
+                const AvgCoef<float> &k = (v == 2 || v == 3) ? ka : kf;
+                sl[v] = avg_right_d<float>(own[v], dl2, dr2, k);
+                sr[v] = avg_left_d<float>(own[v], dl2, dr2, k);
                 if (v == 4 || v == 5) {
-                    sl[v + 3] = avg_right<float>(lft, rgt, a6, ya);
-                    sr[v + 3] = avg_left<float>(lft, rgt, a6, ya);
+                    sl[v + 3] = avg_right_d<float>(own[v], dl2, dr2, ka);
+                    sr[v + 3] = avg_left_d<float>(own[v], dl2, dr2, ka);
                 }
             }
         }
@@ -378,18 +380,15 @@ __global__ void __launch_bounds__(32 * MARCH_WARPS, 1) sweep_march_kernel(const 
         {
             const int z = g - 6;
             const float del_m = dtr * us13, del_p = dtr * us11;
-            float pl[7], pr[7], p6[7];
+            float dl2[7], dr2[7];                      // one-sided differences of the constrained parabola
 #pragma unroll
-            for (int v = 0; v < 7; v++) {
-                pl[v] = reP[v];
-                pr[v] = ren[v];
-                p6[v] = monotone<float, false>(qL6[v], pl[v], pr[v]);
-            }
+            for (int v = 0; v < 7; v++) monotone_d(qL6[v], reP[v], ren[v], dl2[v], dr2[v]);
             if (del_m < 0.0f) {                        // zone g-6 is the donor of g-13/2
                 const float y = -del_m * idxL6;
                 if (sliver_too_wide<float, false>(y) && z >= g0 && z <= g0 + Ce) flags |= FLAG_CFL;
+                const AvgCoef<float> k = avg_coef<float>(y);
 #pragma unroll
-                for (int v = 0; v < 7; v++) Fp[v] = del_m * avg_left<float>(pl[v], pr[v], p6[v], y);
+                for (int v = 0; v < 7; v++) Fp[v] = del_m * avg_left_d<float>(qL6[v], dl2[v], dr2[v], k);
             } else {
 #pragma unroll
                 for (int v = 0; v < 7; v++) Fp[v] = Fc[v];
@@ -397,8 +396,9 @@ __global__ void __launch_bounds__(32 * MARCH_WARPS, 1) sweep_march_kernel(const 
             if (del_p > 0.0f) {                        // zone g-6 is the donor of g-11/2
                 const float y = del_p * idxL6;
                 if (sliver_too_wide<float, false>(y) && z >= g0 - 1 && z <= g0 + Ce - 1) flags |= FLAG_CFL;
+                const AvgCoef<float> k = avg_coef<float>(y);
 #pragma unroll
-                for (int v = 0; v < 7; v++) Fc[v] = del_p * avg_right<float>(pl[v], pr[v], p6[v], y);
+                for (int v = 0; v < 7; v++) Fc[v] = del_p * avg_right_d<float>(qL6[v], dl2[v], dr2[v], k);
             } else {
 #pragma unroll
                 for (int v = 0; v < 7; v++) Fc[v] = 0.0f;

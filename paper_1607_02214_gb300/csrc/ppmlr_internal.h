@@ -16,6 +16,17 @@ constexpr int NSM = 28;        // shared-memory exchange values per slot (see sw
 constexpr int NSMP = 29;       // slot pitch in values: odd, so consecutive slots hit distinct banks
 constexpr int MAXT = 512;      // threads per tile (one thread per cell position and lane), mixed path
 constexpr int MAXT_F64 = 448;  // FP64 path: fewer threads, up to 146 registers each
+// Contracted FP64 x sweep: its kernel is held to 96 registers, so a block of
+// up to 640 threads fits one SM (its 20 warps' registers split over the four
+// schedulers); the budget covers two whole 256-cell pencils (540 threads)
+constexpr int MAXT_F64_X = 576;
+
+// Thread budget of a tile: the limit on (C + 2*GH) * L.
+inline int tile_budget(int prec, int dir)
+{
+    if (prec == PPMLR_MIXED) return MAXT;
+    return prec == PPMLR_FP64 && dir == 0 ? MAXT_F64_X : MAXT_F64;
+}
 
 enum : int { FLAG_CFL = 1, FLAG_NONFINITE = 2, FLAG_TIMEOUT = 4, FLAG_BOUNDS = 8 };
 

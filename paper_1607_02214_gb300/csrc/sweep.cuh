@@ -83,8 +83,9 @@ __device__ __forceinline__ double pow2_scale(double x, int k)
 // 1/x in the contracted double form: the hardware's approximate reciprocal
 // refined by one cubically convergent Newton-Raphson step,
 // r (1 + e + e^2) with e = 1 - x r (three fused multiply-adds: from a seed
-// good to ~2^-22 the error falls to ~2^-66, i.e. the result is within an
-// ulp of 1/x, not necessarily the correctly rounded quotient); other forms
+// good to ~2^-20, as measured on GB300, the error falls to ~2^-60, i.e. the
+// result is within an ulp of 1/x, not necessarily the correctly rounded
+// quotient); other forms
 // divide.  x finite and non-zero where it is used.
 template <typename R, bool EX>
 __device__ __forceinline__ R recip(R x)
@@ -124,16 +125,26 @@ __device__ __forceinline__ bool lt0(R x)
     else return x < R(0);
 }
 
-// Square root of a non-negative value.  Contracted FP64 form: x * rsqrt(x)
-// (the GB300's FP64 pipe spends ~5.9 slots on a reciprocal square root and
-// ~8.6 on a correctly rounded square root; this one is within a few ulp),
-// zero for x = 0; otherwise the library square root.
+// Square root of a non-negative value.  Contracted FP64 form: from the
+// hardware's approximate reciprocal square root y (~2^-20), s = x y is
+// refined by one step of Householder's third-order iteration,
+// sqrt(x) = s (1 - e)^(-1/2) ~ s (1 + e/2 + 3 e^2/8) with e = 1 - s y
+// (five FP64 instructions; the error falls to ~2.5 |e/2|^3 ~ 2^-59, so the
+// result is within an ulp of the correctly rounded root -- measured on GB300
+// over 2^26 arguments spanning 2^-1000..2^1000 -- which costs the GB300's
+// FP64 pipe ~8.6 slots); zero for x = 0 and, as x is a
+// sum of squares or a density here, for subnormal x; otherwise the library
+// square root.
 template <typename R, bool EX>
 __device__ __forceinline__ R fsqrt(R x)
 {
     if constexpr (!EX && std::is_same<R, double>::value) {
-        const double r = x * rsqrt(x);
-        return __double_as_longlong(x) > 0 ? r : 0.0;
+        double y;
+        asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+        const double s = x * y;
+        const double e = fma(-s, y, 1.0);
+        const double r = fma(s * e, fma(e, 0.375, 0.5), s);
+        return __double_as_longlong(x) >= 0x0010000000000000LL ? r : 0.0;   // the smallest normal double
     } else {
         return K<R>::sq(x);
     }
@@ -218,14 +229,14 @@ __device__ __forceinline__ void two_shock(const int iters, const R uL, const R u
 // Lagrangian fast impedance W = rho c_f without a reciprocal of rho:
 // W^2 = rho (rho c_f^2) = rho (S + sqrt(S^2 - 4 gamma p Bn^2)) / 2 with
 // S = gamma p + |B|^2 (the fast-speed formula multiplied through by rho).
-template <typename R>
-__device__ __forceinline__ R fast_impedance(R rho, R p, R Bn, R B1, R B2, R gam)
+// Contracted FP64 form, from parts its callers share: b2 = |B|^2 and
+// bn4 = 4 Bn^2 (the factors 4 and 1/2 as exponent moves on the integer pipe).
+__device__ __forceinline__ double fast_impedance(double rho, double p, double b2, double bn4, double gam)
 {
-    // (the factors 4 and 1/2 as exponent moves on the integer pipe)
-    const R gp = gam * p;
-    const R S = gp + (Bn * Bn + B1 * B1 + B2 * B2);
-    const R D = S * S - pow2_scale(gp, 2) * (Bn * Bn);  // fsqrt gives 0 for D <= 0
-    return fsqrt<R, false>(rho * pow2_scale(S + fsqrt<R, false>(D), -1));
+    const double gp = gam * p;
+    const double S = gp + b2;
+    const double D = fma(-gp, bn4, S * S);              // fsqrt gives 0 for D <= 0
+    return fsqrt<double, false>(rho * pow2_scale(S + fsqrt<double, false>(D), -1));
 }
 
 // Earth dipole along -z: B_d = M [3 (m.r) r - m r^2] / r^5, m = -z.
@@ -346,6 +357,61 @@ __device__ __forceinline__ R monotone(R ai, R &l, R &r)
     return R(6) * (ai - R(0.5) * (l + r));
 }
 
+// The monotonicity constraint as the one-sided differences of the constrained
+// parabola (contracted and mixed forms): with dl = ai - l, dr = r - ai its
+// ends are ai - dl2 and ai + dr2 and a6 = 3 (dl2 - dr2): dl2 = dr2 = 0 at an
+// extremum (dl, dr of different sign or zero), dl2 = 2 dr where |dl| > 2 |dr|,
+// dr2 = 2 dl where |dr| > 2 |dl|, else dl2 = dl, dr2 = dr (the same cases as
+// `monotone`).  Double: the tests on the bit patterns and the doublings as
+// exponent increments on the integer pipe (exact for normal numbers; a
+// subnormal difference is doubled to within 2^-1022), two FP64 instructions.
+__device__ __forceinline__ void monotone_d(double ai, double l, double r, double &dl2, double &dr2)
+{
+    const double dl = ai - l, dr = r - ai;
+    constexpr long long twice = 1LL << 52;
+    const long long bl = __double_as_longlong(dl), br = __double_as_longlong(dr);
+    const long long ml = mag_d(dl), mr = mag_d(dr);
+    long long l2 = ml > mr + twice ? br + twice : bl;
+    long long r2 = mr > ml + twice ? bl + twice : br;
+    if (!same_sign_d(dr, dl)) { l2 = 0; r2 = 0; }
+    dl2 = __longlong_as_double(l2);
+    dr2 = __longlong_as_double(r2);
+}
+__device__ __forceinline__ void monotone_d(float ai, float l, float r, float &dl2, float &dr2)
+{
+    const float dl = ai - l, dr = r - ai;
+    const bool ext = dl * dr <= 0.0f;
+    const float adl = fabsf(dl), adr = fabsf(dr);
+    const float l2 = adl > adr + adr ? dr + dr : dl;
+    const float r2 = adr > adl + adl ? dl + dl : dr;
+    dl2 = ext ? 0.0f : l2;
+    dr2 = ext ? 0.0f : r2;
+}
+
+// Averages of the parabola over the fraction y of the zone at its right and
+// left ends (below), written with the one-sided differences of monotone_d:
+// right: ai + (1 - y)^2 dr2 + y (1 - y) dl2; left: ai - (1 - y)^2 dl2 -
+// y (1 - y) dr2 (the same polynomials in y as avg_right / avg_left with
+// l = ai - dl2, r = ai + dr2, a6 = 3 (dl2 - dr2)); two fused multiply-adds
+// each once P = (1 - y)^2 and Q = y (1 - y) are formed for the fraction.
+template <typename R> struct AvgCoef { R P, Q; };
+template <typename R>
+__device__ __forceinline__ AvgCoef<R> avg_coef(R y)
+{
+    const R u = R(1) - y;
+    return AvgCoef<R>{u * u, y * u};
+}
+template <typename R>
+__device__ __forceinline__ R avg_right_d(R ai, R dl2, R dr2, const AvgCoef<R> &k)
+{
+    return fma(k.Q, dl2, fma(k.P, dr2, ai));
+}
+template <typename R>
+__device__ __forceinline__ R avg_left_d(R ai, R dl2, R dr2, const AvgCoef<R> &k)
+{
+    return fma(-k.Q, dr2, fma(-k.P, dl2, ai));
+}
+
 template <typename R>
 __device__ __forceinline__ R avg_right(R l, R r, R a6, R y)
 {
@@ -395,14 +461,17 @@ __device__ __forceinline__ EdgeCoef<R> edge_coef(R x0, R x1, R x2, R x3)
         const R d1 = R(2) * x1 + x2, d2 = R(2) * x2 + x1, d3 = x1 + x2, d4 = x0 + x1 + x2 + x3;
         const R d12 = d1 * d2, d34 = d3 * d4;
         const R inv = recip<R, EX>(d12 * d34);
-        const R r1 = d2 * d34 * inv, r2 = d1 * d34 * inv, r3 = d12 * d4 * inv, r4 = d12 * d3 * inv;
+        const R i12 = d34 * inv, i34 = d12 * inv;          // 1 / d12, 1 / d34
+        const R r1 = d2 * i12, r2 = d1 * i12, r3 = d4 * i34, r4 = d3 * i34;
         const R z1 = (x0 + x1) * r1, z2 = (x3 + x2) * r2;
+        // k1 = (x1/d3) (1 + 2 (x2/d4)(z1 - z2)), k4 = (x1/d4) z1, k5 = (x2/d4) z2
+        const R x1r3 = x1 * r3, x2r4 = x2 * r4;
         EdgeCoef<R> k;
-        k.k1 = x1 * r3 * (R(1) + R(2) * x2 * r4 * (z1 - z2));
+        k.k1 = x1r3 + x1r3 * (R(2) * x2r4 * (z1 - z2));
         k.k2 = R(0);
         k.k3 = R(0);
-        k.k4 = x1 * z1 * r4;
-        k.k5 = x2 * z2 * r4;
+        k.k4 = (x1 * r4) * z1;
+        k.k5 = x2r4 * z2;
         return k;
     }
     R z1 = (x0 + x1) / (R(2) * x1 + x2);
@@ -672,9 +741,15 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     }
     if constexpr (F64) pdel = pr;
     if (act) {
-        R Pt = pr + R(0.5) * (Bn * Bn + B1 * B1 + B2 * B2);
-        if constexpr (F64 && !EX) W = fast_impedance<R>(rho, pr, Bn, B1, B2, gam);
-        else W = rho * fsqrt<R, EX>(fast2<R, EX>(rho, pr, Bn, B1, B2, gam));
+        R Pt;
+        if constexpr (F64 && !EX) {     // |B|^2 shared by the total pressure and the impedance
+            const double bn2 = Bn * Bn, b2 = fma(B2, B2, fma(B1, B1, bn2));
+            Pt = fma(0.5, b2, pr);
+            W = fast_impedance(rho, pr, b2, pow2_scale(bn2, 2), gam);
+        } else {
+            Pt = pr + R(0.5) * (Bn * Bn + B1 * B1 + B2 * B2);
+            W = rho * fsqrt<R, EX>(fast2<R, EX>(rho, pr, Bn, B1, B2, gam));
+        }
         SM(A_RHO, s) = rho; SM(A_U, s) = u; SM(A_V1, s) = v1; SM(A_V2, s) = v2;
         SM(A_B1, s) = B1; SM(A_B2, s) = B2; SM(A_P, s) = pdel; SM(A_DM, s) = dm;
         SM(A_PT, s) = Pt; SM(A_BN, s) = Bn;
@@ -829,6 +904,8 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         bool blend = true;
         if constexpr (!EX && F64) blend = __double_as_longlong(flat) != 0;
         else if constexpr (!EX) blend = flat != R(0);
+        AvgCoef<R> kf{}, ka{};
+        if constexpr (!EX) { kf = avg_coef<R>(yf); ka = avg_coef<R>(ya); }
 #pragma unroll
         for (int v = 0; v < 7; v++) {
             R lft = SM(SC0 + v, s - PS), rgt = edg[v];
@@ -836,13 +913,25 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
                 lft = flat * own[v] + (R(1) - flat) * lft;
                 rgt = flat * own[v] + (R(1) - flat) * rgt;
             }
-            R a6 = monotone<R, EX>(own[v], lft, rgt);
-            R y = (v == 2 || v == 3) ? ya : yf;
-            sl[v] = avg_right<R>(lft, rgt, a6, y);
-            srv[v] = avg_left<R>(lft, rgt, a6, y);
-            if (v == 4 || v == 5) {
-                sl[v + 3] = avg_right<R>(lft, rgt, a6, ya);
-                srv[v + 3] = avg_left<R>(lft, rgt, a6, ya);
+            if constexpr (EX) {
+                R a6 = monotone<R, EX>(own[v], lft, rgt);
+                R y = (v == 2 || v == 3) ? ya : yf;
+                sl[v] = avg_right<R>(lft, rgt, a6, y);
+                srv[v] = avg_left<R>(lft, rgt, a6, y);
+                if (v == 4 || v == 5) {
+                    sl[v + 3] = avg_right<R>(lft, rgt, a6, ya);
+                    srv[v + 3] = avg_left<R>(lft, rgt, a6, ya);
+                }
+            } else {
+                R dl2, dr2;
+                monotone_d(own[v], lft, rgt, dl2, dr2);
+                const AvgCoef<R> &k = (v == 2 || v == 3) ? ka : kf;
+                sl[v] = avg_right_d<R>(own[v], dl2, dr2, k);
+                srv[v] = avg_left_d<R>(own[v], dl2, dr2, k);
+                if (v == 4 || v == 5) {
+                    sl[v + 3] = avg_right_d<R>(own[v], dl2, dr2, ka);
+                    srv[v + 3] = avg_left_d<R>(own[v], dl2, dr2, ka);
+                }
             }
         }
 #pragma unroll
@@ -862,20 +951,27 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         // total pressures relative to p_reff (mixed path; 0 for the FP64
         // forms): u*, P* - p_reff and the Lagrangian momentum update need only
         // their differences and weighted means
-        R PL = sl[6] + R(0.5) * (sl[4] * sl[4] + sl[5] * sl[5]);
-        R PR = Rs[6] + R(0.5) * (Rs[4] * Rs[4] + Rs[5] * Rs[5]);
+        R PL, PR;
         R pref = R(0);
         if constexpr (!F64) pref = a.p_reff;
         R WL, WR;
+        if constexpr (F64 && !EX) {     // the transverse |B|^2 of each side shared by P and W
+            const double bn2 = Bnf * Bnf, bn4 = pow2_scale(bn2, 2);
+            const double btL = fma(sl[5], sl[5], sl[4] * sl[4]), btR = fma(Rs[5], Rs[5], Rs[4] * Rs[4]);
+            PL = fma(0.5, btL, sl[6]);
+            PR = fma(0.5, btR, Rs[6]);
+            WL = fast_impedance(sl[0], sl[6], btL + bn2, bn4, gam);
+            WR = fast_impedance(Rs[0], Rs[6], btR + bn2, bn4, gam);
+        } else {
+            PL = sl[6] + R(0.5) * (sl[4] * sl[4] + sl[5] * sl[5]);
+            PR = Rs[6] + R(0.5) * (Rs[4] * Rs[4] + Rs[5] * Rs[5]);
+        }
         if constexpr (!F64) {
             WL = sl[0] * K<R>::sq(fast2<R, EX>(sl[0], sl[6] + pref, Bnf, sl[4], sl[5], gam));
             WR = Rs[0] * K<R>::sq(fast2<R, EX>(Rs[0], Rs[6] + pref, Bnf, Rs[4], Rs[5], gam));
         } else if constexpr (EX) {
             WL = sl[0] * K<R>::sq(fast2<R, EX>(sl[0], sl[6], Bnf, sl[4], sl[5], gam));
             WR = Rs[0] * K<R>::sq(fast2<R, EX>(Rs[0], Rs[6], Bnf, Rs[4], Rs[5], gam));
-        } else {            // contracted FP64 form: no reciprocal of the traced densities
-            WL = fast_impedance<R>(sl[0], sl[6], Bnf, sl[4], sl[5], gam);
-            WR = fast_impedance<R>(Rs[0], Rs[6], Bnf, Rs[4], Rs[5], gam);
         }
         if constexpr (!F64) {
             const R PLa = PL + pref, PRa = PR + pref;          // the nonlinear solver takes absolute pressures
@@ -889,6 +985,11 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         if constexpr (EX) {
             us = (WL * sl[1] + WR * Rs[1] + PL - PR) / (WL + WR);
             Ps = (WR * PL + WL * PR + WL * WR * (sl[1] - Rs[1])) / (WL + WR);
+        } else if constexpr (F64) {
+            // P* = PL - WL (u* - uL): the same value in exact arithmetic
+            // (the left wave's jump condition), two instructions
+            us = (WL * sl[1] + WR * Rs[1] + PL - PR) * recip<R, EX>(WL + WR);
+            Ps = fma(-WL, us - sl[1], PL);
         } else {
             const R iW = recip<R, EX>(WL + WR);
             us = (WL * sl[1] + WR * Rs[1] + PL - PR) * iW;
@@ -897,30 +998,56 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         R Ss;
         if constexpr (F64 && !EX) Ss = Ps - pow2_scale(Bnf, -1) * Bnf;
         else Ss = Ps - R(0.5) * Bnf * Bnf;
-        R ZL = fsqrt<R, EX>(sl[0]) * K<R>::ab(Bnf);
-        R ZR = fsqrt<R, EX>(Rs[0]) * K<R>::ab(Bnf);
         R vs[2], ss[2];
-        const R zsum = ZL + ZR;
-        const bool zero_z = (EX || !F64) ? zsum == R(0) : !pos_d(zsum);   // Z >= 0: zero or not
-        const R iZ = (EX || zero_z) ? R(0) : recip<R, EX>(zsum);
+        if constexpr (F64 && !EX) {
+            // Alfven impedances Z = sqrt(rho) |Bn|: with s = Bn B_t the common
+            // factor |Bn| cancels from v* = (ZL vL + ZR vR + sR - sL)/(ZL + ZR),
+            // v* = (qL vL + qR vR + sgn(Bn)(B_tR - B_tL))/(qL + qR) with
+            // q = sqrt(rho), and s* = sL + ZL (v* - vL) (as P* above) =
+            // Bn (B_tL + sgn(Bn) qL (v* - vL)); Bn = 0: v* the mean, s* = 0
+            const bool zero_z = (__double_as_longlong(Bnf) << 1) == 0;
+            const double qL = fsqrt<R, EX>(sl[0]), qR = fsqrt<R, EX>(Rs[0]);
+            const double iQ = recip<R, EX>(qL + qR);
+            const long long sgn = __double_as_longlong(Bnf) & 0x8000000000000000LL;
+            const double sqL = __longlong_as_double(__double_as_longlong(qL) ^ sgn);     // sgn(Bn) qL
 #pragma unroll
-        for (int t = 0; t < 2; t++) {
-            R vL = sl[2 + t], vR = Rs[2 + t];
-            R sL = Bnf * sl[7 + t], sR = Bnf * Rs[7 + t];
-            if (zero_z) {
-                vs[t] = R(0.5) * (vL + vR);
-                ss[t] = R(0);
-            } else if constexpr (EX) {
-                vs[t] = (ZL * vL + ZR * vR + sR - sL) / (ZL + ZR);
-                ss[t] = (ZR * sL + ZL * sR + ZL * ZR * (vR - vL)) / (ZL + ZR);
-            } else {
-                vs[t] = (ZL * vL + ZR * vR + sR - sL) * iZ;
-                ss[t] = (ZR * sL + ZL * sR + ZL * ZR * (vR - vL)) * iZ;
+            for (int t = 0; t < 2; t++) {
+                const double vL = sl[2 + t], vR = Rs[2 + t];
+                const double dB = __longlong_as_double(__double_as_longlong(Rs[7 + t] - sl[7 + t]) ^ sgn);
+                if (zero_z) {
+                    vs[t] = 0.5 * (vL + vR);
+                    ss[t] = 0.0;
+                } else {
+                    vs[t] = (fma(qL, vL, qR * vR) + dB) * iQ;
+                    ss[t] = Bnf * fma(sqL, vs[t] - vL, sl[7 + t]);
+                }
+            }
+        } else {
+            R ZL = fsqrt<R, EX>(sl[0]) * K<R>::ab(Bnf);
+            R ZR = fsqrt<R, EX>(Rs[0]) * K<R>::ab(Bnf);
+            const R zsum = ZL + ZR;
+            const bool zero_z = zsum == R(0);
+            const R iZ = (EX || zero_z) ? R(0) : recip<R, EX>(zsum);
+#pragma unroll
+            for (int t = 0; t < 2; t++) {
+                R vL = sl[2 + t], vR = Rs[2 + t];
+                R sL = Bnf * sl[7 + t], sR = Bnf * Rs[7 + t];
+                if (zero_z) {
+                    vs[t] = R(0.5) * (vL + vR);
+                    ss[t] = R(0);
+                } else if constexpr (EX) {
+                    vs[t] = (ZL * vL + ZR * vR + sR - sL) / (ZL + ZR);
+                    ss[t] = (ZR * sL + ZL * sR + ZL * ZR * (vR - vL)) / (ZL + ZR);
+                } else {
+                    vs[t] = (ZL * vL + ZR * vR + sR - sL) * iZ;
+                    ss[t] = (ZR * sL + ZL * sR + ZL * ZR * (vR - vL)) * iZ;
+                }
             }
         }
         rs_u = us; rs_S = Ss; rs_s1 = ss[0]; rs_s2 = ss[1];
         rs_b1 = Bnf * vs[0]; rs_b2 = Bnf * vs[1];
-        rs_fe = (Ss + pref) * us - ss[0] * vs[0] - ss[1] * vs[1];     // absolute S* in the energy flux
+        if constexpr (F64) rs_fe = Ss * us - ss[0] * vs[0] - ss[1] * vs[1];
+        else rs_fe = (Ss + pref) * us - ss[0] * vs[0] - ss[1] * vs[1];     // absolute S* in the energy flux
         SM(SC0 + 0, s) = rs_u; SM(SC0 + 1, s) = rs_S; SM(SC0 + 2, s) = rs_s1; SM(SC0 + 3, s) = rs_s2;
         SM(SC0 + 4, s) = rs_b1; SM(SC0 + 5, s) = rs_b2; SM(SC0 + 6, s) = rs_fe;
     }
@@ -1022,6 +1149,8 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
 
     // ---------------- P9: remap parabolas and donor fluxes ----------------
     if (act && p >= 6 && p <= NPe - 7) {
+        // exact form: the constrained ends and a6; otherwise the one-sided
+        // differences of the constrained parabola (pl, pr_ reused for them)
         R pl[7], pr_[7], p6[7];
 #pragma unroll
         for (int v = 0; v < 7; v++) {
@@ -1033,14 +1162,21 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
                 pl[v] = pl[v] * (R(1) - eta_k) + eta_k * ld;
                 pr_[v] = pr_[v] * (R(1) - eta_k) + eta_k * rd;
             }
-            p6[v] = monotone<R, EX>(qL[v], pl[v], pr_[v]);
+            if constexpr (EX) p6[v] = monotone<R, EX>(qL[v], pl[v], pr_[v]);
+            else monotone_d(qL[v], pl[v], pr_[v], pl[v], pr_[v]);
         }
         if (p <= NPe - 8) {                       // edge p+1/2: donor is this zone when del >= 0
             if (gt0<R, EX>(del_p)) {
                 R y = EX ? del_p / dxL : del_p * idxL_k;
                 if (sliver_too_wide<R, EX>(y)) atomicOr(a.flags, FLAG_CFL);
+                if constexpr (EX) {
 #pragma unroll
-                for (int v = 0; v < 7; v++) SM(flux_slot(v), s) = del_p * avg_right<R>(pl[v], pr_[v], p6[v], y);
+                    for (int v = 0; v < 7; v++) SM(flux_slot(v), s) = del_p * avg_right<R>(pl[v], pr_[v], p6[v], y);
+                } else {
+                    const AvgCoef<R> k = avg_coef<R>(y);
+#pragma unroll
+                    for (int v = 0; v < 7; v++) SM(flux_slot(v), s) = del_p * avg_right_d<R>(qL[v], pl[v], pr_[v], k);
+                }
             } else if (!lt0<R, EX>(del_p)) {
 #pragma unroll
                 for (int v = 0; v < 7; v++) SM(flux_slot(v), s) = R(0);
@@ -1049,8 +1185,14 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         if (p >= 7 && lt0<R, EX>(del_m)) {       // edge p-1/2: donor is this zone when del < 0
             R y = EX ? -del_m / dxL : -del_m * idxL_k;
             if (sliver_too_wide<R, EX>(y)) atomicOr(a.flags, FLAG_CFL);
+            if constexpr (EX) {
 #pragma unroll
-            for (int v = 0; v < 7; v++) SM(flux_slot(v), s - PS) = del_m * avg_left<R>(pl[v], pr_[v], p6[v], y);
+                for (int v = 0; v < 7; v++) SM(flux_slot(v), s - PS) = del_m * avg_left<R>(pl[v], pr_[v], p6[v], y);
+            } else {
+                const AvgCoef<R> k = avg_coef<R>(y);
+#pragma unroll
+                for (int v = 0; v < 7; v++) SM(flux_slot(v), s - PS) = del_m * avg_left_d<R>(qL[v], pl[v], pr_[v], k);
+            }
         }
     }
     __syncthreads();
@@ -1311,16 +1453,20 @@ __global__ void __launch_bounds__(MaxThreads<R>::value, TmaMinBlocks<R, PERSIST>
 // Register cap of the single-domain kernel: the tile-size limit's share of
 // the register file, except for the contracted FP64 form, where a tighter
 // cap (a few spilled values) lets two blocks of the usual tile shapes reside
-// on an SM: 96 for the x sweep (2 x 288 threads), 72 for y and z
-// (2 x 416 threads).  Measured on GB300 at 256x192x192: x 18.1 -> 16.5 ms,
-// y and z 16.8 -> 15.9 ms per sweep.
+// on an SM: 72 for y and z (2 x 416 threads; measured on GB300 at
+// 256x192x192: 16.8 -> 15.9 ms per sweep), 96 for x (two blocks of 288
+// threads, or one of two whole 256-cell pencils, 544 threads: each of the
+// SM's four schedulers holds a quarter of its registers, so a block of 17 to
+// 20 warps needs 5 x 32 x 96 <= 16384 registers per scheduler).
 template <int DIR, typename R, bool EX> struct SweepRegCap {
     static constexpr int value = 65536 / MaxThreads<R>::value;
 };
 template <int DIR> struct SweepRegCap<DIR, double, false> {
     static constexpr int value = DIR == 0 ? 96 : 72;
 };
-static_assert(SweepRegCap<0, double, false>::value * MAXT_F64 <= 65536, "FP64 tile budget vs register cap");
+static_assert(SweepRegCap<0, double, false>::value * 32 * ((MAXT_F64_X / 32 + 3) / 4) <= 16384,
+              "FP64 x tile budget vs register cap (registers per scheduler)");
+static_assert(SweepRegCap<1, double, false>::value * MAXT_F64 <= 65536, "FP64 tile budget vs register cap");
 
 // Single domain: one block per tile.
 template <int DIR, typename R, bool EX>

@@ -107,6 +107,7 @@ SIGNATURES = [
                                      c_double, c_double, c_double, c_double, c_double, c_int, POINTER(c_double),
                                      c_void_p]),
     ("ppmlr_measure_pipe_rates", c_int, [c_void_p, POINTER(c_double)]),
+    ("ppmlr_selftest_fp64_arith", c_int, [c_void_p, c_longlong, POINTER(c_double)]),
     ("ppmlr_set_march_chunk", c_int, [c_void_p, c_int, c_int]),
 ]
 
@@ -142,6 +143,17 @@ def measure_pipe_rates(stream=None):
     if st != PPMLR_OK:
         raise PPMLRError(st, "ppmlr_measure_pipe_rates failed")
     return {"dfma_per_s": out[0], "dadd_per_s": out[1], "ffma_per_s": out[2]}
+
+
+def selftest_fp64_arith(n=1 << 22, stream=None):
+    """Largest error, in ulps of the correctly rounded result, of the
+    PPMLR_FP64 form's square root and reciprocal over n arguments spanning
+    2^-1000..2^1000 (ppmlr_selftest_fp64_arith)."""
+    out = (c_double * 2)()
+    st = load().ppmlr_selftest_fp64_arith(c_void_p(stream), n, out)
+    if st != PPMLR_OK:
+        raise PPMLRError(st, "ppmlr_selftest_fp64_arith failed")
+    return {"sqrt_ulp": out[0], "recip_ulp": out[1]}
 
 
 class PPMLRError(RuntimeError):

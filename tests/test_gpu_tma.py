@@ -72,10 +72,31 @@ def test_tma_forms_match_plain(case, precision, form):
 def test_set_tiles_bounds():
     got = make_gpu(CASES["periodic_ragged"](), ppmlr.PPMLR_FP64)
     before = got.tiles()
-    for axis, C, L in [(3, 10, 1), (-1, 10, 1), (1, 0, 1), (1, 30, 1), (1, 10, 0), (0, 38, 9)]:
+    for axis, C, L in [(3, 10, 1), (-1, 10, 1), (1, 0, 1), (1, 30, 1), (1, 10, 0), (0, 38, 12), (1, 15, 16)]:
         with pytest.raises(ppmlr.PPMLRError):
             got.set_tiles(axis, C, L)
     assert got.tiles() == before
     got.set_sweep_form(2, 2)
     got.set_tiles(2, 23, 4)
     assert got.sweep_forms()[2] == 0
+
+
+def test_fp64_x_tiles_above_the_general_budget():
+    # the contracted FP64 x sweep takes tiles of up to 576 threads (its
+    # kernel's register cap leaves room for them); the other forms and
+    # directions keep their budgets
+    pr = CASES["magnetosphere"]()
+    ref = make_gpu(pr, ppmlr.PPMLR_FP64)
+    got = make_gpu(pr, ppmlr.PPMLR_FP64)
+    got.set_tiles(0, 48, 8)                       # 62 x 8 = 496 threads
+    assert got.tiles()[0][0] == 48 and got.tiles()[1][0] == 8
+    with pytest.raises(ppmlr.PPMLRError):
+        got.set_tiles(1, 40, 16)                  # 54 x 16 = 864
+    with pytest.raises(ppmlr.PPMLRError):
+        make_gpu(pr, ppmlr.PPMLR_FP64_EXACT).set_tiles(0, 48, 8)
+    for _ in range(3):
+        dt = ref.cfl_dt(0.4)
+        ref.step(dt)
+        got.step(dt)
+    got.check()
+    assert np.max(rel_l1(got.get_state(), ref.get_state())) <= 1e-12
