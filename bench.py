@@ -58,19 +58,19 @@ BYTES_PER_CELL_SWEEP = 128      # read 8 FP64 + write 8 FP64
 # top of the state: traffic above the algorithmic 128 / 64 B by that much; the
 # FP64 y and z sweeps (72-register cap) add ~30 B per cell of spill traffic.
 NCU_TRAFFIC = {
-    "fp64:x": {"bytes_per_cell": 151.2, "src": "4cffd53096c27579"},
-    "fp64:y": {"bytes_per_cell": 181.1, "src": "4cffd53096c27579"},
-    "fp64:z": {"bytes_per_cell": 177.0, "src": "4cffd53096c27579"},
-    "fp64:cfl": {"bytes_per_cell": 89.3, "src": "dd8ed0d0de48614f"},
-    "mixed:x": {"bytes_per_cell": 123.5, "src": "e74a977a95a7eb8e"},
-    "mixed:y": {"bytes_per_cell": 124.5, "src": "e74a977a95a7eb8e"},
-    "mixed:z": {"bytes_per_cell": 124.9, "src": "e74a977a95a7eb8e"},
-    "mixed:cfl": {"bytes_per_cell": 64.3, "src": "e75f597d7ca449b3"},
+    "fp64:x": {"bytes_per_cell": 149.4, "src": "267daf6257502b94"},
+    "fp64:y": {"bytes_per_cell": 179.9, "src": "267daf6257502b94"},
+    "fp64:z": {"bytes_per_cell": 176.7, "src": "267daf6257502b94"},
+    "fp64:cfl": {"bytes_per_cell": 89.3, "src": "a2d3f854bdcc55de"},
+    "mixed:x": {"bytes_per_cell": 123.5, "src": "470d4f77700d50d1"},
+    "mixed:y": {"bytes_per_cell": 124.5, "src": "470d4f77700d50d1"},
+    "mixed:z": {"bytes_per_cell": 124.9, "src": "470d4f77700d50d1"},
+    "mixed:cfl": {"bytes_per_cell": 64.3, "src": "76a9917a27ea1e90"},
     # ensemble sweeps: captured on the first 8 of the 48 instances (14.9 M
     # cells; the full ensemble holds ~10 GB), scaled by cells
-    "ensemble:x": {"bytes_per_cell": 125.1, "src": "85d78e838d4282d2"},
-    "ensemble:y": {"bytes_per_cell": 125.5, "src": "85d78e838d4282d2"},
-    "ensemble:z": {"bytes_per_cell": 125.6, "src": "85d78e838d4282d2"},
+    "ensemble:x": {"bytes_per_cell": 125.1, "src": "88331d354fe572c5"},
+    "ensemble:y": {"bytes_per_cell": 125.4, "src": "88331d354fe572c5"},
+    "ensemble:z": {"bytes_per_cell": 125.5, "src": "88331d354fe572c5"},
 }
 
 
