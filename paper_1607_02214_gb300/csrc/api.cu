@@ -39,6 +39,7 @@ struct ppmlr_ctx {
     unsigned long long *floors;
     double *dt_dev;
     double *bd;                  // FP64 forms with a dipole: B_d at every cell (3 arrays, stride `stride`)
+    float *screen;               // FP64 forms: the CFL screen (one float per cell, then the threshold)
     double *partial;
     unsigned int *counter;
     int cfl_blocks;
@@ -445,6 +446,15 @@ ppmlr_status ppmlr_create(const ppmlr_grid *grid, double gamma, const ppmlr_bc *
             return e == cudaErrorMemoryAllocation ? PPMLR_E_OOM : PPMLR_E_CUDA;
         }
     }
+    if (prec != PPMLR_MIXED) {
+        // the two-pass CFL step's screen: a float bound per cell and the threshold
+        e = cudaMalloc(&c->screen, sizeof(float) * ((size_t)ncell + 1));
+        if (e != cudaSuccess) {
+            cudaFree(c->bd); cudaFree(c->inner_mask); cudaFree(c->geof); cudaFree(c->geo); cudaFree(c->state);
+            delete c;
+            return e == cudaErrorMemoryAllocation ? PPMLR_E_OOM : PPMLR_E_CUDA;
+        }
+    }
     *out = c;
     return PPMLR_OK;
 }
@@ -469,6 +479,7 @@ void ppmlr_destroy(ppmlr_ctx *c)
     cudaFree(c->iono.buf); cudaFree(c->iono.cells); cudaFree(c->iono.state);
     cudaFree(c->iono.nodes); cudaFree(c->iono.inner);
     cudaFree(c->bd);
+    cudaFree(c->screen);
     cudaFree(c->inner_mask);
     cudaFree(c->geof);
     cudaFree(c->geo);
@@ -728,11 +739,12 @@ static ppmlr_status launch_cfl_kernel(ppmlr_ctx *c, double cfl, bool advance_tim
     a.inner_mask = c->inner_mask;
     for (int d = 0; d < 3; d++) { a.wf[d] = c->wf[d]; a.cf[d] = c->cf[d]; }
     a.gammaf = (float)a.gamma; a.p_minf = (float)a.p_min; a.Mf = (float)a.M; a.r_innerf = (float)a.r_inner;
+    if (c->screen) { a.screen = c->screen; a.screen_thr = c->screen + c->ncell; }
     int rec = timing_begin(c, 3);
     cudaError_t e = cfl_launchers(c->prec).single(a, c->cfl_blocks, c->stream);
     timing_end(c, rec);
     if (e != cudaSuccess) return cuda_fail(c, e, "cfl launch");
-    c->launches++;
+    c->launches += c->screen ? 2 : 1;
     return PPMLR_OK;
 }
 

@@ -12,14 +12,26 @@
 // per thread (cfl_fp64.cu, with contraction).  Both forms take the inner
 // sphere from the per-cell mask when the context has one (computed on the
 // host with the reference's expression).
+//
+// Two-pass form (single domain, both FP64 forms): a screening pass first
+// evaluates every cell's bound in float arithmetic (the mixed path's
+// double-float pressure, float wave speeds and dipole: no FP64 work) and the
+// smallest positive finite one, m; the FP64 pass then evaluates only the
+// cells whose float bound is at most (1 + 1 %) m, or not a positive finite
+// number.  The float bound is within ~1e-4 of the FP64 one (the fast-speed
+// discriminant's cancellation being the worst case), so the cell holding the
+// FP64 minimum is always among them and dt is the one-pass result bit for
+// bit, at the cost of a float pass (HBM-bound) instead of FP64 work on every
+// cell.
 #pragma once
 #include <math.h>
 
-#include "ppmlr_internal.h"
+#include "sweep.cuh"
 
 namespace ppmlr {
 
 constexpr int CFL_THREADS = 256;
+constexpr float CFL_SCREEN_MARGIN = 0.01f;
 
 static __device__ __forceinline__ double fast2d(double rho, double p, double Bn, double B1, double B2, double gam)
 {
@@ -61,7 +73,144 @@ static __device__ __forceinline__ double block_min(double v)
     return v;
 }
 
-// Block `bid` of `nb` blocks working on the domain described by `a`.
+static __device__ __forceinline__ float block_min_screen(float v)
+{
+    __shared__ float red[CFL_THREADS / 32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fminf(v, __shfl_down_sync(0xffffffffu, v, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < CFL_THREADS / 32 ? red[threadIdx.x] : INFINITY;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v = fminf(v, __shfl_down_sync(0xffffffffu, v, off));
+    }
+    return v;
+}
+
+// Division by a fixed divisor d >= 1 of dividends n < 2^31 by one 32 x 32 ->
+// 64-bit multiply and a shift (Granlund & Montgomery 1994, Thm. 4.2): with
+// l = ceil(log2 d), k = 31 + l and m = ceil(2^k / d) (< 2^32),
+// floor(n / d) = (n m) >> k.  The cell index of a grid stays below 2^31.
+struct FastDiv { unsigned m; int k; };
+static __device__ __forceinline__ FastDiv make_fastdiv(unsigned d)
+{
+    int l = 0;
+    while ((1ull << l) < d) l++;
+    const int k = 31 + l;
+    return FastDiv{(unsigned)(((1ull << k) + d - 1) / d), k};
+}
+static __device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv &f)
+{
+    return (unsigned)(((unsigned long long)n * f.m) >> f.k);
+}
+
+// Double-float quotient with a fast first approximation (the remainder step
+// restores ~44 bits) and the mixed path's double-float pressure built on it.
+static __device__ __forceinline__ df screen_df_div(df x, df y)
+{
+    const float q1 = __fdividef(x.h, y.h);
+    const float p = q1 * y.h;
+    const float pe = fmaf(q1, y.h, -p);
+    const float r = ((x.h - p) - pe + x.l) - q1 * y.l;
+    return quick_two_sum(q1, __fdividef(r, y.h));
+}
+static __device__ __forceinline__ float screen_pressure(const df *q, float gm1)
+{
+    const df mm = df_add(df_add(df_sqr(q[1]), df_sqr(q[2])), df_sqr(q[3]));
+    const df bb = df_add(df_add(df_sqr(q[4]), df_sqr(q[5])), df_sqr(q[6]));
+    df t = df_add(screen_df_div(mm, q[0]), bb);
+    t.h *= 0.5f;
+    t.l *= 0.5f;
+    const df e = df_add(q[7], df_neg(t));
+    return gm1 * (e.h + e.l);
+}
+// sqrt(max(x, 0)) to a few ulp
+static __device__ __forceinline__ float screen_sqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+// fast magnetosonic speed squared along n: (s + sqrt(s^2 - 4 a^2 bn^2)) / 2
+static __device__ __forceinline__ float screen_fast2(float a2, float ir, float Bn, float B1, float B2)
+{
+    const float bn2 = Bn * Bn * ir;
+    const float s = a2 + fmaf(B2, B2, fmaf(B1, B1, Bn * Bn)) * ir;
+    return 0.5f * (s + screen_sqrt(s * s - 4.0f * a2 * bn2));
+}
+
+// Screen value of cell i = (ix, iy, iz): +inf inside the inner sphere (the
+// same test as the FP64 pass), -1 where the float bound is not a positive
+// finite number (the FP64 pass then always evaluates the cell), else the
+// float bound min over d of dx_d / (|v_d| + max(c_f,d(B'), c_f,d(B' + B_d))).
+static __device__ __forceinline__ float screen_bound(const CflArgs &a, const long long i, const int ix, const int iy,
+                                                    const int iz)
+{
+    if (a.inner_mask) {
+        if (a.inner_mask[i]) return INFINITY;
+    } else if (a.r_inner > 0.0) {
+        const double x = a.c[0][ix + GH], y = a.c[1][iy + GH], z = a.c[2][iz + GH];
+        if (x * x + y * y + z * z < a.r_inner * a.r_inner) return INFINITY;
+    }
+    df q[8];
+#pragma unroll
+    for (int v = 0; v < 8; v++) q[v] = split_double_fast(__ldg(a.U[v] + i));
+    float pr = screen_pressure(q, a.gammaf - 1.0f);
+    if (!(pr == pr)) return -1.0f;
+    if (pr < a.p_minf) pr = a.p_minf;
+    float Bd[3];
+    dipole_f(a.Mf, a.cf[0][ix + GH], a.cf[1][iy + GH], a.cf[2][iz + GH], Bd);
+    const float ir = __fdividef(1.0f, q[0].h);
+    const float a2 = a.gammaf * pr * ir;
+    const int idx[3] = {ix, iy, iz};
+    float best = INFINITY;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+        const float Bn = q[4 + d].h, B1 = q[4 + t1].h, B2 = q[4 + t2].h;
+        const float c1 = screen_fast2(a2, ir, Bn, B1, B2);
+        const float c2 = screen_fast2(a2, ir, Bn + Bd[d], B1 + Bd[t1], B2 + Bd[t2]);
+        const float cf = screen_sqrt(fmaxf(c1, c2));
+        best = fminf(best, __fdividef(a.wf[d][idx[d] + GH], fabsf(q[1 + d].h * ir) + cf));
+    }
+    return best > 0.0f && best < INFINITY ? best : -1.0f;
+}
+
+// Screening pass: every cell's screen value to a.screen, and the threshold
+// (1 + margin) x the smallest positive finite bound (+inf if none) to
+// *a.screen_thr, written by the last block (atomic ticket; resets it).  EX
+// only selects the translation unit's copy.
+template <bool EX>
+__global__ void __launch_bounds__(CFL_THREADS) cfl_screen_kernel(CflArgs a)
+{
+    const unsigned ncell = (unsigned)a.n[0] * a.n[1] * a.n[2];      // < 2^31 (checked at creation)
+    const FastDiv fx = make_fastdiv((unsigned)a.n[0]), fy = make_fastdiv((unsigned)a.n[1]);
+    float best = INFINITY;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += gridDim.x * blockDim.x) {
+        const unsigned row = fdiv(i, fx), iz = fdiv(row, fy);
+        const float v = screen_bound(a, i, (int)(i - row * a.n[0]), (int)(row - iz * a.n[1]), (int)iz);
+        a.screen[i] = v;
+        if (v > 0.0f) best = fminf(best, v);
+    }
+    best = block_min_screen(best);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        a.partial[blockIdx.x] = (double)best;
+        __threadfence();
+        const unsigned int ticket = atomicAdd(a.counter, 1u);
+        last = (ticket == gridDim.x - 1u);
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        float m = INFINITY;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) m = fminf(m, (float)__ldcg(a.partial + b));
+        m = block_min_screen(m);
+        if (threadIdx.x == 0) {
+            *a.screen_thr = m * (1.0f + CFL_SCREEN_MARGIN);
+            *a.counter = 0u;
+        }
+    }
+}
+
+// Block `bid` of `nb` blocks working on the domain described by `a`; with a
+// screen, only the cells it marks are evaluated.
 template <bool EX>
 __device__ __forceinline__ void cfl_body(const CflArgs &a, const int bid, const int nb)
 {
@@ -69,8 +218,10 @@ __device__ __forceinline__ void cfl_body(const CflArgs &a, const int bid, const 
     const long long ncell = nx * ny * nz;
     double best = INFINITY;
     double rate = 0.0;        // contracted form with reciprocal widths: max rate of the thread's cells
+    const float thr = a.screen ? __ldcg(a.screen_thr) : 0.0f;
     for (long long i = (long long)bid * blockDim.x + threadIdx.x; i < ncell;
          i += (long long)nb * blockDim.x) {
+        if (a.screen && !(__ldcg(a.screen + i) <= thr)) continue;
         const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / (nx * ny));
         if (a.inner_mask) {
             if (a.inner_mask[i]) continue;
@@ -196,6 +347,11 @@ template <bool EX>
 struct CflVariant {
     static cudaError_t single(const CflArgs &a, int blocks, cudaStream_t s)
     {
+        if (a.screen) {           // two-pass form: the float screen first
+            cfl_screen_kernel<EX><<<blocks, CFL_THREADS, 0, s>>>(a);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
         cfl_kernel<EX><<<blocks, CFL_THREADS, 0, s>>>(a);
         return cudaGetLastError();
     }

@@ -3,7 +3,7 @@
 // with float wave speeds, the double-float pressure recovery of the mixed
 // sweep and no FP64 instructions in the per-cell work.  Block minima and the
 // last-block combine (atomic ticket, no float atomics) as in cfl.cu.
-#include "sweep.cuh"
+#include "cfl.cuh"
 
 namespace ppmlr {
 
@@ -26,10 +26,9 @@ __device__ __forceinline__ float block_min_f(float v)
 
 // Bound dx_d / (|v_d| + c_f,d) of one cell (INFINITY inside the inner sphere)
 // from its 8 conserved values.
-__device__ __forceinline__ float cell_bound(const CflArgs &a, const long long i, const double *u)
+__device__ __forceinline__ float cell_bound(const CflArgs &a, const int ix, const int iy, const int iz,
+                                            const double *u)
 {
-    const long long nx = a.n[0], ny = a.n[1];
-    const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / (nx * ny));
     const float x = a.cf[0][ix + GH], y = a.cf[1][iy + GH], z = a.cf[2][iz + GH];
     if (a.r_innerf > 0.0f) {
         const float r2 = x * x + y * y + z * z, ri2 = a.r_innerf * a.r_innerf;
@@ -65,21 +64,37 @@ __device__ __forceinline__ float cell_bound(const CflArgs &a, const long long i,
 
 // Grid-stride pass over the cells, two cells per iteration: both cells' 16
 // loads are issued before either is used, doubling the loads in flight.
+// Cell indices (ix, iy, iz) of i < 2^31 by two fixed-divisor divisions.
+__device__ __forceinline__ void cell_xyz(const unsigned i, const CflArgs &a, const FastDiv &fx, const FastDiv &fy,
+                                         int &ix, int &iy, int &iz)
+{
+    const unsigned row = fdiv(i, fx), z = fdiv(row, fy);
+    ix = (int)(i - row * (unsigned)a.n[0]);
+    iy = (int)(row - z * (unsigned)a.n[1]);
+    iz = (int)z;
+}
+
 __device__ __forceinline__ void cfl_mixed_body(const CflArgs &a, const int bid, const int nb)
 {
-    const long long ncell = (long long)a.n[0] * a.n[1] * a.n[2];
-    const long long step = (long long)nb * blockDim.x;
+    const unsigned ncell = (unsigned)a.n[0] * a.n[1] * a.n[2];      // < 2^31 (checked at creation)
+    const unsigned step = (unsigned)nb * blockDim.x;
+    const FastDiv fx = make_fastdiv((unsigned)a.n[0]), fy = make_fastdiv((unsigned)a.n[1]);
     float best = INFINITY;
-    for (long long i0 = (long long)bid * blockDim.x + threadIdx.x; i0 < ncell; i0 += 2 * step) {
-        const long long i1 = i0 + step;
+    for (unsigned i0 = (unsigned)bid * blockDim.x + threadIdx.x; i0 < ncell; i0 += 2 * step) {
+        const unsigned i1 = i0 + step;
         const bool two = i1 < ncell;
         double u0[8], u1[8];
 #pragma unroll
         for (int v = 0; v < 8; v++) u0[v] = __ldg(a.U[v] + i0);
 #pragma unroll
         for (int v = 0; v < 8; v++) u1[v] = two ? __ldg(a.U[v] + i1) : u0[v];
-        best = fminf(best, cell_bound(a, i0, u0));
-        if (two) best = fminf(best, cell_bound(a, i1, u1));
+        int x0, y0, z0, x1, y1, z1;
+        cell_xyz(i0, a, fx, fy, x0, y0, z0);
+        best = fminf(best, cell_bound(a, x0, y0, z0, u0));
+        if (two) {
+            cell_xyz(i1, a, fx, fy, x1, y1, z1);
+            best = fminf(best, cell_bound(a, x1, y1, z1, u1));
+        }
     }
     best = block_min_f(best);
     __shared__ bool last;

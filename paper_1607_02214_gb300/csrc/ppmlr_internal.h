@@ -128,6 +128,10 @@ struct CflArgs {
     long long bd_vs;
     const double *iw[3];       // contracted FP64 form: ghost-extended reciprocal widths, or null
     const unsigned char *inner_mask;   // per cell: 1 inside the inner sphere, or null
+    // FP64 forms, two-pass step (null: one pass): per cell the float screen
+    // bound written by the first pass, and the threshold it leaves (device)
+    float *screen;
+    float *screen_thr;
 };
 
 // Ionosphere shell (ionosphere.cu).  Static per cap node: the trilinear cell
