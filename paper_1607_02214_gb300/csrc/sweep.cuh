@@ -540,6 +540,58 @@ __device__ __forceinline__ int stage_index(int l, int ps, int NP, int L)
 template <int DIR>
 __device__ __forceinline__ int stage_array_stride(int NP, int L) { return DIR == 0 ? (NP + 2) * L : NP * L; }
 
+// ---- TMA staging (y and z sweeps) -------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// Bounded wait on the mbarrier phase (at most `polls` try_wait polls); false
+// if it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int polls = 1 << 22)
+{
+    for (int it = 0; it < polls; it++) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// After a bounded wait gave up: one more bounded wait on each buffer that still
+// has a box copy in flight, so that the block, when it returns, does not
+// leave the copy engine writing into shared memory it no longer owns.  If a
+// copy still has not landed after this second wait the block returns anyway
+// (FLAG_TIMEOUT is already raised and the status reports it).
+__device__ __forceinline__ void mbar_drain(unsigned long long *bar, unsigned parity)
+{
+    (void)mbar_wait(bar, parity);
+}
+
+// One 4D box (x, y, z, variable) of the state into shared memory.
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // One tile of one sweep, processed by the calling block.  `a` describes the
 // domain (the single-domain kernel passes its launch argument, the ensemble
 // kernel a per-instance copy in shared memory); `tile` is the tile index
@@ -549,9 +601,14 @@ __device__ __forceinline__ int stage_array_stride(int NP, int L) { return DIR ==
 // `stage` (optional): this tile's input box staged in shared memory by TMA,
 // 8 arrays of NP * L doubles in the tile's slot order (position p of lane l
 // at the slot of (p, l)); cells outside the box come from global memory.
+// `stage_bar` (optional): the mbarrier (phase 0) that completes when the box
+// has landed; the tile loads its geometry and evaluates the dipole while the
+// copy is in flight, then waits (bounded: on giving up it raises
+// FLAG_TIMEOUT, waits once more for the copy and returns).
 template <int DIR, typename R, bool EX, typename ARGS>
 __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned char *smem_raw, const int flip,
-                                           const double *__restrict__ stage = nullptr)
+                                           const double *__restrict__ stage = nullptr,
+                                           unsigned long long *stage_bar = nullptr)
 {
     // input and output state (flip = 1 exchanges them); array v at base + v * vs
     const double *Uin = flip ? a.Un : a.U;
@@ -618,6 +675,8 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     R dtm_k = 0;               // contracted forms: dt / dm (P1 or P4 -> P6)
     bool floored = false;
     const bool out_cell = act && p >= GH && p < GH + Ce;
+    float dxf = 0.0f;          // mixed path: the cell width
+    // geometry and dipole first: they do not depend on the staged box
     if (act && F64) {
         dx = a.w[CHK(g + GH, NG)];
         pos[0] = a.cx[CHK((DIR == 0 ? g : ix) + GH, NG0)];
@@ -631,6 +690,21 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         } else {
             dipole<EX>(a.M, pos[0], pos[1], pos[2], Bdg);
         }
+    } else if (act) {
+        dxf = a.wf[CHK(g + GH, NG)];
+        const float px = a.cxf[CHK((DIR == 0 ? g : ix) + GH, NG0)];
+        const float py = a.cyf[CHK((DIR == 1 ? g : iy) + GH, NG1)];
+        const float pz = a.czf[CHK((DIR == 2 ? g : iz) + GH, NG2)];
+        float Bdf[3];
+        dipole_f(a.Mf, px, py, pz, Bdf);
+        Bd0 = Bdf[DIR]; Bd1 = Bdf[T1]; Bd2 = Bdf[T2];
+    }
+    if (stage_bar && !mbar_wait(stage_bar, 0u)) {     // every thread of the block waits
+        if (threadIdx.x == 0) atomicOr(a.flags, FLAG_TIMEOUT);
+        mbar_drain(stage_bar, 0u);
+        return;
+    }
+    if (act && F64) {
         double Uc[8];
         int src = g;
         bool fixed = false;
@@ -690,13 +764,6 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     } else if (act) {
         // mixed path: float geometry, float dipole, integer double->float
         // splits and a double-float pressure recovery (no FP64 instructions)
-        const float dxf = a.wf[CHK(g + GH, NG)];
-        const float px = a.cxf[CHK((DIR == 0 ? g : ix) + GH, NG0)];
-        const float py = a.cyf[CHK((DIR == 1 ? g : iy) + GH, NG1)];
-        const float pz = a.czf[CHK((DIR == 2 ? g : iz) + GH, NG2)];
-        float Bdf[3];
-        dipole_f(a.Mf, px, py, pz, Bdf);
-        Bd0 = Bdf[DIR]; Bd1 = Bdf[T1]; Bd2 = Bdf[T2];
         int src = g;
         bool fixed = false;
         if (g < 0 || g >= a.N) {
@@ -1294,58 +1361,6 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
 #undef SM
 }
 
-// ---- TMA staging (y and z sweeps) -------------------------------------------
-__device__ __forceinline__ unsigned smem_u32(const void *p)
-{
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-// Bounded wait on the mbarrier phase (at most `polls` try_wait polls); false
-// if it gave up.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int polls = 1 << 22)
-{
-    for (int it = 0; it < polls; it++) {
-        unsigned done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-// After a bounded wait gave up: one more bounded wait on each buffer that still
-// has a box copy in flight, so that the block, when it returns, does not
-// leave the copy engine writing into shared memory it no longer owns.  If a
-// copy still has not landed after this second wait the block returns anyway
-// (FLAG_TIMEOUT is already raised and the status reports it).
-__device__ __forceinline__ void mbar_drain(unsigned long long *bar, unsigned parity)
-{
-    (void)mbar_wait(bar, parity);
-}
-
-// One 4D box (x, y, z, variable) of the state into shared memory.
-__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
-                                            unsigned long long *bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
-        : "memory");
-}
-
 template <typename R> struct MaxThreads { static constexpr int value = MAXT; };
 template <> struct MaxThreads<double> { static constexpr int value = MAXT_F64; };
 
@@ -1414,12 +1429,8 @@ __global__ void __launch_bounds__(MaxThreads<R>::value, TmaMinBlocks<R, PERSIST>
         tma_load_4d(stage0, &map, cx, cy, cz, 0, &bar[0]);
     }
     if constexpr (!PERSIST) {                            // one tile per block, no loop
-        if (!mbar_wait(&bar[0], 0u)) {
-            if (threadIdx.x == 0) atomicOr(a.flags, FLAG_TIMEOUT);
-            mbar_drain(&bar[0], 0u);
-            return;
-        }
-        sweep_tile<DIR, R, EX, const SweepArgs>(a, t, work, 0, stage0);
+        // the tile waits for the box itself, after its geometry loads
+        sweep_tile<DIR, R, EX, const SweepArgs>(a, t, work, 0, stage0, &bar[0]);
     } else {
     unsigned phase[2] = {0u, 0u};
     for (int k = 0; t < ntiles; k++, t += gridDim.x) {
@@ -1573,12 +1584,7 @@ __global__ void __launch_bounds__(MaxThreads<R>::value, EnsMinBlocks<R>::value) 
         mbar_expect_tx(&bar, (unsigned)stage_bytes);
         tma_load_4d(stage, maps + 2 * lo + e.flip, cx, cy, cz, 0, &bar);
     }
-    if (!mbar_wait(&bar, 0u)) {
-        if (threadIdx.x == 0) atomicOr(args.flags, FLAG_TIMEOUT);
-        mbar_drain(&bar, 0u);
-        return;
-    }
-    sweep_tile<DIR, R, EX, const SweepArgs>(args, tile, smem_raw + stage_pad, e.flip, stage);
+    sweep_tile<DIR, R, EX, const SweepArgs>(args, tile, smem_raw + stage_pad, e.flip, stage, &bar);
 }
 
 // Ensemble, one block per tile, arguments of all instances in the kernel

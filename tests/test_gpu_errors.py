@@ -16,11 +16,15 @@ def built():
     build.build()
 
 
-def test_nonfinite_state_reported():
+@pytest.mark.parametrize("precision", [ppmlr.PPMLR_FP64, ppmlr.PPMLR_FP64_EXACT, ppmlr.PPMLR_MIXED])
+@pytest.mark.parametrize("var,value", [(7, np.nan), (0, np.nan), (4, np.inf), (3, -np.inf)])
+def test_nonfinite_state_reported(precision, var, value):
+    # a non-finite total energy, density, normal field (B_x: the x sweep does
+    # not update it) or transverse momentum in one cell
     pr = inputs.brio_wu_3d((16, 8, 8))
     U = pr.U0.copy()
-    U[7, 3, 4, 5] = np.nan
-    g = ppmlr.Context.from_problem(pr)
+    U[var, 3, 4, 5] = value
+    g = ppmlr.Context.from_problem(pr, precision)
     g.set_state(U)
     g.step(1e-3)
     assert g.check(raise_on_error=False) == ppmlr.PPMLR_E_NONFINITE
