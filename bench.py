@@ -54,23 +54,25 @@ FLOPS_PER_CELL = {"x": 1189.1, "y": 1241.9, "z": 1243.7, "cfl": 207.0}
 BYTES_PER_CELL_SWEEP = 128      # read 8 FP64 + write 8 FP64
 # DRAM bytes per cell of one launch measured by ncu for each kernel, with the
 # sha256 prefix of the kernel source they were taken on (null once it changes).
-# The FP64 sweeps and CFL pass also read the dipole table (24 B per cell) on
-# top of the state: traffic above the algorithmic 128 / 64 B by that much; the
-# FP64 y and z sweeps (72-register cap) add ~30 B per cell of spill traffic.
+# The FP64 sweeps also read the dipole table (24 B per cell) on top of the
+# state: traffic above the algorithmic 128 B by that much; the FP64 y and z
+# sweeps (72-register cap) add ~30 B per cell of spill traffic.  The FP64 CFL
+# step's screen writes 4 B per cell that its FP64 pass reads back.
 NCU_TRAFFIC = {
-    "fp64:x": {"bytes_per_cell": 149.4, "src": "267daf6257502b94"},
-    "fp64:y": {"bytes_per_cell": 179.9, "src": "267daf6257502b94"},
-    "fp64:z": {"bytes_per_cell": 176.7, "src": "267daf6257502b94"},
-    "fp64:cfl": {"bytes_per_cell": 89.3, "src": "a2d3f854bdcc55de"},
-    "mixed:x": {"bytes_per_cell": 123.5, "src": "470d4f77700d50d1"},
-    "mixed:y": {"bytes_per_cell": 124.5, "src": "470d4f77700d50d1"},
-    "mixed:z": {"bytes_per_cell": 124.9, "src": "470d4f77700d50d1"},
-    "mixed:cfl": {"bytes_per_cell": 64.3, "src": "76a9917a27ea1e90"},
+    "fp64:x": {"bytes_per_cell": 149.6, "src": "7a4cf7a35d45c865"},
+    "fp64:y": {"bytes_per_cell": 181.8, "src": "7a4cf7a35d45c865"},
+    "fp64:z": {"bytes_per_cell": 177.5, "src": "7a4cf7a35d45c865"},
+    # the two passes of the FP64 CFL step together (float screen 68.6, FP64 pass 4.0)
+    "fp64:cfl": {"bytes_per_cell": 72.6, "src": "c1895d5d362f9eaa"},
+    "mixed:x": {"bytes_per_cell": 123.6, "src": "b6ec5325f5e04110"},
+    "mixed:y": {"bytes_per_cell": 124.6, "src": "b6ec5325f5e04110"},
+    "mixed:z": {"bytes_per_cell": 124.9, "src": "b6ec5325f5e04110"},
+    "mixed:cfl": {"bytes_per_cell": 64.3, "src": "03374d4cc320bd48"},
     # ensemble sweeps: captured on the first 8 of the 48 instances (14.9 M
     # cells; the full ensemble holds ~10 GB), scaled by cells
-    "ensemble:x": {"bytes_per_cell": 125.1, "src": "88331d354fe572c5"},
-    "ensemble:y": {"bytes_per_cell": 125.4, "src": "88331d354fe572c5"},
-    "ensemble:z": {"bytes_per_cell": 125.5, "src": "88331d354fe572c5"},
+    "ensemble:x": {"bytes_per_cell": 125.2, "src": "43362ffc6ac7402e"},
+    "ensemble:y": {"bytes_per_cell": 125.5, "src": "43362ffc6ac7402e"},
+    "ensemble:z": {"bytes_per_cell": 125.6, "src": "43362ffc6ac7402e"},
 }
 
 
@@ -81,8 +83,8 @@ KERNEL_SOURCES = {
     "fp64:sweep": _SWEEP + ("sweep_fp64.cu",),
     "mixed:sweep": _SWEEP + ("sweep_mixed.cu",),
     "ensemble:sweep": _SWEEP + ("sweep_mixed.cu", "ensemble.cu"),
-    "fp64:cfl": ("cfl.cuh", "cfl_fp64.cu", "ppmlr_internal.h"),
-    "mixed:cfl": ("cfl_mixed.cu", "sweep.cuh", "mixed_util.cuh", "ppmlr_internal.h"),
+    "fp64:cfl": ("cfl.cuh", "cfl_fp64.cu", "sweep.cuh", "mixed_util.cuh", "ppmlr_internal.h"),
+    "mixed:cfl": ("cfl_mixed.cu", "cfl.cuh", "sweep.cuh", "mixed_util.cuh", "ppmlr_internal.h"),
 }
 
 
@@ -413,12 +415,16 @@ def run_ours(args, rank, world, dist):
         ach = BYTES_PER_CELL_SWEEP * cells / (avg_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "traffic": traffic, "kernel": f"sweep_{dom}", "avg_launch_ms": avg_ms, "peak_source": hbm_src}
+    # algorithmic bytes: 128 B per cell for a sweep, 64 B (the state read) for the CFL step
     per_kernel = {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1],
-                      "hbm_frac_of_measured": BYTES_PER_CELL_SWEEP * cells / (v[0] / max(v[1], 1) * 1e-3) / 1e9 / hbm
-                      if k != "cfl" else None} for k, v in kern.items()}
+                      "hbm_frac_of_measured": (BYTES_PER_CELL_SWEEP if k != "cfl" else 64) * cells
+                      / (v[0] / max(v[1], 1) * 1e-3) / 1e9 / hbm} for k, v in kern.items()}
     if args.precision == "fp64":
         for k, v in per_kernel.items():
-            v["fp64_frac_of_measured"] = FLOPS_PER_CELL[k] * cells / (v["avg_ms"] * 1e-3) / 1e9 / fp64_peak
+            if k == "cfl":      # two passes: a float screen, FP64 only for the cells near the minimum
+                v["note"] = "float screen of every cell, FP64 only near the minimum: an HBM-bound pass"
+            else:
+                v["fp64_frac_of_measured"] = FLOPS_PER_CELL[k] * cells / (v["avg_ms"] * 1e-3) / 1e9 / fp64_peak
 
     # ---- the other precision, and its error against the FP64 path
     extra = {}
@@ -768,7 +774,7 @@ def run_large(args, barrier, fp64_peak):
             avg = tot / max(n, 1)
             byts = (BYTES_PER_CELL_SWEEP if k != "cfl" else 64) * cells
             per[k] = {"avg_ms": avg, "hbm_frac_of_measured": byts / (avg * 1e-3) / 1e9 / hbm}
-            if name == "fp64":
+            if name == "fp64" and k != "cfl":     # (the FP64 CFL step is a float screen plus a few cells)
                 per[k]["fp64_gflops"] = FLOPS_PER_CELL[k] * cells / (avg * 1e-3) / 1e9
                 per[k]["fp64_frac_of_measured"] = per[k]["fp64_gflops"] / fp64_peak
         out[name] = {"value": cells * steps / (ms * 1e-3), "ms_per_step": ms / steps, "steps": steps,
