@@ -244,6 +244,25 @@ def config_dict(prob, name, args, world):
 
 # ------------------------------------------------------------ reference -------
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
 def oracle_sample(prob, steps, threads=0, keep=False):
     """Time the oracle on the host cores: `steps` steps of prob with its CFL dt.
     keep: also return the time steps and the final state."""
@@ -573,8 +592,11 @@ def run_ours(args, rank, world, dist):
         r_small, _, _ = oracle_sample(small, 1)
         steps = max(1, min(3, int(20.0 * r_small / cells)))
         rate, t, cores, dts, Uo = oracle_sample(prob, steps, keep=True)
+        rate1, t1, _ = oracle_sample(prob, 1, threads=1)       # the same code on one core
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{steps} full step(s) of {name}, OpenMP over pencils, {t:.1f} s"}
+               "sample": f"{steps} full step(s) of {name}, OpenMP over pencils, {t:.1f} s",
+               "single_core": {"value": rate1, "sample": f"1 full step on 1 thread, {t1:.1f} s"},
+               "cpu_model": cpu_model()}
         # the GPU paths replayed with the oracle's time steps: their error
         # against the oracle on the full workload
         acc = {"steps": steps}
