@@ -396,9 +396,11 @@ ppmlr_status ppmlr_ensemble_time_kernels(ppmlr_ens *ens, double cfl, int nsteps,
  * table; 2: one block per tile, arguments of all instances in the kernel
  * parameter, up to 64 instances; 3: one block per tile with the input box
  * staged by TMA; 4: persistent blocks taking tiles from a work counter,
- * arguments of all instances in the kernel parameter, up to 64 instances),
- * timed out of place; a persistent form (0 or 4) is kept when it is within
- * 2 % of the fastest; best_ms: 3 entries or NULL. */
+ * arguments of all instances in the kernel parameter, up to 64 instances;
+ * 5: one block per tile with the input box staged by TMA and the arguments
+ * of all instances in the kernel parameter, up to 64 instances), timed out
+ * of place; a persistent form (0 or 4) is kept when it is within 2 % of the
+ * fastest; best_ms: 3 entries or NULL. */
 ppmlr_status ppmlr_ensemble_autotune(ppmlr_ens *ens, double *best_ms);
 /* Fix the launch of one sweep direction instead of autotuning it: form 0 =
  * persistent blocks taking tiles from a work counter, 1 = one block per tile
@@ -409,7 +411,9 @@ ppmlr_status ppmlr_ensemble_autotune(ppmlr_ens *ens, double *best_ms);
  * 256 positions per tile; along x also C even and ny a multiple of the
  * lanes), 4 = persistent blocks taking tiles from a work counter with the
  * arguments of all instances in the kernel parameter (at most 64
- * instances); budget = positions x lanes per
+ * instances), 5 = one block per tile with the box staged as in form 3 and
+ * the arguments of all instances in the kernel parameter (the conditions of
+ * form 3; at most 64 instances); budget = positions x lanes per
  * tile (15..448 for the FP64 forms, ..512 for PPMLR_MIXED).  Tiles: whole
  * pencils when they fit (else equal chunks), then as many lanes as fit; for
  * y and z, budget + 10000 selects the other rule: the most lanes (a power of

@@ -53,8 +53,10 @@ struct ppmlr_ens {
     int mode[3];                 // 0: persistent work queue, 1: one block per tile (table),
                                  // 2: one block per tile (arguments in the kernel parameter),
                                  // 3: one block per tile, input box staged by TMA (y, z),
-                                 // 4: persistent work queue, arguments in the kernel parameter
-    CUtensorMap *d_maps[3];      // mode 3: per instance the maps of its two state sets
+                                 // 4: persistent work queue, arguments in the kernel parameter,
+                                 // 5: one block per tile, input box staged by TMA, arguments in
+                                 //    the kernel parameter
+    CUtensorMap *d_maps[3];      // modes 3, 5: per instance the maps of its two state sets
     std::vector<SweepArgs> host_args[3];
     std::vector<Tile> tiles[3];
     // CFL tables for states in A and in B
@@ -124,7 +126,8 @@ static void pick_tile(const int *n, int d, int maxt, bool lanes_first, int &C, i
 
 static bool plan_direction(ppmlr_ens *e, int d, int maxt, int mode, bool lanes_first = false)
 {
-    if (mode == 3) {     // TMA staging: every instance's box within the copy engine's rules
+    if ((mode == 2 || mode == 4 || mode == 5) && e->count > ENS_PARAM_MAX) return false;
+    if (mode == 3 || mode == 5) {     // TMA staging: every instance's box within the copy engine's rules
         if (!tensor_map_encoder()) return false;
         size_t sm = 0;
         int thr = 32;
@@ -139,7 +142,9 @@ static bool plan_direction(ppmlr_ens *e, int d, int maxt, int mode, bool lanes_f
             sm = std::max(sm, stage_pad_bytes(t, d) + t.smem);
             thr = std::max(thr, t.threads);
         }
-        if (sm > 224 * 1024 || sweep_launchers(e->prec).ens_tma_per_sm(d, thr, sm) < 1) return false;
+        const int fit = mode == 5 ? sweep_launchers(e->prec).ens_tma_param_per_sm(d, thr, sm)
+                                  : sweep_launchers(e->prec).ens_tma_per_sm(d, thr, sm);
+        if (sm > 224 * 1024 || fit < 1) return false;
     }
     e->maxt[d] = maxt;
     e->mode[d] = mode;
@@ -155,14 +160,13 @@ static bool plan_direction(ppmlr_ens *e, int d, int maxt, int mode, bool lanes_f
         Tile t = make_tile(d, n, real_size(e), C, L);
         e->tiles[d].push_back(t);
         if (t.threads > thr) thr = t.threads;
-        const size_t need = mode == 3 ? stage_pad_bytes(t, d) + t.smem : t.smem;
+        const size_t need = mode == 3 || mode == 5 ? stage_pad_bytes(t, d) + t.smem : t.smem;
         if (need > sm) sm = need;
         total += t.ntiles;
     }
     e->threads[d] = thr;
     e->smem[d] = sm;
     e->total_tiles[d] = total;
-    if (mode == 4 && e->count > ENS_PARAM_MAX) return false;
     const bool persist = mode == 0 || mode == 4;
     int per_sm = mode == 4 ? sweep_launchers(e->prec).param_persist_per_sm(d, thr, sm)
                            : sweep_launchers(e->prec).per_sm(d, thr, sm);
@@ -247,7 +251,7 @@ static ppmlr_status upload_direction(ppmlr_ens *e, int d)
         acc += t.ntiles;
     }
     e->host_args[d] = args;
-    if (e->mode[d] == 3) {
+    if (e->mode[d] == 3 || e->mode[d] == 5) {
         ppmlr_status st = upload_maps(e, d);
         if (st != PPMLR_OK) return st;
     }
@@ -263,7 +267,7 @@ static ppmlr_status upload_direction(ppmlr_ens *e, int d)
 static cudaError_t launch_dir(ppmlr_ens *e, int d, int flip, unsigned int *queue, cudaStream_t s)
 {
     const SweepLaunchers &L = sweep_launchers(e->prec);
-    if (e->mode[d] == 2 || e->mode[d] == 4) {
+    if (e->mode[d] == 2 || e->mode[d] == 4 || e->mode[d] == 5) {
         EnsSweepParams p;
         memset(&p, 0, sizeof(p));
         for (int i = 0; i < e->count; i++) p.args[i] = e->host_args[d][i];
@@ -273,6 +277,7 @@ static cudaError_t launch_dir(ppmlr_ens *e, int d, int flip, unsigned int *queue
         p.flip = flip;
         p.total_tiles = acc;
         if (e->mode[d] == 4) return L.param_persist(d, p, queue, e->blocks[d], e->threads[d], e->smem[d], s);
+        if (e->mode[d] == 5) return L.ens_tma_param(d, p, e->d_maps[d], e->blocks[d], e->threads[d], e->smem[d], s);
         return L.param(d, p, e->blocks[d], e->threads[d], e->smem[d], s);
     }
     EnsSweepArgs ea{e->d_args[d], e->d_first_tile[d], e->count, e->total_tiles[d], flip, queue};
@@ -616,9 +621,10 @@ ppmlr_status ppmlr_ensemble_autotune(ppmlr_ens *e, double *best_ms)
         const int rules = d == 0 ? 1 : 2;
         // per candidate (budget, form, tile rule) the time of two sweeps
         std::vector<std::tuple<float, int, int, int>> timed;
-        for (int k = 0; k < 5 * nc * rules; k++) {
-            const int mode = (k / nc) % 5, rule = k / (5 * nc);
-            if ((mode == 2 || mode == 4) && e->count > ENS_PARAM_MAX) continue;
+        constexpr int NF = 6;           // launch forms 0..5
+        for (int k = 0; k < NF * nc * rules; k++) {
+            const int mode = (k / nc) % NF, rule = k / (NF * nc);
+            if ((mode == 2 || mode == 4 || mode == 5) && e->count > ENS_PARAM_MAX) continue;
             if (!plan_direction(e, d, cands[k % nc], mode, rule == 1)) continue;
             ppmlr_status st = upload_direction(e, d);
             if (st != PPMLR_OK) return st;
@@ -719,11 +725,11 @@ ppmlr_status ppmlr_ensemble_set_launch(ppmlr_ens *e, int axis, int form, int bud
     const int maxb = e->prec == PPMLR_MIXED ? MAXT : MAXT_F64;
     const bool lanes_first = budget >= 10000;
     if (lanes_first) budget -= 10000;
-    if (axis < 0 || axis > 2 || form < 0 || form > 4 || budget < 2 * GH + 1 || budget > maxb ||
+    if (axis < 0 || axis > 2 || form < 0 || form > 5 || budget < 2 * GH + 1 || budget > maxb ||
         (lanes_first && axis == 0))
         return efail(e, PPMLR_E_INVALID, "set_launch: bad axis, form or budget");
-    if ((form == 2 || form == 4) && e->count > ENS_PARAM_MAX)
-        return efail(e, PPMLR_E_INVALID, "set_launch: forms 2 and 4 take at most 64 instances");
+    if ((form == 2 || form == 4 || form == 5) && e->count > ENS_PARAM_MAX)
+        return efail(e, PPMLR_E_INVALID, "set_launch: forms 2, 4 and 5 take at most 64 instances");
     if (!plan_direction(e, axis, budget, form, lanes_first))
         return efail(e, PPMLR_E_INVALID, "set_launch: the TMA form does not fit every instance along this axis");
     ppmlr_status st = upload_direction(e, axis);

@@ -181,6 +181,50 @@ struct SweepVariant {
         return dir == 0 ? ens_tma_per_sm_dir<0>(threads, smem)
                : dir == 1 ? ens_tma_per_sm_dir<1>(threads, smem) : ens_tma_per_sm_dir<2>(threads, smem);
     }
+    // ensemble, one block per tile, TMA-staged box, arguments in the kernel parameter
+    template <int DIR>
+    static cudaError_t allow_ens_tma_param_smem()
+    {
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, sweep_ensemble_tma_param_kernel<DIR, R, EX>);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(sweep_ensemble_tma_param_kernel<DIR, R, EX>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - (int)fa.sharedSizeBytes);
+    }
+    template <int DIR>
+    static cudaError_t ens_tma_param_dir(const EnsSweepParams &p, const CUtensorMap *maps, int blocks, int threads,
+                                         size_t smem, cudaStream_t s)
+    {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t r = allow_ens_tma_param_smem<DIR>();
+            if (r != cudaSuccess) return r;
+            attr = true;
+        }
+        sweep_ensemble_tma_param_kernel<DIR, R, EX><<<blocks, threads, smem, s>>>(p, maps);
+        return cudaGetLastError();
+    }
+    static cudaError_t ens_tma_param(int dir, const EnsSweepParams &p, const CUtensorMap *maps, int blocks,
+                                     int threads, size_t smem, cudaStream_t s)
+    {
+        return dir == 0 ? ens_tma_param_dir<0>(p, maps, blocks, threads, smem, s)
+               : dir == 1 ? ens_tma_param_dir<1>(p, maps, blocks, threads, smem, s)
+                          : ens_tma_param_dir<2>(p, maps, blocks, threads, smem, s);
+    }
+    template <int DIR>
+    static int ens_tma_param_per_sm_dir(int threads, size_t smem)
+    {
+        if (allow_ens_tma_param_smem<DIR>() != cudaSuccess) return 0;
+        int n = 0;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_ensemble_tma_param_kernel<DIR, R, EX>,
+                                                             threads, smem) == cudaSuccess ? n : 0;
+    }
+    static int ens_tma_param_per_sm(int dir, int threads, size_t smem)
+    {
+        if (threads > MaxThreads<R>::value) return 0;
+        return dir == 0 ? ens_tma_param_per_sm_dir<0>(threads, smem)
+               : dir == 1 ? ens_tma_param_per_sm_dir<1>(threads, smem) : ens_tma_param_per_sm_dir<2>(threads, smem);
+    }
     static cudaError_t dipole_table(double M, const int n[3], const double *cx, const double *cy, const double *cz,
                                     double *bd, long long vs, cudaStream_t s)
     {
@@ -241,7 +285,7 @@ struct SweepVariant {
     {
         return {single, ens, param, per_sm, tma, tma_per_sm,
                 std::is_same<R, double>::value ? &dipole_table : nullptr, ens_tma, ens_tma_per_sm,
-                param_persist, param_persist_per_sm, march};
+                param_persist, param_persist_per_sm, ens_tma_param, ens_tma_param_per_sm, march};
     }
 };
 

@@ -215,6 +215,11 @@ struct SweepLaunchers {
     cudaError_t (*param_persist)(int dir, const EnsSweepParams &p, unsigned int *queue, int blocks, int threads,
                                  size_t smem, cudaStream_t s);
     int (*param_persist_per_sm)(int dir, int threads, size_t smem);
+    // ensemble, one block per tile, input box staged by TMA, all instances'
+    // arguments in the kernel parameter
+    cudaError_t (*ens_tma_param)(int dir, const EnsSweepParams &p, const CUtensorMap *maps, int blocks,
+                                 int threads, size_t smem, cudaStream_t s);
+    int (*ens_tma_param_per_sm)(int dir, int threads, size_t smem);
     // marching form (one thread per pencil; PPMLR_MIXED only, else cudaErrorNotSupported):
     // `a` carries the chunk length C, nchunk and the lane groups ngx (of 32)
     cudaError_t (*march)(int dir, const SweepArgs &a, cudaStream_t s);

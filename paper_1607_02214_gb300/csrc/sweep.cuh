@@ -1587,6 +1587,40 @@ __global__ void __launch_bounds__(MaxThreads<R>::value, EnsMinBlocks<R>::value) 
     sweep_tile<DIR, R, EX, const SweepArgs>(args, tile, smem_raw + stage_pad, e.flip, stage, &bar);
 }
 
+// Ensemble, one block per tile with the tile's input box staged by TMA and
+// every instance's arguments in the kernel parameter (constant bank): the
+// block finds its instance by a search in the parameter space, thread 0
+// issues the box copy at once, and the tile loads its geometry while the copy
+// is in flight (no per-block copy of the arguments, no device-table search).
+template <int DIR, typename R, bool EX>
+__global__ void __launch_bounds__(MaxThreads<R>::value, EnsMinBlocks<R>::value)
+    sweep_ensemble_tma_param_kernel(const __grid_constant__ EnsSweepParams p, const CUtensorMap *maps)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long bar;
+    const int t = blockIdx.x;
+    int lo = 0, hi = p.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.first_tile[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const SweepArgs &a = p.args[lo];
+    const int tile = t - p.first_tile[lo];
+    const size_t stage_bytes = (size_t)8 * stage_array_stride<DIR>(a.NP, a.L) * sizeof(double);
+    const size_t stage_pad = (stage_bytes + 1023) / 1024 * 1024;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        int cx, cy, cz;
+        tile_box_origin<DIR>(a, tile, cx, cy, cz);
+        mbar_expect_tx(&bar, (unsigned)stage_bytes);
+        tma_load_4d(smem_raw, maps + 2 * lo + p.flip, cx, cy, cz, 0, &bar);
+    }
+    __syncthreads();                           // the mbarrier is initialised before anyone waits on it
+    sweep_tile<DIR, R, EX, const SweepArgs>(a, tile, smem_raw + stage_pad, p.flip,
+                                            reinterpret_cast<const double *>(smem_raw), &bar);
+}
+
 // Ensemble, one block per tile, arguments of all instances in the kernel
 // parameter (constant bank): the block finds its instance from the first-tile
 // table and reads that instance's fields straight from the parameter space.

@@ -107,14 +107,16 @@ def test_autotune_changes_speed_not_results(precision):
 
 
 @pytest.mark.parametrize("precision", [ppmlr.PPMLR_FP64_EXACT, ppmlr.PPMLR_FP64, ppmlr.PPMLR_MIXED])
-def test_ensemble_tma_form_matches_the_other_forms(precision):
+@pytest.mark.parametrize("form", [3, 5])
+def test_ensemble_tma_form_matches_the_other_forms(precision, form):
+    # form 3: arguments from the device table; form 5: from the kernel parameter
     probs = small_ensemble(5)
     a = ppmlr.Ensemble(probs, precision=precision)
     b = ppmlr.Ensemble(probs, precision=precision)
-    b.set_launch(0, 3, 124)                          # 2 pencils per x tile: divides every ny
+    b.set_launch(0, form, 124)                       # 2 pencils per x tile: divides every ny
     for axis in (1, 2):
-        b.set_launch(axis, 3, 256)                   # TMA-staged boxes, per-instance tensor maps
-    assert [t // 1000 for t in b.tiles()] == [3, 3, 3]
+        b.set_launch(axis, form, 256)                # TMA-staged boxes, per-instance tensor maps
+    assert [t // 1000 for t in b.tiles()] == [form] * 3
     for i, p in enumerate(probs):
         a.set_state(i, p.U0)
         b.set_state(i, p.U0)
@@ -128,9 +130,9 @@ def test_ensemble_tma_form_matches_the_other_forms(precision):
             tol = 1e-12 if precision == ppmlr.PPMLR_FP64 else 1e-6
             assert np.max(rel_l1(b.get_state(i), a.get_state(i))) <= tol, i
     odd = ppmlr.Ensemble([inputs.magnetosphere(n=(41, 30, 30), h0=1.0)], precision=precision)
-    assert odd.set_launch(1, 3, 256, raise_on_error=False) == ppmlr.PPMLR_E_INVALID  # nx odd
+    assert odd.set_launch(1, form, 256, raise_on_error=False) == ppmlr.PPMLR_E_INVALID  # nx odd
     skew = ppmlr.Ensemble([inputs.magnetosphere(n=(40, 30, 30), h0=1.0)], precision=precision)
-    assert skew.set_launch(0, 3, 216, raise_on_error=False) == ppmlr.PPMLR_E_INVALID  # 4 lanes do not divide ny
+    assert skew.set_launch(0, form, 216, raise_on_error=False) == ppmlr.PPMLR_E_INVALID  # 4 lanes do not divide ny
 
 
 @pytest.mark.parametrize("precision", [ppmlr.PPMLR_FP64_EXACT, ppmlr.PPMLR_FP64, ppmlr.PPMLR_MIXED])
@@ -159,12 +161,12 @@ def test_ensemble_persistent_parameter_form_matches_the_other_forms(precision):
     assert a.diagnostics()["floor_hits"] == b.diagnostics()["floor_hits"]
     many = ppmlr.Ensemble([inputs.magnetosphere(n=(24, 20, 20), h0=2.0, x_ext=(-30, 20), yz_ext=(-25, 25),
                                                 name=f"t{i}") for i in range(65)], precision=precision)
-    for form in (2, 4):                              # the kernel parameter holds at most 64 instances
+    for form in (2, 4, 5):                           # the kernel parameter holds at most 64 instances
         assert many.set_launch(1, form, 256, raise_on_error=False) == ppmlr.PPMLR_E_INVALID
 
 
 @pytest.mark.parametrize("precision", [ppmlr.PPMLR_FP64_EXACT, ppmlr.PPMLR_MIXED])
-@pytest.mark.parametrize("form", [0, 3, 4])
+@pytest.mark.parametrize("form", [0, 3, 4, 5])
 def test_ensemble_lanes_first_tiles_match_whole_pencil_tiles(precision, form):
     """The y/z lanes-first rule (budget + 10000: chunked pencils, more lanes)
     gives the whole-pencil rule's results (bit for bit on the exact path)."""
