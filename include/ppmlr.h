@@ -134,7 +134,12 @@ ppmlr_status ppmlr_set_layers(ppmlr_ctx *ctx, int k0, int nk, const double *cons
  *   dt = cfl * min over non-inner interior cells and axes d of
  *        dx_d / (|v_d| + max(c_f,d(B'), c_f,d(B' + B_d))).
  * Computed on the device by a block-min reduction (no float atomics) and
- * copied to *dt_out (synchronises).  The value also stays on the device for
+ * copied to *dt_out (synchronises).  The FP64 forms take two passes: a float
+ * screen bounds every cell, then the form's own FP64 expressions evaluate
+ * only the cells within 1 % of the smallest float bound (and any whose float
+ * bound is not a positive finite number), which always include the cell of
+ * the minimum: the same dt bit for bit as one FP64 pass over every cell, at
+ * the cost of a float pass.  The value also stays on the device for
  * ppmlr_step_cfl.  Reports pending device flags. */
 ppmlr_status ppmlr_cfl_dt(ppmlr_ctx *ctx, double cfl, double *dt_out);
 
