@@ -125,26 +125,61 @@ __device__ __forceinline__ bool lt0(R x)
     else return x < R(0);
 }
 
-// Square root of a non-negative value.  Contracted FP64 form: from the
-// hardware's approximate reciprocal square root y (~2^-20), s = x y is
-// refined by one step of Householder's third-order iteration,
-// sqrt(x) = s (1 - e)^(-1/2) ~ s (1 + e/2 + 3 e^2/8) with e = 1 - s y
-// (five FP64 instructions; the error falls to ~2.5 |e/2|^3 ~ 2^-59, so the
-// result is within an ulp of the correctly rounded root -- measured on GB300
-// over 2^26 arguments spanning 2^-1000..2^1000 -- which costs the GB300's
-// FP64 pipe ~8.6 slots); zero for x = 0 and, as x is a
-// sum of squares or a density here, for subnormal x; otherwise the library
-// square root.
+// Correctly rounded square root of a positive normal double with no FP64
+// instruction (integer and FP32 pipes; the GB300's FP64 pipe would spend
+// ~8.6 slots on it).  With x = m 2^(e-52), m the 53-bit significand, made
+// m in [2^52, 2^54) with e even: sqrt(x) = sqrt(N) 2^(e/2 - 52), N = m 2^52,
+// and the significand of the result is R = round(sqrt(N)) in [2^52, 2^53).
+//  1. sqrt(m / 2^30) = sqrt(xh + xl) as a float pair h + l: xh = m >> 30
+//     exact, h the correctly rounded float root, l = (xh - h^2 + xl) / (2h)
+//     with the residual xh - h^2 exact by one fused multiply-add; R1 =
+//     (h + l) 2^41 is within ~2^8.3 of sqrt(N) (the series' next term
+//     (xh - h^2 + xl)^2 / (8 h^3) < 2^-34 and the float roundings of l).
+//  2. One Newton step on the exact integer remainder: R2 = R1 +
+//     round((N - R1^2) / (2 R1)) (N - R1^2 from a 128-bit square), within
+//     one of sqrt(N).
+//  3. R = R2 + k, k in {-1, 0, 1}, such that -R < N - R^2 <= R (round to
+//     nearest; sqrt(N) of an integer N is never a half-integer, so there
+//     are no ties).
+__device__ __forceinline__ double sqrt_int(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    int e = (int)(b >> 52) - 1023;
+    unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+    if (e & 1) { m <<= 1; e -= 1; }
+    // 1. float-pair seed
+    const float xh = (float)(unsigned)(m >> 30);                  // < 2^24: exact
+    const float xl = (float)(unsigned)(m & 0x3FFFFFFFull) * 0x1p-30f;
+    const float h = __fsqrt_rn(xh);
+    const float l = (fmaf(-h, h, xh) + xl) * (0.5f * __frcp_rn(h));
+    const unsigned hb = __float_as_uint(h);                         // h in [2^11, 2^12]
+    const long long Rh = (long long)((hb & 0x7FFFFFu) | 0x800000u) << ((int)(hb >> 23) - 127 + 18);
+    long long R = Rh + (long long)__float2int_rn(l * 0x1p41f);       // |l 2^41| < 2^30
+    // 2. Newton step on the exact remainder N - R^2: |N - R^2| < 2^63 (R is
+    //    within ~2^8.3 of sqrt(N)), so its low 64 bits are the value
+    const unsigned long long ur = (unsigned long long)R;
+    long long d = (long long)((m << 52) - ur * ur);
+    const long long k = (long long)__float2int_rn((float)(int)(d >> 32) * __fdividef(0x1p-10f, h));
+    d -= k * (2 * R + k);                                           // N - (R + k)^2
+    R += k;
+    // 3. round to nearest
+    if (d > R) { d -= 2 * R + 1; R += 1; }
+    else if (d <= -R) { d += 2 * R - 1; R -= 1; }
+    return __longlong_as_double((long long)(((unsigned long long)((e >> 1) + 1022) << 52) + (unsigned long long)R));
+}
+
+// Square root of a non-negative value.  Contracted FP64 form: sqrt_int
+// (correctly rounded, no FP64 instruction); zero for x = 0, for a negative x
+// (a rounded discriminant) and, as x is a sum of squares or a density here,
+// for subnormal x; +inf and NaN pass through, so a non-finite state stays
+// non-finite.  Otherwise the library square root.
 template <typename R, bool EX>
 __device__ __forceinline__ R fsqrt(R x)
 {
     if constexpr (!EX && std::is_same<R, double>::value) {
-        double y;
-        asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-        const double s = x * y;
-        const double e = fma(-s, y, 1.0);
-        const double r = fma(s * e, fma(e, 0.375, 0.5), s);
-        return __double_as_longlong(x) >= 0x0010000000000000LL ? r : 0.0;   // the smallest normal double
+        const long long b = __double_as_longlong(x);
+        if (b >= 0x7FF0000000000000LL) return x;                      // +inf, NaN
+        return b >= 0x0010000000000000LL ? sqrt_int(x) : 0.0;         // the smallest normal double
     } else {
         return K<R>::sq(x);
     }

@@ -10,31 +10,45 @@ namespace {
 
 // Error, in ulps of the correctly rounded result, of this form's square root
 // and reciprocal over n arguments x = (1 + f) 2^e, e cycling over
-// -1000..1000 and f from a Weyl sequence: out[0] square root, out[1]
-// reciprocal (non-negative doubles compared as their bit patterns).
+// -1000..1000 and f from a Weyl sequence, every fourth argument an exact
+// square s^2 2^(2j) instead (s a 26-bit integer, 2j = e - 52 with e first
+// made even toward zero) moved by -3..3 units in its last place, so that
+// the root is exact or lies within a fraction of an ulp of s 2^j: out[0]
+// square root, out[1] reciprocal (non-negative doubles compared as their
+// bit patterns), out[2] the arguments whose square root differs from the
+// correctly rounded one.
 __global__ void __launch_bounds__(256) arith_selftest_kernel(long long n, unsigned long long *out)
 {
     double m_sqrt = 0.0, m_rcp = 0.0;
+    unsigned long long wrong = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int ex = (int)(i % 2001) - 1000;
         const double f = (double)(((unsigned long long)i * 0x9E3779B97F4A7C15ULL) >> 11) * 0x1.0p-53;
-        const double x = ldexp(1.0 + f, ex);
+        double x = ldexp(1.0 + f, ex);
+        if ((i & 3) == 3) {
+            const unsigned long long q = (1ull << 25) + ((((unsigned long long)i * 0x2545F4914F6CDD1DULL) >> 20) &
+                                                         ((1ull << 25) - 1));
+            const double sq = ldexp((double)(q * q), 2 * (ex / 2) - 52);     // q^2 < 2^52: exact; sq < 2^1000
+            x = __longlong_as_double(__double_as_longlong(sq) + (i % 7) - 3);
+        }
         const double s = fsqrt<double, false>(x), s_ref = sqrt(x);
         const double r = recip<double, false>(x), r_ref = 1.0 / x;
         m_sqrt = fmax(m_sqrt, fabs(s - s_ref) / ldexp(1.0, ilogb(s_ref) - 52));
         m_rcp = fmax(m_rcp, fabs(r - r_ref) / ldexp(1.0, ilogb(r_ref) - 52));
+        wrong += __double_as_longlong(s) != __double_as_longlong(s_ref);
     }
     atomicMax(out, (unsigned long long)__double_as_longlong(m_sqrt));
     atomicMax(out + 1, (unsigned long long)__double_as_longlong(m_rcp));
+    atomicAdd(out + 2, wrong);
 }
 
 }  // namespace
 }  // namespace ppmlr
 
-extern "C" ppmlr_status ppmlr_selftest_fp64_arith(void *cuda_stream, long long n, double max_ulp[2])
+extern "C" ppmlr_status ppmlr_selftest_fp64_arith(void *cuda_stream, long long n, double max_ulp[3])
 {
     if (!max_ulp || n < 1) return PPMLR_E_INVALID;
-    unsigned long long *d = nullptr, h[2] = {0, 0};
+    unsigned long long *d = nullptr, h[3] = {0, 0, 0};   // max ulp bits (2), mismatch count
     if (cudaMalloc(&d, sizeof(h)) != cudaSuccess) return PPMLR_E_OOM;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     cudaError_t e = cudaMemsetAsync(d, 0, sizeof(h), s);
@@ -48,5 +62,6 @@ extern "C" ppmlr_status ppmlr_selftest_fp64_arith(void *cuda_stream, long long n
     cudaFree(d);
     if (e != cudaSuccess) return PPMLR_E_CUDA;
     for (int k = 0; k < 2; k++) memcpy(&max_ulp[k], &h[k], sizeof(double));
+    max_ulp[2] = (double)h[2];
     return PPMLR_OK;
 }
