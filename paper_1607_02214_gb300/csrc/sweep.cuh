@@ -168,6 +168,60 @@ __device__ __forceinline__ double sqrt_int(double x)
     return __longlong_as_double((long long)(((unsigned long long)((e >> 1) + 1022) << 52) + (unsigned long long)R));
 }
 
+// Product of two doubles on the integer pipes.  The GB300's FP64 pipe
+// retires ~1.7 lanes per SM and clock and the FP64 sweeps keep it the
+// busiest unit, while integer instructions issue beside it: a product moved
+// here frees an FP64 slot.  With a = ma 2^(ea-1075), b = mb 2^(eb-1075)
+// (53-bit significands): the 106-bit P = ma mb from four 32 x 32 -> 64-bit
+// partial products; the result's significand is P >> (52 + t), t = 1 when
+// P >= 2^105, rounded up when the next bit is set and the rest (sticky bits)
+// or the significand's last bit is; the exponent field is ea + eb - 1023 + t
+// (the carry of a significand rounded to 2^53 moves into it).  Normal
+// operands with a normal result: the correctly rounded (to nearest, ties to
+// even) IEEE product, bit for bit.  Otherwise, without a branch (a branch
+// here would let the compiler's fusion of the surrounding multiplies and adds
+// differ between kernels): a zero or subnormal operand or an underflowing
+// result gives a signed zero, an overflowing one infinity, and an inf or NaN
+// operand a result with an all-ones exponent (inf or NaN), so a non-finite
+// state stays non-finite.
+__device__ __forceinline__ double dmul_int(double a, double b)
+{
+    const unsigned long long A = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long B = (unsigned long long)__double_as_longlong(b);
+    const unsigned ah = (unsigned)(A >> 32), al = (unsigned)A;
+    const unsigned bh = (unsigned)(B >> 32), bl = (unsigned)B;
+    const unsigned ea = (ah >> 20) & 0x7FFu, eb = (bh >> 20) & 0x7FFu;
+    const unsigned mah = (ah & 0xFFFFFu) | 0x100000u, mbh = (bh & 0xFFFFFu) | 0x100000u;
+    const unsigned long long p0 = (unsigned long long)al * bl;
+    const unsigned long long p1 = (unsigned long long)al * mbh + (p0 >> 32);
+    const unsigned long long p2 = (unsigned long long)mah * bl + p1;              // < 2^54
+    const unsigned long long p3 = (unsigned long long)mah * mbh + (p2 >> 32);     // P >> 64, < 2^42
+    const unsigned t = (unsigned)(p3 >> 41);
+    const unsigned long long G = (p3 << 22) | ((unsigned)p2 >> 10);              // P >> 42
+    const unsigned sh = 10u + t;
+    unsigned long long M = G >> sh;
+    const unsigned g = (unsigned)G;
+    const unsigned rb = (g >> (sh - 1u)) & 1u;
+    const unsigned st = (g & ((1u << (sh - 1u)) - 1u)) | ((unsigned)p2 & 0x3FFu) | (unsigned)p0;
+    M += rb & ((st != 0u) | (unsigned)M);
+    const int E = (int)(ea + eb) - 1023 + (int)t;
+    const unsigned long long sgn = (unsigned long long)((ah ^ bh) & 0x80000000u) << 32;
+    unsigned long long r = (sgn | ((unsigned long long)(E - 1) << 52)) + M;
+    r = E > 2046 ? (sgn | 0x7FF0000000000000ull) : r;                          // overflow: inf
+    r = (E < 1 || ea == 0u || eb == 0u) ? sgn : r;                             // zero, subnormal, underflow
+    r = (ea == 0x7FFu || eb == 0x7FFu) ? (sgn | 0x7FF0000000000000ull | ((A | B) & 0xFFFFFFFFFFFFFull)) : r;
+    return __longlong_as_double((long long)r);
+}
+
+// A product that the contracted FP64 form takes on the integer pipes
+// (dmul_int; not fused with a following add); elsewhere a * b.
+template <typename R, bool EX>
+__device__ __forceinline__ R imul(R a, R b)
+{
+    if constexpr (!EX && std::is_same<R, double>::value) return dmul_int(a, b);
+    else return a * b;
+}
+
 // Square root of a non-negative value.  Contracted FP64 form: sqrt_int
 // (correctly rounded, no FP64 instruction); zero for x = 0, for a negative x
 // (a rounded discriminant) and, as x is a sum of squares or a density here,
@@ -268,10 +322,10 @@ __device__ __forceinline__ void two_shock(const int iters, const R uL, const R u
 // bn4 = 4 Bn^2 (the factors 4 and 1/2 as exponent moves on the integer pipe).
 __device__ __forceinline__ double fast_impedance(double rho, double p, double b2, double bn4, double gam)
 {
-    const double gp = gam * p;
+    const double gp = dmul_int(gam, p);
     const double S = gp + b2;
-    const double D = fma(-gp, bn4, S * S);              // fsqrt gives 0 for D <= 0
-    return fsqrt<double, false>(rho * pow2_scale(S + fsqrt<double, false>(D), -1));
+    const double D = fma(-gp, bn4, dmul_int(S, S));     // fsqrt gives 0 for D <= 0
+    return fsqrt<double, false>(dmul_int(rho, pow2_scale(S + fsqrt<double, false>(D), -1)));
 }
 
 // Earth dipole along -z: B_d = M [3 (m.r) r - m r^2] / r^5, m = -z.
@@ -309,7 +363,7 @@ __device__ __forceinline__ R limit_slope(R am, R a0, R ap, R c1, R c2, R c3, R *
         const double dp = ap - a0, dm = a0 - am;
         if (dp_out) *dp_out = dp;
         if (!same_sign_d(dp, dm)) return 0.0;
-        const double da = c2 * dp + c3 * dm;
+        const double da = fma(c2, dp, dmul_int(c3, dm));
         // twice the smaller difference (both non-zero here): the exponent field + 1
         const double lim = __longlong_as_double(min(mag_d(dm), mag_d(dp)) + (1LL << 52));
         const double m = mag_d(lim) < mag_d(da) ? lim : fabs(da);
@@ -434,7 +488,7 @@ template <typename R>
 __device__ __forceinline__ AvgCoef<R> avg_coef(R y)
 {
     const R u = R(1) - y;
-    return AvgCoef<R>{u * u, y * u};
+    return AvgCoef<R>{imul<R, false>(u, u), imul<R, false>(y, u)};
 }
 template <typename R>
 __device__ __forceinline__ R avg_right_d(R ai, R dl2, R dr2, const AvgCoef<R> &k)
@@ -471,11 +525,11 @@ __device__ __forceinline__ SlopeCoef<R> slope_coef(R xm, R x0, R xp)
 {
     if constexpr (!EX) {
         const R d1 = xm + x0 + xp, d2 = xp + x0, d3 = xm + x0;
-        const R q = x0 * recip<R, EX>(d1 * (d2 * d3));
+        const R q = imul<R, EX>(x0, recip<R, EX>(imul<R, EX>(d1, imul<R, EX>(d2, d3))));
         SlopeCoef<R> k;
         k.c1 = R(1);
-        k.c2 = (R(2) * xm + x0) * d3 * q;
-        k.c3 = (x0 + R(2) * xp) * d2 * q;
+        k.c2 = imul<R, EX>(imul<R, EX>(R(2) * xm + x0, d3), q);
+        k.c3 = imul<R, EX>(imul<R, EX>(x0 + R(2) * xp, d2), q);
         return k;
     }
     R s3 = xm + x0 + xp;
@@ -494,19 +548,20 @@ __device__ __forceinline__ EdgeCoef<R> edge_coef(R x0, R x1, R x2, R x3)
 {
     if constexpr (!EX) {
         const R d1 = R(2) * x1 + x2, d2 = R(2) * x2 + x1, d3 = x1 + x2, d4 = x0 + x1 + x2 + x3;
-        const R d12 = d1 * d2, d34 = d3 * d4;
-        const R inv = recip<R, EX>(d12 * d34);
-        const R i12 = d34 * inv, i34 = d12 * inv;          // 1 / d12, 1 / d34
-        const R r1 = d2 * i12, r2 = d1 * i12, r3 = d4 * i34, r4 = d3 * i34;
-        const R z1 = (x0 + x1) * r1, z2 = (x3 + x2) * r2;
+        const R d12 = imul<R, EX>(d1, d2), d34 = imul<R, EX>(d3, d4);
+        const R inv = recip<R, EX>(imul<R, EX>(d12, d34));
+        const R i12 = imul<R, EX>(d34, inv), i34 = imul<R, EX>(d12, inv);          // 1 / d12, 1 / d34
+        const R r1 = imul<R, EX>(d2, i12), r2 = imul<R, EX>(d1, i12);
+        const R r3 = imul<R, EX>(d4, i34), r4 = imul<R, EX>(d3, i34);
+        const R z1 = imul<R, EX>(x0 + x1, r1), z2 = imul<R, EX>(x3 + x2, r2);
         // k1 = (x1/d3) (1 + 2 (x2/d4)(z1 - z2)), k4 = (x1/d4) z1, k5 = (x2/d4) z2
-        const R x1r3 = x1 * r3, x2r4 = x2 * r4;
+        const R x1r3 = imul<R, EX>(x1, r3), x2r4 = imul<R, EX>(x2, r4);
         EdgeCoef<R> k;
-        k.k1 = x1r3 + x1r3 * (R(2) * x2r4 * (z1 - z2));
+        k.k1 = x1r3 + x1r3 * imul<R, EX>(R(2) * x2r4, z1 - z2);
         k.k2 = R(0);
         k.k3 = R(0);
-        k.k4 = (x1 * r4) * z1;
-        k.k5 = x2r4 * z2;
+        k.k4 = imul<R, EX>(imul<R, EX>(x1, r4), z1);
+        k.k5 = imul<R, EX>(x2r4, z2);
         return k;
     }
     R z1 = (x0 + x1) / (R(2) * x1 + x2);
@@ -784,18 +839,18 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             e = R(E / rd);
         } else {
             const double ir = recip<double, EX>(rd);
-            prd = (a.gamma - 1.0) * (E - pow2_scale(mn * mn + m1 * m1 + m2 * m2, -1) * ir
-                                     - 0.5 * (bn * bn + b1 * b1 + b2 * b2));
-            rho = R(rd); u = R(mn * ir); v1 = R(m1 * ir); v2 = R(m2 * ir);
-            e = R(E * ir);
-            if (a.iw) dtm_k = R(dt * ir * a.iw[CHK(g + GH, NG)]);    // dt / (rho dx) without a division
+            prd = dmul_int(a.gamma - 1.0, E - pow2_scale(dmul_int(mn, mn) + m1 * m1 + m2 * m2, -1) * ir
+                                          - 0.5 * (dmul_int(bn, bn) + b1 * b1 + b2 * b2));
+            rho = R(rd); u = R(dmul_int(mn, ir)); v1 = R(dmul_int(m1, ir)); v2 = R(dmul_int(m2, ir));
+            e = R(dmul_int(E, ir));
+            if (a.iw) dtm_k = R(dmul_int(dmul_int(dt, ir), a.iw[CHK(g + GH, NG)]));    // dt / (rho dx) without a division
         }
         // p_min >= 0: the floor test is a signed comparison of the bit patterns in
         // the contracted form (integer pipe); the exact form compares doubles
         const bool below = EX ? prd < a.p_min : __double_as_longlong(prd) < __double_as_longlong(a.p_min);
         if (below) { prd = a.p_min; floored = out_cell; }
         Bn = R(bn); B1 = R(b1); B2 = R(b2); pr = R(prd);
-        dm = R(rd * dx);
+        dm = R(imul<double, EX>(rd, dx));
     } else if (act) {
         // mixed path: float geometry, float dipole, integer double->float
         // splits and a double-float pressure recovery (no FP64 instructions)
@@ -845,7 +900,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
     if (act) {
         R Pt;
         if constexpr (F64 && !EX) {     // |B|^2 shared by the total pressure and the impedance
-            const double bn2 = Bn * Bn, b2 = fma(B2, B2, fma(B1, B1, bn2));
+            const double bn2 = dmul_int(Bn, Bn), b2 = fma(B2, B2, fma(B1, B1, bn2));
             Pt = fma(0.5, b2, pr);
             W = fast_impedance(rho, pr, b2, pow2_scale(bn2, 2), gam);
         } else {
@@ -856,9 +911,9 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         SM(A_B1, s) = B1; SM(A_B2, s) = B2; SM(A_P, s) = pdel; SM(A_DM, s) = dm;
         SM(A_PT, s) = Pt; SM(A_BN, s) = Bn;
         if (a.do_src) {   // v x B_d in the local frame
-            SM(A_AX, s) = v1 * Bd2 - v2 * Bd1;
-            SM(A_AY, s) = v2 * Bd0 - u * Bd2;
-            SM(A_AZ, s) = u * Bd1 - v1 * Bd0;
+            SM(A_AX, s) = v1 * Bd2 - imul<R, EX>(v2, Bd1);
+            SM(A_AY, s) = v2 * Bd0 - imul<R, EX>(u, Bd2);
+            SM(A_AZ, s) = u * Bd1 - imul<R, EX>(v1, Bd0);
         }
     }
     {
@@ -918,11 +973,11 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
                 DA2 = (SM(A_AZ, s + PS) - SM(A_AZ, s - PS)) / h;
             } else {
                 const R ih = h_table ? R(a.ih[CHK(g + GH, NG)]) : R(1) / h;
-                DB0 = (SM(A_BN, s + PS) - SM(A_BN, s - PS)) * ih;
-                DB1 = (SM(A_B1, s + PS) - SM(A_B1, s - PS)) * ih;
-                DB2 = (SM(A_B2, s + PS) - SM(A_B2, s - PS)) * ih;
-                DA1 = (SM(A_AY, s + PS) - SM(A_AY, s - PS)) * ih;
-                DA2 = (SM(A_AZ, s + PS) - SM(A_AZ, s - PS)) * ih;
+                DB0 = imul<R, EX>(SM(A_BN, s + PS) - SM(A_BN, s - PS), ih);
+                DB1 = imul<R, EX>(SM(A_B1, s + PS) - SM(A_B1, s - PS), ih);
+                DB2 = imul<R, EX>(SM(A_B2, s + PS) - SM(A_B2, s - PS), ih);
+                DA1 = imul<R, EX>(SM(A_AY, s + PS) - SM(A_AY, s - PS), ih);
+                DA2 = imul<R, EX>(SM(A_AZ, s + PS) - SM(A_AZ, s - PS), ih);
             }
             R J0 = 0, J1 = -DB2, J2 = DB1;
             R cA0 = 0, cA1 = -DA2, cA2 = DA1;
@@ -937,16 +992,16 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
                 src_b[2] = cA2 - pw * v2 * divB;
                 src_e = u * src_m[0] + v1 * src_m[1] + v2 * src_m[2] + Bn * cA0 + B1 * cA1 + B2 * cA2;
             } else {            // the same terms without the products with J0 = cA0 = 0
-                src_m[0] = J1 * Bd2 - J2 * Bd1;
-                src_m[1] = J2 * Bd0;
-                src_m[2] = -(J1 * Bd0);
+                src_m[0] = J1 * Bd2 - imul<R, EX>(J2, Bd1);
+                src_m[1] = imul<R, EX>(J2, Bd0);
+                src_m[2] = -imul<R, EX>(J1, Bd0);
                 src_b[0] = R(0); src_b[1] = cA1; src_b[2] = cA2;
                 if (a.powell) {
-                    src_b[0] = -(u * divB);
+                    src_b[0] = -imul<R, EX>(u, divB);
                     src_b[1] = cA1 - v1 * divB;
                     src_b[2] = cA2 - v2 * divB;
                 }
-                src_e = u * src_m[0] + v1 * src_m[1] + v2 * src_m[2] + B1 * cA1 + B2 * cA2;
+                src_e = imul<R, EX>(u, src_m[0]) + v1 * src_m[1] + v2 * src_m[2] + B1 * cA1 + B2 * cA2;
             }
         }
     }
@@ -996,8 +1051,8 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         } else {
             if (!(F64 && a.iw)) dtm_k = dtr / dm;       // else from P1
             const R dtm = dtm_k;
-            yf = W * dtm;
-            ya = fsqrt<R, EX>(rho) * K<R>::ab(Bn) * dtm;
+            yf = imul<R, EX>(W, dtm);
+            ya = imul<R, EX>(imul<R, EX>(fsqrt<R, EX>(rho), K<R>::ab(Bn)), dtm);
         }
         const R own[7] = {rho, u, v1, v2, B1, B2, pdel};
         R srv[9];
@@ -1058,8 +1113,8 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         if constexpr (!F64) pref = a.p_reff;
         R WL, WR;
         if constexpr (F64 && !EX) {     // the transverse |B|^2 of each side shared by P and W
-            const double bn2 = Bnf * Bnf, bn4 = pow2_scale(bn2, 2);
-            const double btL = fma(sl[5], sl[5], sl[4] * sl[4]), btR = fma(Rs[5], Rs[5], Rs[4] * Rs[4]);
+            const double bn2 = dmul_int(Bnf, Bnf), bn4 = pow2_scale(bn2, 2);
+            const double btL = fma(sl[5], sl[5], dmul_int(sl[4], sl[4])), btR = fma(Rs[5], Rs[5], dmul_int(Rs[4], Rs[4]));
             PL = fma(0.5, btL, sl[6]);
             PR = fma(0.5, btR, Rs[6]);
             WL = fast_impedance(sl[0], sl[6], btL + bn2, bn4, gam);
@@ -1090,7 +1145,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         } else if constexpr (F64) {
             // P* = PL - WL (u* - uL): the same value in exact arithmetic
             // (the left wave's jump condition), two instructions
-            us = (WL * sl[1] + WR * Rs[1] + PL - PR) * recip<R, EX>(WL + WR);
+            us = dmul_int(fma(WR, Rs[1], dmul_int(WL, sl[1])) + PL - PR, recip<R, EX>(WL + WR));
             Ps = fma(-WL, us - sl[1], PL);
         } else {
             const R iW = recip<R, EX>(WL + WR);
@@ -1120,8 +1175,8 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
                     vs[t] = 0.5 * (vL + vR);
                     ss[t] = 0.0;
                 } else {
-                    vs[t] = (fma(qL, vL, qR * vR) + dB) * iQ;
-                    ss[t] = Bnf * fma(sqL, vs[t] - vL, sl[7 + t]);
+                    vs[t] = dmul_int(fma(qL, vL, dmul_int(qR, vR)) + dB, iQ);
+                    ss[t] = dmul_int(Bnf, fma(sqL, vs[t] - vL, sl[7 + t]));
                 }
             }
         } else {
@@ -1147,8 +1202,8 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             }
         }
         rs_u = us; rs_S = Ss; rs_s1 = ss[0]; rs_s2 = ss[1];
-        rs_b1 = Bnf * vs[0]; rs_b2 = Bnf * vs[1];
-        if constexpr (F64) rs_fe = Ss * us - ss[0] * vs[0] - ss[1] * vs[1];
+        rs_b1 = imul<R, EX>(Bnf, vs[0]); rs_b2 = imul<R, EX>(Bnf, vs[1]);
+        if constexpr (F64) rs_fe = imul<R, EX>(Ss, us) - ss[0] * vs[0] - ss[1] * vs[1];
         else rs_fe = (Ss + pref) * us - ss[0] * vs[0] - ss[1] * vs[1];     // absolute S* in the energy flux
         SM(SC0 + 0, s) = rs_u; SM(SC0 + 1, s) = rs_S; SM(SC0 + 2, s) = rs_s1; SM(SC0 + 3, s) = rs_s2;
         SM(SC0 + 4, s) = rs_b1; SM(SC0 + 5, s) = rs_b2; SM(SC0 + 6, s) = rs_fe;
@@ -1165,8 +1220,8 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         else dxr = a.wf[CHK(g + GH, NG)];
         dxL = dxr + dtr * (rs_u - lu);
         if (!gt0<R, EX>(dxL)) atomicOr(a.flags, FLAG_CFL);
-        R bv1 = dtr * (rs_b1 - lb1);
-        R bv2 = dtr * (rs_b2 - lb2);
+        R bv1 = imul<R, EX>(dtr, rs_b1 - lb1);
+        R bv2 = imul<R, EX>(dtr, rs_b2 - lb2);
         R B1dx = B1 * dxr + bv1;
         R B2dx = B2 * dxr + bv2;
         if constexpr (EX) {
@@ -1184,18 +1239,18 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             R v1L = v1 + (rs_s1 - ls1) * dtm;
             R v2L = v2 + (rs_s2 - ls2) * dtm;
             R eL = e - (rs_fe - lfe) * dtm;
-            R rhoL = dm * idxL;
-            qL[0] = rhoL; qL[1] = rhoL * uL; qL[2] = rhoL * v1L; qL[3] = rhoL * v2L;
-            qL[4] = B1dx * idxL; qL[5] = B2dx * idxL; qL[6] = rhoL * eL;
+            R rhoL = imul<R, EX>(dm, idxL);
+            qL[0] = rhoL; qL[1] = imul<R, EX>(rhoL, uL); qL[2] = imul<R, EX>(rhoL, v1L); qL[3] = imul<R, EX>(rhoL, v2L);
+            qL[4] = imul<R, EX>(B1dx, idxL); qL[5] = imul<R, EX>(B2dx, idxL); qL[6] = imul<R, EX>(rhoL, eL);
         }
-        dC[0] = -dtr * (rs_S - lS);
-        dC[1] = dtr * (rs_s1 - ls1);
-        dC[2] = dtr * (rs_s2 - ls2);
+        dC[0] = imul<R, EX>(-dtr, rs_S - lS);
+        dC[1] = imul<R, EX>(dtr, rs_s1 - ls1);
+        dC[2] = imul<R, EX>(dtr, rs_s2 - ls2);
         dC[3] = bv1;
         dC[4] = bv2;
-        dC[5] = -dtr * (rs_fe - lfe);
-        del_p = dtr * rs_u;
-        del_m = dtr * lu;
+        dC[5] = imul<R, EX>(-dtr, rs_fe - lfe);
+        del_p = imul<R, EX>(dtr, rs_u);
+        del_m = imul<R, EX>(dtr, lu);
 #pragma unroll
         for (int v = 0; v < 7; v++) SM(SB0 + v, s) = qL[v];
         SM(SB0 + 7, s) = dxL;
@@ -1277,7 +1332,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
                 } else {
                     const AvgCoef<R> k = avg_coef<R>(y);
 #pragma unroll
-                    for (int v = 0; v < 7; v++) SM(flux_slot(v), s) = del_p * avg_right_d<R>(qL[v], pl[v], pr_[v], k);
+                    for (int v = 0; v < 7; v++) SM(flux_slot(v), s) = imul<R, EX>(del_p, avg_right_d<R>(qL[v], pl[v], pr_[v], k));
                 }
             } else if (!lt0<R, EX>(del_p)) {
 #pragma unroll
@@ -1293,7 +1348,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             } else {
                 const AvgCoef<R> k = avg_coef<R>(y);
 #pragma unroll
-                for (int v = 0; v < 7; v++) SM(flux_slot(v), s - PS) = del_m * avg_left_d<R>(qL[v], pl[v], pr_[v], k);
+                for (int v = 0; v < 7; v++) SM(flux_slot(v), s - PS) = imul<R, EX>(del_m, avg_left_d<R>(qL[v], pl[v], pr_[v], k));
             }
         }
     }

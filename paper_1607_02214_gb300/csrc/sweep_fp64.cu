@@ -16,11 +16,15 @@ namespace {
 // the root is exact or lies within a fraction of an ulp of s 2^j: out[0]
 // square root, out[1] reciprocal (non-negative doubles compared as their
 // bit patterns), out[2] the arguments whose square root differs from the
-// correctly rounded one.
+// correctly rounded one, out[3] the pairs (x, y) whose integer-pipe product
+// differs from the IEEE product; y = (1 + f') 2^e', e' cycling over
+// -500..500, or for every fourth pair x = 1 + k 2^-52 (k < 2^10) and
+// y = (2c + 1) 2^-8 (c < 2^8), products whose discarded bits are often
+// exactly one half (ties).
 __global__ void __launch_bounds__(256) arith_selftest_kernel(long long n, unsigned long long *out)
 {
     double m_sqrt = 0.0, m_rcp = 0.0;
-    unsigned long long wrong = 0;
+    unsigned long long wrong = 0, wrong_mul = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int ex = (int)(i % 2001) - 1000;
         const double f = (double)(((unsigned long long)i * 0x9E3779B97F4A7C15ULL) >> 11) * 0x1.0p-53;
@@ -36,19 +40,28 @@ __global__ void __launch_bounds__(256) arith_selftest_kernel(long long n, unsign
         m_sqrt = fmax(m_sqrt, fabs(s - s_ref) / ldexp(1.0, ilogb(s_ref) - 52));
         m_rcp = fmax(m_rcp, fabs(r - r_ref) / ldexp(1.0, ilogb(r_ref) - 52));
         wrong += __double_as_longlong(s) != __double_as_longlong(s_ref);
+        const unsigned long long h = (unsigned long long)i * 0xD1B54A32D192ED03ULL;
+        double xa = ldexp(1.0 + f, ex / 2), ya = ldexp(1.0 + (double)(h >> 11) * 0x1.0p-53, (int)(h % 1001) - 500);
+        if ((i & 3) == 1) {
+            xa = 1.0 + (double)((h >> 20) & 1023) * 0x1.0p-52;
+            ya = (double)(2 * ((h >> 40) & 255) + 1) * 0x1.0p-8;
+        }
+        if ((i & 8) != 0) xa = -xa;
+        wrong_mul += __double_as_longlong(dmul_int(xa, ya)) != __double_as_longlong(__dmul_rn(xa, ya));
     }
     atomicMax(out, (unsigned long long)__double_as_longlong(m_sqrt));
     atomicMax(out + 1, (unsigned long long)__double_as_longlong(m_rcp));
     atomicAdd(out + 2, wrong);
+    atomicAdd(out + 3, wrong_mul);
 }
 
 }  // namespace
 }  // namespace ppmlr
 
-extern "C" ppmlr_status ppmlr_selftest_fp64_arith(void *cuda_stream, long long n, double max_ulp[3])
+extern "C" ppmlr_status ppmlr_selftest_fp64_arith(void *cuda_stream, long long n, double max_ulp[4])
 {
     if (!max_ulp || n < 1) return PPMLR_E_INVALID;
-    unsigned long long *d = nullptr, h[3] = {0, 0, 0};   // max ulp bits (2), mismatch count
+    unsigned long long *d = nullptr, h[4] = {0, 0, 0, 0};   // max ulp bits (2), mismatch counts (2)
     if (cudaMalloc(&d, sizeof(h)) != cudaSuccess) return PPMLR_E_OOM;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     cudaError_t e = cudaMemsetAsync(d, 0, sizeof(h), s);
@@ -63,5 +76,6 @@ extern "C" ppmlr_status ppmlr_selftest_fp64_arith(void *cuda_stream, long long n
     if (e != cudaSuccess) return PPMLR_E_CUDA;
     for (int k = 0; k < 2; k++) memcpy(&max_ulp[k], &h[k], sizeof(double));
     max_ulp[2] = (double)h[2];
+    max_ulp[3] = (double)h[3];
     return PPMLR_OK;
 }

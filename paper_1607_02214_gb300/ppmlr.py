@@ -148,13 +148,15 @@ def measure_pipe_rates(stream=None):
 def selftest_fp64_arith(n=1 << 22, stream=None):
     """Largest error, in ulps of the correctly rounded result, of the
     PPMLR_FP64 form's square root and reciprocal over n arguments spanning
-    2^-1000..2^1000, and how many of the square roots differ from the
-    correctly rounded ones (ppmlr_selftest_fp64_arith)."""
-    out = (c_double * 3)()
+    2^-1000..2^1000, how many of the square roots differ from the correctly
+    rounded ones, and how many of n products on the integer pipes differ
+    from the IEEE products (ppmlr_selftest_fp64_arith)."""
+    out = (c_double * 4)()
     st = load().ppmlr_selftest_fp64_arith(c_void_p(stream), n, out)
     if st != PPMLR_OK:
         raise PPMLRError(st, "ppmlr_selftest_fp64_arith failed")
-    return {"sqrt_ulp": out[0], "recip_ulp": out[1], "sqrt_mismatches": int(out[2])}
+    return {"sqrt_ulp": out[0], "recip_ulp": out[1], "sqrt_mismatches": int(out[2]),
+            "mul_mismatches": int(out[3])}
 
 
 class PPMLRError(RuntimeError):
