@@ -455,14 +455,13 @@ void ppmlr_ensemble_destroy(ppmlr_ens *ens);
  * PPMLR_E_CUDA. */
 ppmlr_status ppmlr_measure_pipe_rates(void *cuda_stream, double rates[3]);
 
-/* Self-test of the PPMLR_FP64 form's own square root (integer and FP32
- * arithmetic, correctly rounded), reciprocal (a hardware approximation
- * refined by one third-order step) and integer-pipe product; no paper
+/* Self-test of the PPMLR_FP64 form's own square root, reciprocal and
+ * product (integer and FP32 arithmetic, each correctly rounded); no paper
  * counterpart.  Over n >= 1 arguments (1 + f) 2^e, e cycling over
  * -1000..1000, every fourth one an exact square moved by -3..3 units in its
  * last place instead: max_ulp[0] and max_ulp[1] the largest errors of the
  * square root and the reciprocal in ulps of the correctly rounded result
- * (0 and at most 1 for the form's accuracy claim), max_ulp[2] the count of
+ * (both 0 for the form's accuracy claim), max_ulp[2] the count of
  * square roots that differ from the correctly rounded ones (0), max_ulp[3]
  * the count of n products of normal doubles with normal results (a quarter
  * of them built to round a tie) that differ from the IEEE product (0).

@@ -80,24 +80,67 @@ __device__ __forceinline__ double pow2_scale(double x, int k)
     return (b << 1) == 0 ? x : __longlong_as_double(b + ((long long)k << 52));
 }
 
-// 1/x in the contracted double form: the hardware's approximate reciprocal
-// refined by one cubically convergent Newton-Raphson step,
-// r (1 + e + e^2) with e = 1 - x r (three fused multiply-adds: from a seed
-// good to ~2^-20, as measured on GB300, the error falls to ~2^-60, i.e. the
-// result is within an ulp of 1/x, not necessarily the correctly rounded
-// quotient); other forms
-// divide.  x finite and non-zero where it is used.
+// 1/x of a double on the integer and FP32 pipes, correctly rounded (no FP64
+// instruction; the hardware-seeded FP64 refinement costs the GB300's FP64
+// pipe three fused multiply-adds).  With x = m 2^(e-1075), m the 53-bit
+// significand, 1/x = Q 2^(970-e), Q = 2^105 / m in (2^52, 2^53], and the
+// result's significand is R = round(Q):
+//  1. float seed: h ~ 1/mh from the hardware's approximate reciprocal of
+//     the top 24 bits mh = m >> 29; with eh = 1 - mh h (exact by one fused
+//     multiply-add) and delta = (m - mh 2^29) / (mh 2^29) < 2^-23,
+//     1/m ~ h 2^-29 (1 + d + d^2), d = eh - delta, so R1 = h 2^76 +
+//     round(h (d + d^2) 2^76) lies within ~2^8.3 of Q (the omitted
+//     eh delta term and the float roundings);
+//  2. one Newton step on the exact integer remainder r = 2^105 - m R1
+//     (|r| < 2^63, so its low 64 bits are the value): R2 = R1 + round(r / m),
+//     r / m from r >> 41 and h in float, within one of Q;
+//  3. R = R2 + k, k in {-1, 0, 1}, such that |2^105 - m R| < m / 2 (round
+//     to nearest; a tie would need m to be a power of two, where Q is
+//     exact).
+// Floats are built from and read back to integers by exponent-field
+// arithmetic (the 1.5 2^23 offset), not by conversion instructions.
+// Zero or subnormal x gives a signed inf, inf a signed zero, NaN itself; a
+// result below the normal range flushes to a signed zero.
+__device__ __forceinline__ double recip_int(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned ex = (unsigned)(b >> 52) & 0x7FFu;
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+    const unsigned mh = (unsigned)(m >> 29);                                     // [2^23, 2^24)
+    const float xh = __uint_as_float((150u << 23) | (mh & 0x7FFFFFu));           // = mh
+    const float xl = __uint_as_float(0x4B000000u | ((unsigned)(m >> 6) & 0x7FFFFFu)) - 8388608.0f;  // (m mod 2^29) >> 6
+    float h;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(h) : "f"(xh));
+    const float eh = fmaf(-xh, h, 1.0f);
+    const float d = fmaf(-xl * 0x1p-23f, h, eh);
+    const float l = h * fmaf(d, d, d);
+    const unsigned hb = __float_as_uint(h);                                      // h in (2^-24, 2^-23]
+    long long R = (long long)((hb & 0x7FFFFFu) | 0x800000u) << ((int)(hb >> 23) - 74);
+    const float l66 = fmaf(l, 0x1p66f, 12582912.0f);                            // round(l 2^66), |.| < 2^22
+    const float lr = fmaf(-(l66 - 12582912.0f), 0x1p-66f, l);                   // its remainder (exact)
+    R += ((long long)(__float_as_int(l66) - 0x4B400000) << 10) +
+         (long long)(__float_as_int(fmaf(lr, 0x1p76f, 12582912.0f)) - 0x4B400000);
+    long long r = -(long long)(m * (unsigned long long)R);                     // 2^105 - m R
+    const float vr = __int_as_float(0x4B400000 + (int)(r >> 41)) - 12582912.0f;  // r 2^-41, |.| < 2^22
+    const long long k = (long long)(__float_as_int(fmaf(vr, h * 0x1p12f, 12582912.0f)) - 0x4B400000);
+    R += k;
+    r -= k * (long long)m;
+    const long long mm = (long long)m;
+    R += (long long)(2 * r > mm) - (long long)(2 * r < -mm);
+    const unsigned long long sgn = b & 0x8000000000000000ull;
+    unsigned long long res = (sgn | ((unsigned long long)(2044u - ex) << 52)) + (unsigned long long)R;
+    res = ex >= 2045u ? sgn : res;                                               // result below the normal range
+    res = ex == 0u ? (sgn | 0x7FF0000000000000ull) : res;                       // zero, subnormal
+    res = ex == 0x7FFu ? ((b << 12) != 0 ? b : sgn) : res;                       // NaN, inf
+    return __longlong_as_double((long long)res);
+}
+
+// 1/x: recip_int in the contracted double form; other forms divide.
 template <typename R, bool EX>
 __device__ __forceinline__ R recip(R x)
 {
-    if constexpr (!EX && std::is_same<R, double>::value) {
-        double r;
-        asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-        const double e = fma(-x, r, 1.0);
-        return fma(r, fma(e, e, e), r);
-    } else {
-        return R(1) / x;
-    }
+    if constexpr (!EX && std::is_same<R, double>::value) return recip_int(x);
+    else return R(1) / x;
 }
 
 // The remap's donor fraction y (> 0 where it is used) reaches the zone width:

@@ -1,8 +1,8 @@
 """The contracted FP64 form's own square root (a float-pair seed, one Newton
 step on the exact integer remainder and a final rounding step) equals CUDA's
 IEEE square root bit for bit, also on exact squares and their neighbours
-a few ulps away; its reciprocal (the hardware's approximate seed refined
-by the cubic Newton-Raphson step) stays within one ulp of IEEE division;
+a few ulps away; its reciprocal (a float seed, one Newton step on the
+exact integer remainder and a final rounding step) equals IEEE division;
 its integer-pipe product equals the IEEE product bit for bit on normal
 operands with normal results, ties included.  Arguments span
 2^-1000..2^1000."""
@@ -19,13 +19,13 @@ def built():
     build.build()
 
 
-def test_sqrt_and_product_exact_reciprocal_within_one_ulp():
+def test_sqrt_reciprocal_and_product_exact():
     err = ppmlr.selftest_fp64_arith(1 << 24)
     print(err)
     assert err["sqrt_mismatches"] == 0
     assert err["mul_mismatches"] == 0
     assert err["sqrt_ulp"] == 0.0
-    assert 0.0 <= err["recip_ulp"] <= 1.0
+    assert err["recip_ulp"] == 0.0
 
 
 def test_rejects_bad_arguments():
