@@ -46,7 +46,9 @@ typedef enum {
 
 typedef enum {
     PPMLR_FP64 = 0,         /* every stage in IEEE double; fused multiply-add and one reciprocal
-                               per shared denominator (agrees with the CPU reference to roundoff) */
+                               per shared denominator; products, reciprocals and square roots
+                               partly on the integer pipes, each correctly rounded (subnormals
+                               flush to zero); agrees with the CPU reference to roundoff */
     PPMLR_MIXED = 1,        /* FP32 reconstruction, Riemann, remap and sources; pressure recovered
                                in double-float arithmetic; FP64 state accumulation */
     PPMLR_FP64_EXACT = 2    /* every stage in IEEE double with the CPU reference's expression
