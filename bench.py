@@ -62,6 +62,7 @@ BYTES_PER_CELL_SWEEP = 128      # read 8 FP64 + write 8 FP64
 NCU_TRAFFIC = {
     "fp64:x": {"bytes_per_cell": 155.2, "src": "fc4fe0bd5032235c"},
     "fp64:y": {"bytes_per_cell": 309.6, "src": "fc4fe0bd5032235c"},
+    "fp64:z": {"bytes_per_cell": 295.7, "src": "fc4fe0bd5032235c"},
     # the two passes of the FP64 CFL step together (float screen 68.7, FP64 pass 4.0)
     "fp64:cfl": {"bytes_per_cell": 72.7, "src": "e187dbc3cdd24379"},
     "mixed:x": {"bytes_per_cell": 123.5, "src": "9090d9d48887f905"},
