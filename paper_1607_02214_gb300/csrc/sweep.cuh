@@ -64,6 +64,25 @@ __device__ __forceinline__ bool neg_d(double x)                                 
     return b < 0 && (b << 1) != 0;
 }
 __device__ __forceinline__ long long mag_d(double x) { return __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL; }
+// Sign flip and absolute value of a double on the integer pipe: on the GB300
+// a double negation or fabs that is not an operand of a fused multiply-add
+// is an FP64 add (measured with ncu), doublings likewise.
+__device__ __forceinline__ double neg_i(double x)
+{
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+}
+template <typename R, bool EX>
+__device__ __forceinline__ R negx(R x)
+{
+    if constexpr (!EX && std::is_same<R, double>::value) return neg_i(x);
+    else return -x;
+}
+template <typename R, bool EX>
+__device__ __forceinline__ R absx(R x)
+{
+    if constexpr (!EX && std::is_same<R, double>::value) return __longlong_as_double(mag_d(x));
+    else return K<R>::ab(x);
+}
 // x * y > 0 (both non-zero, same sign; ignores underflow of the product)
 __device__ __forceinline__ bool same_sign_d(double x, double y)
 {
@@ -407,10 +426,12 @@ __device__ __forceinline__ R limit_slope(R am, R a0, R ap, R c1, R c2, R c3, R *
         if (dp_out) *dp_out = dp;
         if (!same_sign_d(dp, dm)) return 0.0;
         const double da = fma(c2, dp, dmul_int(c3, dm));
-        // twice the smaller difference (both non-zero here): the exponent field + 1
-        const double lim = __longlong_as_double(min(mag_d(dm), mag_d(dp)) + (1LL << 52));
-        const double m = mag_d(lim) < mag_d(da) ? lim : fabs(da);
-        return pos_d(da) ? m : (neg_d(da) ? -m : 0.0);
+        // twice the smaller difference (both non-zero here): the exponent field
+        // + 1; |da| limited to it and da's sign put back, on the bit patterns
+        // (+0 for da = 0)
+        const long long lim = min(mag_d(dm), mag_d(dp)) + (1LL << 52);
+        const long long m = min(lim, mag_d(da));
+        return __longlong_as_double(m == 0 ? 0LL : (m | (__double_as_longlong(da) & (long long)0x8000000000000000ULL)));
     }
     if constexpr (!EX && std::is_same<R, float>::value) {   // branch-free: min/max and selects
         const float dp = ap - a0, dm = a0 - am;
@@ -600,7 +621,10 @@ __device__ __forceinline__ EdgeCoef<R> edge_coef(R x0, R x1, R x2, R x3)
         // k1 = (x1/d3) (1 + 2 (x2/d4)(z1 - z2)), k4 = (x1/d4) z1, k5 = (x2/d4) z2
         const R x1r3 = imul<R, EX>(x1, r3), x2r4 = imul<R, EX>(x2, r4);
         EdgeCoef<R> k;
-        k.k1 = x1r3 + x1r3 * imul<R, EX>(R(2) * x2r4, z1 - z2);
+        R x2r4_2;                                          // 2 x2r4 (an exponent move for doubles)
+        if constexpr (std::is_same<R, double>::value) x2r4_2 = pow2_scale(x2r4, 1);
+        else x2r4_2 = R(2) * x2r4;
+        k.k1 = x1r3 + x1r3 * imul<R, EX>(x2r4_2, z1 - z2);
         k.k2 = R(0);
         k.k3 = R(0);
         k.k4 = imul<R, EX>(imul<R, EX>(x1, r4), z1);
@@ -981,10 +1005,14 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         if (p >= 2 && p <= NPe - 3) {
             R Pp = SM(A_PT, s + PS), Pm = SM(A_PT, s - PS);
             R dP = Pp - Pm;
-            R pmin = Pp < Pm ? Pp : Pm;
+            R pmin;
+            if constexpr (!EX && F64)      // total pressures >= 0: ordered as their bit patterns
+                pmin = __longlong_as_double(min(__double_as_longlong(Pp), __double_as_longlong(Pm)));
+            else
+                pmin = Pp < Pm ? Pp : Pm;
             bool shock;
             if constexpr (!EX && F64)      // the same tests on the bit patterns (integer pipe)
-                shock = mag_d(dP) > mag_d(R(0.33) * pmin) && pos_d(SM(A_U, s - PS) - SM(A_U, s + PS));
+                shock = mag_d(dP) > mag_d(dmul_int(0.33, pmin)) && pos_d(SM(A_U, s - PS) - SM(A_U, s + PS));
             else
                 shock = K<R>::ab(dP) > R(0.33) * pmin && SM(A_U, s - PS) - SM(A_U, s + PS) > R(0);
             if (shock) {
@@ -1022,8 +1050,8 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
                 DA1 = imul<R, EX>(SM(A_AY, s + PS) - SM(A_AY, s - PS), ih);
                 DA2 = imul<R, EX>(SM(A_AZ, s + PS) - SM(A_AZ, s - PS), ih);
             }
-            R J0 = 0, J1 = -DB2, J2 = DB1;
-            R cA0 = 0, cA1 = -DA2, cA2 = DA1;
+            R J0 = 0, J1 = negx<R, EX>(DB2), J2 = DB1;
+            R cA0 = 0, cA1 = negx<R, EX>(DA2), cA2 = DA1;
             R divB = DB0;
             if constexpr (EX) {
                 src_m[0] = J1 * Bd2 - J2 * Bd1;
@@ -1037,10 +1065,10 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             } else {            // the same terms without the products with J0 = cA0 = 0
                 src_m[0] = J1 * Bd2 - imul<R, EX>(J2, Bd1);
                 src_m[1] = imul<R, EX>(J2, Bd0);
-                src_m[2] = -imul<R, EX>(J1, Bd0);
+                src_m[2] = negx<R, EX>(imul<R, EX>(J1, Bd0));
                 src_b[0] = R(0); src_b[1] = cA1; src_b[2] = cA2;
                 if (a.powell) {
-                    src_b[0] = -imul<R, EX>(u, divB);
+                    src_b[0] = negx<R, EX>(imul<R, EX>(u, divB));
                     src_b[1] = cA1 - v1 * divB;
                     src_b[2] = cA2 - v2 * divB;
                 }
@@ -1095,7 +1123,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             if (!(F64 && a.iw)) dtm_k = dtr / dm;       // else from P1
             const R dtm = dtm_k;
             yf = imul<R, EX>(W, dtm);
-            ya = imul<R, EX>(imul<R, EX>(fsqrt<R, EX>(rho), K<R>::ab(Bn)), dtm);
+            ya = imul<R, EX>(imul<R, EX>(fsqrt<R, EX>(rho), absx<R, EX>(Bn)), dtm);
         }
         const R own[7] = {rho, u, v1, v2, B1, B2, pdel};
         R srv[9];
@@ -1286,12 +1314,12 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             qL[0] = rhoL; qL[1] = imul<R, EX>(rhoL, uL); qL[2] = imul<R, EX>(rhoL, v1L); qL[3] = imul<R, EX>(rhoL, v2L);
             qL[4] = imul<R, EX>(B1dx, idxL); qL[5] = imul<R, EX>(B2dx, idxL); qL[6] = imul<R, EX>(rhoL, eL);
         }
-        dC[0] = imul<R, EX>(-dtr, rs_S - lS);
+        dC[0] = negx<R, EX>(imul<R, EX>(dtr, rs_S - lS));
         dC[1] = imul<R, EX>(dtr, rs_s1 - ls1);
         dC[2] = imul<R, EX>(dtr, rs_s2 - ls2);
         dC[3] = bv1;
         dC[4] = bv2;
-        dC[5] = imul<R, EX>(-dtr, rs_fe - lfe);
+        dC[5] = negx<R, EX>(imul<R, EX>(dtr, rs_fe - lfe));
         del_p = imul<R, EX>(dtr, rs_u);
         del_m = imul<R, EX>(dtr, lu);
 #pragma unroll
@@ -1367,7 +1395,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         }
         if (p <= NPe - 8) {                       // edge p+1/2: donor is this zone when del >= 0
             if (gt0<R, EX>(del_p)) {
-                R y = EX ? del_p / dxL : del_p * idxL_k;
+                R y = EX ? del_p / dxL : imul<R, EX>(del_p, idxL_k);
                 if (sliver_too_wide<R, EX>(y)) atomicOr(a.flags, FLAG_CFL);
                 if constexpr (EX) {
 #pragma unroll
@@ -1383,7 +1411,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             }
         }
         if (p >= 7 && lt0<R, EX>(del_m)) {       // edge p-1/2: donor is this zone when del < 0
-            R y = EX ? -del_m / dxL : -del_m * idxL_k;
+            R y = EX ? -del_m / dxL : imul<R, EX>(negx<R, EX>(del_m), idxL_k);
             if (sliver_too_wide<R, EX>(y)) atomicOr(a.flags, FLAG_CFL);
             if constexpr (EX) {
 #pragma unroll
