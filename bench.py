@@ -57,23 +57,23 @@ BYTES_PER_CELL_SWEEP = 128      # read 8 FP64 + write 8 FP64
 # The FP64 sweeps also read the dipole table (24 B per cell) on top of the
 # state: traffic above the algorithmic 128 B by that much.  The FP64 y and z
 # sweeps (72-register cap) also write back their register spills: the
-# blocks' dead stack frames leave L2 as DRAM writes, ~180 B per cell.  The
+# blocks' dead stack frames leave L2 as DRAM writes, ~130 B per cell.  The
 # FP64 CFL step's screen writes 4 B per cell that its FP64 pass reads back.
 NCU_TRAFFIC = {
-    "fp64:x": {"bytes_per_cell": 155.2, "src": "fc4fe0bd5032235c"},
-    "fp64:y": {"bytes_per_cell": 309.6, "src": "fc4fe0bd5032235c"},
-    "fp64:z": {"bytes_per_cell": 295.7, "src": "fc4fe0bd5032235c"},
-    # the two passes of the FP64 CFL step together (float screen 68.7, FP64 pass 4.0)
-    "fp64:cfl": {"bytes_per_cell": 72.7, "src": "e187dbc3cdd24379"},
-    "mixed:x": {"bytes_per_cell": 123.5, "src": "9090d9d48887f905"},
-    "mixed:y": {"bytes_per_cell": 124.6, "src": "9090d9d48887f905"},
-    "mixed:z": {"bytes_per_cell": 124.9, "src": "9090d9d48887f905"},
-    "mixed:cfl": {"bytes_per_cell": 64.3, "src": "a6f30ea0bd4cf058"},
+    "fp64:x": {"bytes_per_cell": 154.9, "src": "2c731ef70a588526"},
+    "fp64:y": {"bytes_per_cell": 267.2, "src": "2c731ef70a588526"},
+    "fp64:z": {"bytes_per_cell": 257.2, "src": "2c731ef70a588526"},
+    # the two passes of the FP64 CFL step together (float screen 68.6, FP64 pass 4.0)
+    "fp64:cfl": {"bytes_per_cell": 72.6, "src": "2493567777267e47"},
+    "mixed:x": {"bytes_per_cell": 123.6, "src": "64849b0245e3e2b7"},
+    "mixed:y": {"bytes_per_cell": 124.6, "src": "64849b0245e3e2b7"},
+    "mixed:z": {"bytes_per_cell": 124.9, "src": "64849b0245e3e2b7"},
+    "mixed:cfl": {"bytes_per_cell": 64.3, "src": "a5190bfe1746983c"},
     # ensemble sweeps: captured on the first 8 of the 48 instances (14.9 M
     # cells; the full ensemble holds ~10 GB), scaled by cells
-    "ensemble:x": {"bytes_per_cell": 125.1, "src": "cb21beb7cc2b286a"},
-    "ensemble:y": {"bytes_per_cell": 125.6, "src": "cb21beb7cc2b286a"},
-    "ensemble:z": {"bytes_per_cell": 125.5, "src": "cb21beb7cc2b286a"},
+    "ensemble:x": {"bytes_per_cell": 125.1, "src": "349c6cdb8894219f"},
+    "ensemble:y": {"bytes_per_cell": 125.6, "src": "349c6cdb8894219f"},
+    "ensemble:z": {"bytes_per_cell": 125.5, "src": "349c6cdb8894219f"},
 }
 
 
@@ -433,7 +433,7 @@ def run_ours(args, rank, world, dist):
                 "peak_nominal": FP64_NOMINAL_GFLOPS, "frac_of_nominal": ach / FP64_NOMINAL_GFLOPS,
                 "note": "frac can exceed 1: products, reciprocals and square roots of the FP64 sweeps run "
                         "correctly rounded on the integer and FP32 pipes beside the FP64 pipe (ncu: FP64 pipe "
-                        "69 % busy in x, 79 % in y)"}
+                        "75 % busy in x, 78 % in y)"}
     else:
         ach = BYTES_PER_CELL_SWEEP * cells / (avg_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
@@ -551,16 +551,16 @@ def run_ours(args, rank, world, dist):
                 ictx.close()
             extra["ionosphere_shell"] = io
 
-    # ---- end to end through the C ABI with host buffers: two contexts on
-    # two streams, each driven by its own host thread, so that one step's
-    # host<->device copies overlap the other context's kernels (every step
-    # still copies its whole input in from pinned host memory and its result
-    # out)
+    # ---- end to end through the C ABI with host buffers: three contexts on
+    # three streams, each driven by its own host thread,
+    # so that one context's host->device copy, another's device->host copy
+    # and a third's kernels run at once (every step still copies its whole
+    # input in from pinned host memory and its result out)
     e2e = None
     if not args.quick:
         host_in = torch.from_numpy(prob.U0).pin_memory()
         hin = host_in.numpy()
-        streams = [torch.cuda.Stream() for _ in range(2)]
+        streams = [torch.cuda.Stream() for _ in range(3)]
         ectxs = [ppmlr.Context.from_problem(prob, prec, stream=st.cuda_stream) for st in streams]
         houts = [torch.empty_like(host_in).pin_memory().numpy() for _ in ectxs]
         for c, h in zip(ectxs, houts):
@@ -568,7 +568,7 @@ def run_ours(args, rank, world, dist):
             c.autotune()                   # the tuned tiles (cached from the main run)
             c.step_cfl(prob.cfl, 1)
             c.get_state(h)
-        per_ctx = max(1, min(args.steps, 6) // 2)
+        per_ctx = max(1, min(args.steps, 12) // len(ectxs))
         errors = []
 
         def drive(c, h):
@@ -595,8 +595,8 @@ def run_ours(args, rank, world, dist):
         nbytes = 8 * 8 * cells
         e2e = {"value": world * cells * ksteps / t, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": ksteps,
-               "contexts": len(ectxs), "note": "two contexts on two streams and two host threads: one step's "
-                                               "copies overlap the other context's kernels"}
+               "contexts": len(ectxs), "note": "three contexts on three streams and host threads: one step's "
+                                               "input copy and another's result copy overlap a third's kernels"}
         for c in ectxs:
             c.close()
         del ectxs

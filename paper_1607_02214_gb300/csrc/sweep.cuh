@@ -1206,7 +1206,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
             if (a.riemann_iters > 0 && PLa > R(0) && PRa > R(0))
                 two_shock<R, EX>(a.riemann_iters, sl[1], Rs[1], PLa, PRa, gam, WL, WR);
         } else {
-            if (a.riemann_iters > 0 && PL > R(0) && PR > R(0))
+            if (a.riemann_iters > 0 && gt0<R, EX>(PL) && gt0<R, EX>(PR))
                 two_shock<R, EX>(a.riemann_iters, sl[1], Rs[1], PL, PR, gam, WL, WR);
         }
         R us, Ps;
@@ -1384,7 +1384,7 @@ __device__ __forceinline__ void sweep_tile(ARGS &a, const int tile, unsigned cha
         for (int v = 0; v < 7; v++) {
             pl[v] = SM(SC0 + v, s - PS);
             pr_[v] = red[v];
-            if (eta_k > R(0)) {   // steepened ends: towards the neighbours' one-sided values
+            if (gt0<R, EX>(eta_k)) {   // steepened ends: towards the neighbours' one-sided values
                 const R ld = SM(SB0 + v, s - PS) + R(0.5) * SM(v, s - PS);
                 const R rd = SM(SB0 + v, s + PS) - R(0.5) * SM(v, s + PS);
                 pl[v] = pl[v] * (R(1) - eta_k) + eta_k * ld;
