@@ -240,12 +240,12 @@ __device__ __forceinline__ double sqrt_int(double x)
 // or the significand's last bit is; the exponent field is ea + eb - 1023 + t
 // (the carry of a significand rounded to 2^53 moves into it).  Normal
 // operands with a normal result: the correctly rounded (to nearest, ties to
-// even) IEEE product, bit for bit.  Otherwise, without a branch (a branch
-// here would let the compiler's fusion of the surrounding multiplies and adds
-// differ between kernels): a zero or subnormal operand or an underflowing
-// result gives a signed zero, an overflowing one infinity, and an inf or NaN
-// operand a result with an all-ones exponent (inf or NaN), so a non-finite
-// state stays non-finite.
+// even) IEEE product, bit for bit.  Otherwise, with selects and no branch
+// (an inline fallback to the hardware product was compiled into a DMUL
+// issued every time, which took away the gain): a zero or subnormal operand
+// or an underflowing result gives a signed zero, an overflowing one
+// infinity, and an inf or NaN operand a result with an all-ones exponent
+// (inf or NaN), so a non-finite state stays non-finite.
 __device__ __forceinline__ double dmul_int(double a, double b)
 {
     const unsigned long long A = (unsigned long long)__double_as_longlong(a);
