@@ -17,6 +17,7 @@ barriers and the max-over-ranks reduction.
 """
 import argparse
 import hashlib
+import re
 import json
 import os
 import subprocess
@@ -53,27 +54,28 @@ def hbm_peak():
 FLOPS_PER_CELL = {"x": 1189.1, "y": 1241.9, "z": 1243.7, "cfl": 207.0}
 BYTES_PER_CELL_SWEEP = 128      # read 8 FP64 + write 8 FP64
 # DRAM bytes per cell of one launch measured by ncu for each kernel, with the
-# sha256 prefix of the kernel source they were taken on (null once it changes).
+# sha256 prefix of the kernel sources' code (comments left out) they were taken
+# on (null once it changes).
 # The FP64 sweeps also read the dipole table (24 B per cell) on top of the
 # state: traffic above the algorithmic 128 B by that much.  The FP64 y and z
 # sweeps (72-register cap) also write back their register spills: the
 # blocks' dead stack frames leave L2 as DRAM writes, ~130 B per cell.  The
 # FP64 CFL step's screen writes 4 B per cell that its FP64 pass reads back.
 NCU_TRAFFIC = {
-    "fp64:x": {"bytes_per_cell": 154.9, "src": "2c731ef70a588526"},
-    "fp64:y": {"bytes_per_cell": 267.2, "src": "2c731ef70a588526"},
-    "fp64:z": {"bytes_per_cell": 257.2, "src": "2c731ef70a588526"},
+    "fp64:x": {"bytes_per_cell": 154.9, "src": "9ba4c5569ffc3f83"},
+    "fp64:y": {"bytes_per_cell": 267.2, "src": "9ba4c5569ffc3f83"},
+    "fp64:z": {"bytes_per_cell": 257.2, "src": "9ba4c5569ffc3f83"},
     # the two passes of the FP64 CFL step together (float screen 68.6, FP64 pass 4.0)
-    "fp64:cfl": {"bytes_per_cell": 72.6, "src": "2493567777267e47"},
-    "mixed:x": {"bytes_per_cell": 123.6, "src": "64849b0245e3e2b7"},
-    "mixed:y": {"bytes_per_cell": 124.6, "src": "64849b0245e3e2b7"},
-    "mixed:z": {"bytes_per_cell": 124.9, "src": "64849b0245e3e2b7"},
-    "mixed:cfl": {"bytes_per_cell": 64.3, "src": "a5190bfe1746983c"},
+    "fp64:cfl": {"bytes_per_cell": 72.6, "src": "6549a833db154b84"},
+    "mixed:x": {"bytes_per_cell": 123.6, "src": "9831875bc4f8409c"},
+    "mixed:y": {"bytes_per_cell": 124.6, "src": "9831875bc4f8409c"},
+    "mixed:z": {"bytes_per_cell": 124.9, "src": "9831875bc4f8409c"},
+    "mixed:cfl": {"bytes_per_cell": 64.3, "src": "18b652b6cfc0a2d3"},
     # ensemble sweeps: captured on the first 8 of the 48 instances (14.9 M
     # cells; the full ensemble holds ~10 GB), scaled by cells
-    "ensemble:x": {"bytes_per_cell": 125.1, "src": "349c6cdb8894219f"},
-    "ensemble:y": {"bytes_per_cell": 125.6, "src": "349c6cdb8894219f"},
-    "ensemble:z": {"bytes_per_cell": 125.5, "src": "349c6cdb8894219f"},
+    "ensemble:x": {"bytes_per_cell": 125.1, "src": "be4670adf4282b76"},
+    "ensemble:y": {"bytes_per_cell": 125.6, "src": "be4670adf4282b76"},
+    "ensemble:z": {"bytes_per_cell": 125.5, "src": "be4670adf4282b76"},
 }
 
 
@@ -89,9 +91,19 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_only(text):
+    """C/C++ source without its comments, trailing blanks and empty lines:
+    what the hash of a kernel's sources covers, so that editing a comment
+    does not mark a capture stale."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
 def kernel_source_hash(key=None):
-    """sha256 prefix of the sources behind one NCU_TRAFFIC key ("fp64:x",
-    "mixed:cfl", ...), or of all kernel sources when key is None."""
+    """sha256 prefix of the code (comments left out) of the sources behind
+    one NCU_TRAFFIC key ("fp64:x", "mixed:cfl", ...), or of all kernel
+    sources when key is None."""
     if key is None:
         files = sorted({f for v in KERNEL_SOURCES.values() for f in v})
     else:
@@ -99,8 +111,8 @@ def kernel_source_hash(key=None):
         files = KERNEL_SOURCES[f"{prec}:{'cfl' if kern == 'cfl' else 'sweep'}"]
     h = hashlib.sha256()
     for f in files:
-        with open(os.path.join(ROOT, "paper_1607_02214_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1607_02214_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

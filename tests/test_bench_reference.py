@@ -23,3 +23,19 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("magnetosphere_32x24x24")
+
+
+def test_traffic_table_is_keyed_to_code_not_comments():
+    """The ncu traffic entries are keyed to a hash of the kernels' code: a
+    comment edit keeps them, a code edit marks them stale; every entry names
+    a kernel whose sources are listed."""
+    sys.path.insert(0, ROOT)
+    import bench
+    base = "int f(int a) { return a + 1; }\n"
+    assert bench._code_only(base) == bench._code_only("// one\n" + base + "/* two\n three */\n\n")
+    assert bench._code_only(base) != bench._code_only(base.replace("+ 1", "+ 2"))
+    for key, entry in bench.NCU_TRAFFIC.items():
+        prec, kern = key.split(":")
+        assert f"{prec}:{'cfl' if kern == 'cfl' else 'sweep'}" in bench.KERNEL_SOURCES
+        assert entry["bytes_per_cell"] > 0 and len(entry["src"]) == 16
+    assert len(bench.kernel_source_hash("fp64:x")) == 16
