@@ -1,5 +1,7 @@
 // FP64 sweep kernels, default form: IEEE double throughout, compiled with
-// contraction (fused multiply-add) and one reciprocal per shared denominator.
+// contraction (fused multiply-add) and one reciprocal per shared denominator;
+// products, reciprocals and square roots partly on the integer and FP32 pipes
+// (each correctly rounded), sign flips and compares on the bit patterns.
 // Agrees with the CPU reference to roundoff (parity bar: relative L1 1e-11).
 #include "launch.cuh"
 
