@@ -420,6 +420,8 @@ def run_ours(args, rank, world, dist):
 
     # ---- FP64 and FP32 pipe rates of this GPU (the FP64 roofline's peak)
     rates = ppmlr.measure_pipe_rates(torch.cuda.current_stream().cuda_stream)
+    if args.precision == "fp64":        # the integer-pipe product beside the FP64 pipe
+        rates.update(ppmlr.measure_coissue(torch.cuda.current_stream().cuda_stream))
     fp64_peak = 2.0 * rates["dfma_per_s"] * 1e-9
     hbm, hbm_src = hbm_peak()
 

@@ -457,6 +457,17 @@ void ppmlr_ensemble_destroy(ppmlr_ens *ens);
  * PPMLR_E_CUDA. */
 ppmlr_status ppmlr_measure_pipe_rates(void *cuda_stream, double rates[3]);
 
+/* Co-issue of the PPMLR_FP64 form's integer-pipe double product with the
+ * FP64 pipe (no paper counterpart): rates[0] products per second of that
+ * product alone (eight independent chains per thread, as above), rates[1]
+ * operations per second of four FP64 FMA chains beside four product chains
+ * per thread -- above rates[0] and above the FP64 FMA rate of
+ * ppmlr_measure_pipe_rates when the two pipes issue side by side.  Runs on
+ * `cuda_stream` (NULL = default), allocates and frees one scratch buffer,
+ * synchronises the stream.  Errors: PPMLR_E_INVALID (rates NULL),
+ * PPMLR_E_OOM, PPMLR_E_CUDA. */
+ppmlr_status ppmlr_measure_coissue(void *cuda_stream, double rates[2]);
+
 /* Self-test of the PPMLR_FP64 form's own square root, reciprocal and
  * product (integer and FP32 arithmetic, each correctly rounded); no paper
  * counterpart.  Over n >= 1 arguments (1 + f) 2^e, e cycling over

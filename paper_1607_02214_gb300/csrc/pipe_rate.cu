@@ -3,12 +3,14 @@
 // dependency chains of one operation so that the pipe, not the latency of a
 // chain, sets the rate; 8 blocks of 256 threads per SM; CUDA events on the
 // caller's stream around one launch after a warm-up launch.
-#include "ppmlr_internal.h"
+#include "sweep.cuh"
 
 namespace ppmlr {
 namespace {
 
-enum PipeOp { OP_DFMA = 0, OP_DADD = 1, OP_FFMA = 2 };
+// OP_IMUL: the integer-pipe double product of the contracted FP64 sweeps
+// (dmul_int); OP_MIX: four chains of FP64 FMAs beside four of dmul_int
+enum PipeOp { OP_DFMA = 0, OP_DADD = 1, OP_FFMA = 2, OP_IMUL = 3, OP_MIX = 4 };
 
 template <int OP>
 __global__ void __launch_bounds__(256) pipe_chains_kernel(double *out, int iters, double seed)
@@ -26,6 +28,8 @@ __global__ void __launch_bounds__(256) pipe_chains_kernel(double *out, int iters
         for (int k = 0; k < 8; k++) {
             if (OP == OP_DFMA) a[k] = fma(a[k], m, c);
             if (OP == OP_DADD) a[k] = a[k] + c;
+            if (OP == OP_IMUL) a[k] = dmul_int(a[k], m);
+            if (OP == OP_MIX) a[k] = (k & 1) ? dmul_int(a[k], m) : fma(a[k], m, c);
             if (OP == OP_FFMA) {
 #pragma unroll
                 for (int r = 0; r < 8; r++) f[k] = fmaf(f[k], 0.999f, 1e-3f);
@@ -87,6 +91,29 @@ extern "C" ppmlr_status ppmlr_measure_pipe_rates(void *cuda_stream, double rates
                                         : time_chains<OP_FFMA>(out, blocks, iters[op], s, &ms);
         if (e != cudaSuccess || !(ms > 0.0f)) st = PPMLR_E_CUDA;
         else rates[op] = ops_per_iter[op] * iters[op] * (double)blocks * threads / (ms * 1e-3);
+    }
+    cudaFree(out);
+    return st;
+}
+
+extern "C" ppmlr_status ppmlr_measure_coissue(void *cuda_stream, double rates[2])
+{
+    if (!rates) return PPMLR_E_INVALID;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        return PPMLR_E_CUDA;
+    const int blocks = 8 * sms, threads = 256, iters = 2000;
+    double *out = nullptr;
+    if (cudaMalloc(&out, sizeof(double) * blocks * threads) != cudaSuccess) return PPMLR_E_OOM;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    ppmlr_status st = PPMLR_OK;
+    for (int k = 0; k < 2 && st == PPMLR_OK; k++) {
+        float ms = 0.0f;
+        cudaError_t e = k == 0 ? time_chains<OP_IMUL>(out, blocks, iters, s, &ms)
+                               : time_chains<OP_MIX>(out, blocks, iters, s, &ms);
+        if (e != cudaSuccess || !(ms > 0.0f)) st = PPMLR_E_CUDA;
+        else rates[k] = 8.0 * iters * (double)blocks * threads / (ms * 1e-3);
     }
     cudaFree(out);
     return st;

@@ -108,6 +108,7 @@ SIGNATURES = [
                                      c_void_p]),
     ("ppmlr_measure_pipe_rates", c_int, [c_void_p, POINTER(c_double)]),
     ("ppmlr_selftest_fp64_arith", c_int, [c_void_p, c_longlong, POINTER(c_double)]),
+    ("ppmlr_measure_coissue", c_int, [c_void_p, POINTER(c_double)]),
     ("ppmlr_set_march_chunk", c_int, [c_void_p, c_int, c_int]),
 ]
 
@@ -143,6 +144,16 @@ def measure_pipe_rates(stream=None):
     if st != PPMLR_OK:
         raise PPMLRError(st, "ppmlr_measure_pipe_rates failed")
     return {"dfma_per_s": out[0], "dadd_per_s": out[1], "ffma_per_s": out[2]}
+
+
+def measure_coissue(stream=None):
+    """Integer-pipe double products per second alone, and FP64 FMAs plus
+    such products per second when interleaved (ppmlr_measure_coissue)."""
+    out = (c_double * 2)()
+    st = load().ppmlr_measure_coissue(c_void_p(stream), out)
+    if st != PPMLR_OK:
+        raise PPMLRError(st, "ppmlr_measure_coissue failed")
+    return {"int_dmul_per_s": out[0], "dfma_plus_int_dmul_per_s": out[1]}
 
 
 def selftest_fp64_arith(n=1 << 22, stream=None):

@@ -31,3 +31,14 @@ def test_sqrt_reciprocal_and_product_exact():
 def test_rejects_bad_arguments():
     with pytest.raises(ppmlr.PPMLRError):
         ppmlr.selftest_fp64_arith(0)
+
+
+def test_integer_product_issues_beside_the_fp64_pipe():
+    """The integer-pipe product runs at a useful rate alone, and interleaved
+    with FP64 FMAs the two together retire more operations per second than
+    the FP64 pipe alone (the premise of moving products off it)."""
+    co = ppmlr.measure_coissue()
+    fp = ppmlr.measure_pipe_rates()
+    print(co, fp)
+    assert co["int_dmul_per_s"] > 0.5 * fp["dfma_per_s"]
+    assert co["dfma_plus_int_dmul_per_s"] > 1.2 * fp["dfma_per_s"]
